@@ -1,0 +1,19 @@
+"""CPU FP64 oracle of the matrix-free FMG Stokes solver.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+or run anything in this package.  The CUDA library never links, imports or
+calls it, and it never calls the CUDA library.
+
+Modules:
+  * fe         -- exact element matrices (barycentric monomial integration)
+  * mesh       -- Kuhn lattices of refined Kuhn-box macro meshes, Bey's rule
+  * stokes     -- assembly, rhs, multicolour Gauss-Seidel, inexact Uzawa,
+                  transfers, bordered coarse solve, V-cycle, FMG, errors,
+                  power iteration for omega^{-1}
+  * workmodel  -- the paper's work-unit model
+
+Parity status of each function is listed in the design notes; every function
+here is pinned by a test in tests/test_oracle_*.py against values the paper
+prints, closed forms, invariants or brute force.
+"""
