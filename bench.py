@@ -1,0 +1,359 @@
+"""Benchmark: FMG-solved Stokes DoF/s at discretisation-error accuracy.
+
+Workload (default): P2-P1 Taylor-Hood Stokes on the unit cube split into 6
+macro tetrahedra, refined to level 6 (3 x 129^3 velocity + 65^3 pressure
+DoFs = 6,714,692 incl. Dirichlet nodes), manufactured curl solution, one FMG
+solve per step with FP32 V-cycles inside FP64 iterative refinement.  The
+inputs (right-hand sides of all levels) are resident in HBM before the timed
+region; L2 is flushed before every timed step and each step is timed alone
+with CUDA events on the solver's stream.
+
+Also reported: the FP64-only GPU solve of the same workload, the accuracy
+(gamma_u, gamma_p of Sec. 5.1, error against the exact solution relative to
+the discretisation error), the operator-apply roofline, the CPU oracle on a
+bounded sample, and an end-to-end number through the C ABI with host data.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {hhg,reference}]
+Multi-GPU: one independent replica per rank ("replicas only"), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMG-solved Stokes DoF/s at disc.-error accuracy; operator-apply HBM GB/s"
+WORKLOAD = dict(disc="P2P1", box=(1, 1, 1), L=6, lc=1, kind="curl")
+# FMG tuple s = (nu_pre, nu_post, nu_inc, kappa, A_hat, xi); omega^{-1} from 100
+# power iterations on the finest level
+PARAMS = dict(nu_pre=1, nu_post=2, nu_inc=1, kappa=2, ahat="f", xi=3)
+CPU_SAMPLE_LEVEL = 4
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def make_problem(solve, error_level=False):
+    from hhg_inputs import Workload
+    from paper_2010_13513_gb300 import hhg
+    w = WORKLOAD
+    pb = hhg.Problem(hhg.Mesh.box(*w["box"], 1.0), disc=w["disc"], L=w["L"], coarse_level=w["lc"], solve=solve,
+                     error_level=error_level)
+    wl = Workload(w["kind"])
+    hhg.set_workload_rhs(pb, wl)
+    return pb, wl
+
+
+def omega_inv(pb):
+    info = pb.layout(WORKLOAD["L"])
+    v0 = np.random.default_rng(0).uniform(-1, 1, info.n_pressure_nodes)
+    return pb.estimate_omega(WORKLOAD["L"], v0, iters=100)
+
+
+def accuracy(pb, wl, prm, x):
+    """gamma_u, gamma_p (Eqs. error, gamma): error of the FMG result over the
+    error of the discrete solution (residuals < 1e-12)."""
+    import torch
+    from paper_2010_13513_gb300 import hhg
+    L = WORKLOAD["L"]
+    info = pb.layout(L + 1)
+    ue = wl.exact_velocity(hhg.velocity_coords(info)).T.ravel()
+    pe = wl.exact_pressure(hhg.pressure_coords(info))
+    e_fmg = pb.error_norms(L, x, ue, pe)
+    xs = x.clone()
+    b = pb.level_vector(L, "rhs")
+    r = pb.new_vector(L)
+    cycles = 0
+    for cycles in range(1, 400):
+        pb.vcycle(L, prm, xs, b)
+        nu, npp = pb.residual(L, xs, b, r, norms=True)
+        if max(nu, npp) < 1e-12:
+            break
+    e_disc = pb.error_norms(L, xs, ue, pe)
+    torch.cuda.synchronize()
+    return e_fmg[0] / e_disc[0], e_fmg[1] / e_disc[1], e_fmg, e_disc, cycles, (nu, npp)
+
+
+def time_steps(pb, prm, x, steps, warmup, stream):
+    import torch
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        pb.fmg_solve(prm, x, stats=False)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.fill_(1.0)                          # evict L2 (512 MB > 129 MB)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        pb.fmg_solve(prm, x, stats=False)
+        e.record(stream)
+        e.synchronize()
+        times.append(s.elapsed_time(e))
+    return times
+
+
+def apply_roofline(pb, steps=20):
+    """Average duration of the FP32 operator apply y = calA x on the finest
+    level, each launch timed alone after an L2 flush."""
+    import torch
+    L = WORKLOAD["L"]
+    info = pb.layout(L)
+    x = pb.new_vector(L, prec=1)
+    x.uniform_(-1, 1)
+    y = pb.new_vector(L, prec=1)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        pb.apply(L, "FULL", x, y)
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(st)
+        pb.apply(L, "FULL", x, y)
+        e.record(st)
+        e.synchronize()
+        ts.append(s.elapsed_time(e))
+    t = statistics.mean(ts) * 1e-3
+    alg_bytes = info.n_dofs * 4 * 2           # read every DoF once, write every DoF once (FP32)
+    return alg_bytes, t
+
+
+def e2e_steps(pb, wl, prm, steps):
+    """Through the public API with host data: nodal forcing/Dirichlet data from
+    host memory (hhg_set_rhs on every level, assembled on the GPU), the FMG
+    solve, and the solution copied back to the host."""
+    import torch
+    from paper_2010_13513_gb300 import hhg
+    L = WORKLOAD["L"]
+    host = {}
+    h2d = 0
+    for l in range(WORKLOAD["lc"], L + 1):
+        info = pb.layout(l)
+        X = hhg.velocity_coords(info)
+        f = np.ascontiguousarray(wl.forcing(X).T.ravel())
+        w = np.ascontiguousarray(wl.dirichlet(X).T.ravel())
+        host[l] = (f, w)
+        h2d += f.nbytes + w.nbytes
+    x = pb.new_vector(L)
+    d2h = pb.layout(L).n_dofs * 8
+    ts = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for l, (f, w) in host.items():
+            pb.set_rhs(l, f, w)
+        pb.fmg_solve(prm, x, stats=False)
+        out = pb.to_host(L, x)
+        ts.append(time.perf_counter() - t0)
+    assert np.isfinite(out).all()
+    return ts, h2d, d2h
+
+
+def cpu_baseline(prm_dict, level=CPU_SAMPLE_LEVEL):
+    """The FP64 CPU oracle as it stands, FMG on the same workload at a smaller
+    level (bounded sample), timed on the host cores."""
+    from hhg_inputs import Workload
+    from oracle.stokes import Params, StokesHierarchy
+    w = WORKLOAD
+    hy = StokesHierarchy(w["box"], 1.0, level, w["disc"], coarse_level=w["lc"], workload=Workload(w["kind"]))
+    prm = Params(**prm_dict)
+    hy.fmg(prm)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        hy.fmg(prm)
+        n += 1
+        if time.perf_counter() - t0 > 10.0 or n >= 5:
+            break
+    dt = (time.perf_counter() - t0) / n
+    dofs = hy.lv[level].size
+    return {"value": dofs / dt, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{w['disc']} 6-tet cube level {level} ({dofs} DoF), FMG {n}x, {dt:.2f} s each, single-threaded numpy/scipy"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prm = dict(PARAMS, omega_inv=0.3)
+    times, dofs = [], 0
+    from hhg_inputs import Workload
+    from oracle.stokes import Params, StokesHierarchy
+    w = WORKLOAD
+    hy = StokesHierarchy(w["box"], 1.0, CPU_SAMPLE_LEVEL, w["disc"], coarse_level=w["lc"], workload=Workload(w["kind"]))
+    dofs = hy.lv[CPU_SAMPLE_LEVEL].size
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        hy.fmg(Params(**prm))
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    v = dofs / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w['disc']} Stokes, 6-macro-tet cube, oracle sample at level {CPU_SAMPLE_LEVEL} "
+                                   f"of the level-{w['L']} workload", "params": PARAMS},
+            "cpu_baseline": {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"level {CPU_SAMPLE_LEVEL} ({dofs} DoF) per step"},
+            "e2e": {"value": v, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hhg", choices=["hhg", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="only set-up, warm-up and the timed FMG steps, bracketed by cudaProfilerStart/Stop")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2010_13513_gb300 import hhg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    hhg.load()
+    L = WORKLOAD["L"]
+
+    # ---------------- set-up (not timed): hierarchy, rhs on all levels, omega
+    pb, wl = make_problem("mixed", error_level=(rank == 0 and not args.profile_region))
+    if args.profile_region:
+        prm = hhg.Params.make(**PARAMS, omega_inv=0.32)
+        x = pb.new_vector(L)
+        for _ in range(args.warmup):
+            pb.fmg_solve(prm, x, stats=False)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.steps):
+            pb.fmg_solve(prm, x, stats=False)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return
+    om = omega_inv(pb)
+    prm = hhg.Params.make(**PARAMS, omega_inv=om)
+    stream = pb.stream
+    x = pb.new_vector(L)
+    st = pb.fmg_solve(prm, x)
+    launches = st.kernel_launches
+    acc = accuracy(pb, wl, prm, x) if rank == 0 else None
+
+    # ---------------- timed region
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = time_steps(pb, prm, x, args.steps, args.warmup, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    t_step = statistics.mean(times) * 1e-3
+    if world > 1:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    dofs = pb.layout(L).n_dofs
+    value = world * dofs / t_step
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    # FP64-only GPU solve of the same workload (same tuple, same omega)
+    pb64, _ = make_problem("fp64")
+    x64 = pb64.new_vector(L)
+    t64 = statistics.mean(time_steps(pb64, prm, x64, max(3, args.steps // 2), 2, pb64.stream)) * 1e-3
+    mixed_vs_fp64 = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+    del pb64
+
+    alg_bytes, t_apply = apply_roofline(pb)
+    pk, src = peaks()
+    achieved = alg_bytes / t_apply / 1e9
+    e2e_t, h2d, d2h = e2e_steps(pb, wl, prm, max(2, min(args.steps, 3)))
+    e2e_v = dofs / statistics.mean(e2e_t)
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "P2-P1 Taylor-Hood Stokes, 6-macro-tet unit cube, level 6, curl manufactured solution, "
+                               "FMG with FP32 V-cycles in FP64 iterative refinement",
+                   "dofs": dofs, "params": PARAMS, "omega_inv": om, "coarse_level": WORKLOAD["lc"],
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "gamma_u": acc[0], "gamma_p": acc[1], "disc_accuracy": bool(acc[0] <= 2 and acc[1] <= 2),
+                   "err_fmg": acc[2], "err_disc": acc[3], "disc_solve_cycles": acc[4],
+                   "wu_model": st.wu_model, "wu_counted": st.wu_counted,
+                   "fp64_gpu_ms_per_step": t64 * 1e3, "mixed_speedup_vs_fp64_gpu": t64 / t_step,
+                   "mixed_vs_fp64_rel_diff": mixed_vs_fp64},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "FP32 operator apply y = calA x, level 6 (k_apply)",
+                     "alg_bytes": alg_bytes, "avg_launch_us": t_apply * 1e6, "peak_source": src},
+        "e2e": {"value": e2e_v, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(dict(PARAMS, omega_inv=om))
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * hhg.h -- C ABI of the GB300 matrix-free FMG Stokes library.
+ *
+ * The library solves the discrete Stokes system of Kohl & Ruede,
+ * "Textbook efficiency: massively parallel matrix-free multigrid for the
+ * Stokes system" (arXiv 2010.13513):
+ *
+ *     [ A   B^T ] [u]   [f]
+ *     [ B   -C  ] [p] = [g],        A = diag(A, A, A)          (Sec. 2, Eq. stokes-discrete)
+ *
+ * with stabilised P1-P1 (PSPG, Eq. pspg, delta = 1/12) or Taylor-Hood P2-P1
+ * elements on a hierarchy of uniformly refined macro meshes (Sec. 2.1),
+ * by full multigrid with variable V-cycles (Algorithm 1), an inexact Uzawa
+ * smoother (Sec. 3.2, Eqs. uzawa-iteration / uzawa-velocity / uzawa-pressure)
+ * and nodal-interpolation transfers (Sec. 3.3).  Every step of the solve
+ * runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ *  - Return value: 0 (HHG_OK) or a negative HHG_E* code.  A human-readable
+ *    description of the most recent error of the calling thread is returned
+ *    by hhg_last_error().  No entry point aborts the process.
+ *  - Handles (hhg_mesh, hhg_problem) are opaque, created and freed by the
+ *    library (*_create / *_destroy).
+ *  - Device memory: the library never allocates device memory for a
+ *    problem.  The caller allocates one workspace of the size reported by
+ *    hhg_problem_workspace_bytes() (e.g. as a torch tensor) and binds it with
+ *    hhg_problem_bind(); the library owns its contents until the problem is
+ *    destroyed, the caller keeps ownership of the allocation.
+ *  - Vector arguments "x", "b", "y", "r" are device pointers into caller-owned
+ *    buffers laid out as described by hhg_layout(); they are borrowed for the
+ *    duration of the call and never freed by the library.  Their element type
+ *    is given by the `prec` argument (HHG_FP64: double, HHG_FP32: float).
+ *  - Every kernel is issued on the CUDA stream passed to hhg_problem_bind()
+ *    and all calls are asynchronous with respect to the host unless they
+ *    return host values (norms, statistics), which synchronise that stream.
+ *  - Host arrays are "canonical": nodal values in lexicographic order of the
+ *    velocity nodes (first index fastest) -- the level-l lattice for P1-P1,
+ *    the doubled lattice (the level-(l+1) lattice) for P2-P1 -- and of the
+ *    pressure nodes (level-l lattice); a block vector is [u1 | u2 | u3 | p].
+ *
+ * Supported macro meshes
+ * ----------------------
+ *  Unions of Kuhn-split cubes: an mx x my x mz box of cubes of side H, each cut
+ *  into the 6 tetrahedra around its (0,0,0)-(1,1,1) diagonal.  Bey refinement
+ *  of such a macro mesh is the Kuhn (Freudenthal) lattice with spacing
+ *  h = H / 2^l on every level, so each field is stored box-shaped and every
+ *  macro-cell carries the same constant stencils (Sec. 2.1).  All boundary
+ *  faces are Dirichlet for the velocity; the pressure is fixed by its zero
+ *  mean (Sec. 2).
+ */
+#ifndef HHG_H
+#define HHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define HHG_OK          0
+#define HHG_EINVAL     -1   /* invalid argument, unsupported mesh or size */
+#define HHG_ENOMEM     -2   /* bound workspace too small / host allocation failed */
+#define HHG_ECUDA      -3   /* a CUDA runtime call failed */
+#define HHG_EDIVERGED  -4   /* residual grew beyond the divergence guard or became NaN */
+#define HHG_ETIMEOUT   -5   /* a bounded device-side wait gave up */
+#define HHG_EREJECTED  -6   /* learned coarse correction rejected (internal) */
+#define HHG_ESTATE     -7   /* call out of order (e.g. before hhg_problem_bind) */
+
+#define HHG_P1P1_PSPG   1   /* stabilised equal order (Sec. 2, Eq. pspg) */
+#define HHG_P2P1_TH     2   /* Taylor-Hood, C = 0 */
+
+#define HHG_FP64        0
+#define HHG_FP32        1
+
+/* solve precision of a problem */
+#define HHG_SOLVE_FP64  0   /* every level in double */
+#define HHG_SOLVE_MIXED 1   /* FP32 V-cycles inside FP64 iterative refinement */
+
+/* operators for hhg_apply */
+#define HHG_OP_FULL     0   /* y = calA x                                     */
+#define HHG_OP_A        1   /* velocity rows: A u_c; pressure rows 0          */
+#define HHG_OP_BT       2   /* velocity rows: B^T p                           */
+#define HHG_OP_B        3   /* pressure rows: B u                             */
+#define HHG_OP_C        4   /* pressure rows: C p                             */
+#define HHG_OP_MASS     5   /* consistent mass, all rows incl. boundary       */
+
+/* velocity smoother A_hat (Sec. 3.2) */
+#define HHG_AHAT_F      0   /* forward Gauss-Seidel                  */
+#define HHG_AHAT_S      1   /* forward + backward Gauss-Seidel       */
+
+typedef struct hhg_mesh hhg_mesh;
+typedef struct hhg_problem hhg_problem;
+
+typedef struct {
+    int disc;            /* HHG_P1P1_PSPG or HHG_P2P1_TH                                  */
+    int L;               /* finest level                                                  */
+    int coarse_level;    /* level of the direct coarse solve (0 = Algorithm 1)            */
+    int solve;           /* HHG_SOLVE_FP64 or HHG_SOLVE_MIXED                             */
+    double nu_a;         /* viscosity nu = exp(nu_a * z); 0 gives nu = 1                  */
+    int pspg_rhs;        /* 1: consistent PSPG load term in g (P1-P1 only)                */
+    int error_level;     /* 1: also set up level L+1 for hhg_error_norms                   */
+} hhg_problem_desc;
+
+typedef struct {
+    int level;
+    int nx, ny, nz;            /* cells per direction, m * 2^level                          */
+    int groups;                /* velocity DoF groups per component: 1 (P1) or 8 (P2)       */
+    int sx;                    /* element pitch between j rows of one group array           */
+    int64_t sy;                /* element pitch between k planes                            */
+    int64_t array_elems;       /* elements of one group array (incl. one halo layer, padded)*/
+    int64_t vector_elems;      /* elements of a block vector: (3 * groups + 1) * array_elems */
+    int64_t n_velocity_nodes;  /* canonical velocity nodes per component                    */
+    int64_t n_pressure_nodes;  /* canonical pressure nodes                                  */
+    int64_t n_dofs;            /* 3 * n_velocity_nodes + n_pressure_nodes (incl. Dirichlet) */
+    double h;                  /* mesh width of the level                                   */
+} hhg_layout_info;
+
+/* The FMG parameter tuple s = (nu_pre, nu_post, nu_inc, kappa, A_hat, xi) of
+ * Algorithm 1 / Sec. 5.1 and the pressure relaxation parameter omega^{-1}
+ * (S_hat = omega^{-1} M_L). */
+typedef struct {
+    int nu_pre, nu_post, nu_inc, kappa;
+    int ahat;            /* HHG_AHAT_F or HHG_AHAT_S */
+    int xi;              /* inner Gauss-Seidel sweeps of the velocity step */
+    double omega_inv;
+} hhg_params;
+
+typedef struct {
+    double wu_model;          /* W(FMG(s)) of the paper's cost model (Sec. 4.2)          */
+    double wu_counted;        /* operator-apply equivalents actually executed            */
+    double res_u, res_p;      /* final Euclidean residual norms on level L (FP64)        */
+    int64_t kernel_launches;  /* kernels issued by the call                              */
+} hhg_stats;
+
+/* ------------------------------------------------------------------ errors */
+/* Copies the last error message of the calling thread (NUL-terminated). */
+int hhg_last_error(char* buf, size_t len);
+
+/* ------------------------------------------------------------------ meshes */
+/* Macro mesh T_0 (Sec. 2): nv vertices (xyz, row-major doubles), nt tetrahedra
+ * (4 vertex ids each).  Must be a Kuhn-split box of cubes (see above);
+ * otherwise HHG_EINVAL.  Arrays are read during the call only. */
+int hhg_mesh_create(const double* verts, int nv, const int* tets, int nt, hhg_mesh** out);
+/* Same mesh given by its box: mx x my x mz cubes of side H. */
+int hhg_mesh_create_box(int mx, int my, int mz, double H, hhg_mesh** out);
+int hhg_mesh_destroy(hhg_mesh* mesh);
+
+/* ---------------------------------------------------------------- problems */
+/* Level hierarchy coarse_level..L and its constant stencils (Sec. 2.1-2.2,
+ * Table 2): element matrices of the 6 Kuhn classes are summed into per-group
+ * stencils.  Host-only; no device memory is touched. */
+int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* desc, hhg_problem** out);
+int hhg_problem_workspace_bytes(const hhg_problem* pb, size_t* bytes);
+/* Binds a device workspace (>= hhg_problem_workspace_bytes, 256-byte aligned)
+ * and the CUDA stream (cudaStream_t, 0 = legacy default stream); uploads the
+ * stencil and transfer tables, assembles and inverts the bordered coarse
+ * system.  Synchronises the stream. */
+int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, void* stream);
+int hhg_problem_destroy(hhg_problem* pb);
+int hhg_layout(const hhg_problem* pb, int level, hhg_layout_info* info);
+
+/* Canonical host vector -> device layout (and back); halo and padding
+ * entries are written as zeros.  Velocity Dirichlet entries are copied as
+ * given.  Synchronous. */
+int hhg_vector_from_host(hhg_problem* pb, int level, int prec, const double* host, void* dev);
+int hhg_vector_to_host(hhg_problem* pb, int level, int prec, const void* dev, double* host);
+
+/* Right-hand side of level l (Sec. 2, below Eq. stokes-discrete):
+ *   f = M f_h - A w_h (interior velocity rows), g = -B w_h (+ PSPG load),
+ * g projected to sum zero.  f_nodal: forcing at the canonical velocity nodes
+ * (3 x n_velocity_nodes, component-major); w_nodal: Dirichlet data at the same
+ * nodes (only boundary entries are read).  Kept inside the workspace. */
+int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal);
+/* Device pointer of a library-owned FP64 level vector: 0 = rhs, 1 = boundary
+ * lifting w_h, 2 = FMG solution x. */
+int hhg_level_vector(hhg_problem* pb, int level, int which, void** dev);
+
+/* ---------------------------------------------------------- hot-path steps */
+/* y = Op x on level l (Eq. stokes-discrete blocks); Dirichlet velocity rows
+ * of y are 0 except for HHG_OP_MASS. */
+int hhg_apply(hhg_problem* pb, int level, int op, int prec, const void* x, void* y);
+/* r = b - calA x; if norms != NULL, norms[0] = ||r_u||_2, norms[1] = ||r_p||_2
+ * (synchronises). */
+int hhg_residual(hhg_problem* pb, int level, int prec, const void* x, const void* b, void* r, double* norms);
+/* `sweeps` inexact Uzawa iterations (Eq. uzawa-iteration) on x in place. */
+int hhg_smooth(hhg_problem* pb, int level, const hhg_params* prm, int sweeps, int prec, void* x, const void* b);
+/* r_coarse = I_l^{l-1} r_fine = (I_{l-1}^l)^T r_fine (Sec. 3.3), Dirichlet rows 0. */
+int hhg_restrict(hhg_problem* pb, int level, int prec, const void* r_fine, void* r_coarse);
+/* x_fine += I_{l-1}^l x_coarse (linear P1 / quadratic P2 interpolation). */
+int hhg_prolongate_add(hhg_problem* pb, int level, int prec, const void* x_coarse, void* x_fine);
+/* Direct solve on the coarse level, bordered by the mean-pressure constraint. */
+int hhg_coarse_solve(hhg_problem* pb, int prec, const void* b, void* x);
+/* One VAR-V-CYCLE(l, l, ...) of Algorithm 1 on x in place. */
+int hhg_vcycle(hhg_problem* pb, int level, const hhg_params* prm, int prec, void* x, const void* b);
+/* FMG of Algorithm 1 with the rhs set by hhg_set_rhs on every level.  Writes
+ * the level-L FP64 solution (lifting form: Dirichlet rows 0, p mean zero) to
+ * x_out (device, may be NULL to keep it only in the workspace).  stats may be
+ * NULL; if given, residual norms are computed (synchronises). */
+int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats* stats);
+/* omega^{-1}: `iters` power iterations on M_L^{-1}(C + B A_s^{-1} B^T)
+ * (Eq. omega-eigenvalue-problem) from the host start vector v0 (canonical
+ * pressure order). */
+int hhg_estimate_omega(hhg_problem* pb, int level, int iters, const double* v0, double* omega_inv);
+/* ||e(x)||_2 of Eq. error: M-norm on level l+1 of x* - I x (x the lifting-form
+ * FP64 solution on level l; the boundary values w_h are added), pressures with
+ * zero mean.  u_exact / p_exact: exact nodal values on level l+1 (canonical).
+ * Needs desc.error_level = 1 and l == L. */
+int hhg_error_norms(hhg_problem* pb, int level, const void* x, const double* u_exact,
+                    const double* p_exact, double* err_u, double* err_p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HHG_H */

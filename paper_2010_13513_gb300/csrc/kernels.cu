@@ -1,0 +1,414 @@
+// CUDA kernels of the HHG Stokes library (sm_103a).
+//
+// All kernels work on the box-shaped group arrays described in internal.h.
+// One thread owns one DoF site (coarse index (i,j,k)); consecutive threads
+// of a warp own consecutive i, so every stencil term is one coalesced load
+// of 32 consecutive elements.  Stencil tables are warp-uniform reads of a few
+// KB that stay in L1.  Reductions are deterministic (fixed grid, fixed
+// order of the final pass).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "kernels.h"
+
+namespace hhg {
+
+thread_local int64_t g_launches = 0;
+
+namespace {
+
+template <class T> __device__ __forceinline__ T wsel(const double* w64, const float* w32, int t);
+template <> __device__ __forceinline__ double wsel<double>(const double* w64, const float*, int t) { return __ldg(w64 + t); }
+template <> __device__ __forceinline__ float wsel<float>(const double*, const float* w32, int t) { return __ldg(w32 + t); }
+
+__device__ __forceinline__ int64_t site_index(const Geo& g, int i, int j, int k) {
+  return int64_t(i + 1) + int64_t(j + 1) * g.sx + int64_t(k + 1) * g.sy;
+}
+
+// DoF at coarse index (i,j,k) of group offset (ox,oy,oz): valid and on the boundary?
+__device__ __forceinline__ bool dof_valid(const Geo& g, int i, int j, int k, int ox, int oy, int oz) {
+  return i <= g.nx - ox && j <= g.ny - oy && k <= g.nz - oz && i >= 0 && j >= 0 && k >= 0;
+}
+__device__ __forceinline__ bool dof_boundary(const Geo& g, int i, int j, int k, int ox, int oy, int oz) {
+  const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
+  return Px == 0 || Py == 0 || Pz == 0 || Px == 2 * g.nx || Py == 2 * g.ny || Pz == 2 * g.nz;
+}
+
+__constant__ int c_goff[8][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
+
+// ------------------------------------------------------------------ apply
+template <class T, int MODE>
+__global__ void __launch_bounds__(128) k_apply(Geo g, OpDev op, const T* __restrict__ x, const T* __restrict__ b,
+                                               T* __restrict__ y, T alpha) {
+  const int nzp = g.nz + 1;
+  const int r = blockIdx.z / nzp;
+  const int k = blockIdx.z - r * nzp;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const DRow row = op.rows[r];
+  const int ox = c_goff[row.og][0], oy = c_goff[row.og][1], oz = c_goff[row.og][2];
+  if (!dof_valid(g, i, j, k, ox, oy, oz)) return;
+  const int64_t idx = site_index(g, i, j, k);
+  T* yo = y + int64_t(row.out_arr) * g.arr + idx;
+  const bool bnd = dof_boundary(g, i, j, k, ox, oy, oz);
+  T acc[3] = {T(0), T(0), T(0)};
+  if (!bnd) {
+    int t = row.t0;
+    const int ns[3] = {row.n0, row.n1, row.n2};
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      T a = T(0);
+      for (int e = 0; e < ns[s]; ++e, ++t) {
+        const DTerm tm = op.terms[t];
+        a += wsel<T>(op.w64, op.w32, t) * x[int64_t(tm.arr) * g.arr + idx + tm.off];
+      }
+      acc[s] = a;
+    }
+  } else if (row.all_rows) {
+    int t = row.b0;
+    const int ms[3] = {row.m0, row.m1, row.m2};
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      T a = T(0);
+      for (int e = 0; e < ms[s]; ++e, ++t) {
+        const DTermB tm = op.bterms[t];
+        const int qx = i + tm.cx, qy = j + tm.cy, qz = k + tm.cz;
+        if (qx < 0 || qy < 0 || qz < 0 || qx >= g.nx || qy >= g.ny || qz >= g.nz) continue;
+        a += wsel<T>(op.bw64, op.bw32, t) * x[int64_t(tm.arr) * g.arr + idx + tm.off];
+      }
+      acc[s] = a;
+    }
+  } else {
+    if (MODE != MODE_ADD) *yo = T(0);
+    return;
+  }
+  T v = acc[0];
+  if (g.nu_ah != 0.0) {
+    const T e = T(exp(g.nu_ah * k));
+    v += e * acc[1] + acc[2] / e;
+  } else {
+    v += acc[1] + acc[2];
+  }
+  if (MODE == MODE_SET) *yo = v;
+  else if (MODE == MODE_RES) *yo = b[int64_t(row.out_arr) * g.arr + idx] - v;
+  else *yo += alpha * v;
+}
+
+// ------------------------------------------------------- Gauss-Seidel phase
+template <class T>
+__global__ void __launch_bounds__(128) k_gs(Geo g, OpDev A, int grp, int colour, T inv_diag, T* __restrict__ u,
+                                            const T* __restrict__ rhs) {
+  const int k = blockIdx.z;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ox = c_goff[grp][0], oy = c_goff[grp][1], oz = c_goff[grp][2];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (colour >= 0) i = 4 * i + (((colour - j - k) % 4) + 4) % 4;
+  if (!dof_valid(g, i, j, k, ox, oy, oz) || dof_boundary(g, i, j, k, ox, oy, oz)) return;
+  const int64_t idx = site_index(g, i, j, k);
+  const DRow row = A.rows[grp];          // component-0 row of group grp; comps 1,2 shift by G arrays
+  const int64_t cstride = int64_t(g.G) * g.arr;
+  T a0 = T(0), a1 = T(0), a2 = T(0);
+  for (int t = row.t0 + 1; t < row.t0 + row.n1; ++t) {     // all A terms are in seg 1, diagonal first
+    const DTerm tm = A.terms[t];
+    const T w = wsel<T>(A.w64, A.w32, t);
+    const T* p = u + int64_t(tm.arr) * g.arr + idx + tm.off;
+    a0 += w * p[0];
+    a1 += w * p[cstride];
+    a2 += w * p[2 * cstride];
+  }
+  T einv = T(1);
+  if (g.nu_ah != 0.0) einv = T(exp(-g.nu_ah * k));
+  const int64_t o0 = int64_t(grp) * g.arr + idx;
+  u[o0] = (rhs[o0] * einv - a0) * inv_diag;
+  u[o0 + cstride] = (rhs[o0 + cstride] * einv - a1) * inv_diag;
+  u[o0 + 2 * cstride] = (rhs[o0 + 2 * cstride] * einv - a2) * inv_diag;
+}
+
+// --------------------------------------------------------- pressure update
+template <class T>
+__global__ void k_pupdate(Geo g, T* __restrict__ p, const T* __restrict__ r, const double* __restrict__ inv_ml,
+                          double s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i > g.nx || j > g.ny) return;
+  const int64_t idx = site_index(g, i, j, k);
+  p[idx] -= T(s * inv_ml[idx]) * r[idx];
+}
+
+template <class T>
+__global__ void k_sub_scalar_p(Geo g, T* __restrict__ p, const double* __restrict__ sum, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i > g.nx || j > g.ny) return;
+  p[site_index(g, i, j, k)] -= T(sum[0] * scale);
+}
+
+// ---------------------------------------------------------------- transfers
+template <class T>
+__global__ void __launch_bounds__(128) k_prolong(Geo gf, Geo gc, XferDev X, int base_f, int base_c, int ncomp, int G,
+                                                 int interior_only, const T* __restrict__ xc, T* __restrict__ xf) {
+  const int nzp = gf.nz + 1;
+  const int gfi = blockIdx.z / nzp;
+  const int k = blockIdx.z - gfi * nzp;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ox = G == 1 ? 0 : c_goff[gfi][0], oy = G == 1 ? 0 : c_goff[gfi][1], oz = G == 1 ? 0 : c_goff[gfi][2];
+  if (!dof_valid(gf, i, j, k, ox, oy, oz)) return;
+  if (interior_only && dof_boundary(gf, i, j, k, ox, oy, oz)) return;
+  int ax, ay, az, cls;
+  if (X.order == 2) {
+    const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
+    ax = Px >> 2; ay = Py >> 2; az = Pz >> 2;
+    cls = (Px & 3) + 4 * ((Py & 3) + 4 * (Pz & 3));
+  } else {
+    ax = i >> 1; ay = j >> 1; az = k >> 1;
+    cls = (i & 1) + 2 * ((j & 1) + 2 * (k & 1));
+  }
+  const int64_t cidx = site_index(gc, ax, ay, az);
+  const int64_t fidx = site_index(gf, i, j, k);
+  const int t0 = X.pcls_start[cls], t1 = X.pcls_start[cls + 1];
+  const int64_t cstride_c = int64_t(G) * gc.arr, cstride_f = int64_t(G) * gf.arr;
+  for (int c = 0; c < ncomp; ++c) {
+    T a = T(0);
+    for (int t = t0; t < t1; ++t) {
+      const DXTerm tm = X.pterms[t];
+      const int64_t off = int64_t(tm.di) + int64_t(tm.dj) * gc.sx + int64_t(tm.dk) * gc.sy;
+      a += wsel<T>(X.pw64, X.pw32, t) * xc[int64_t(base_c + tm.arr) * gc.arr + c * cstride_c + cidx + off];
+    }
+    xf[int64_t(base_f + gfi) * gf.arr + c * cstride_f + fidx] += a;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_restrict(Geo gf, Geo gc, XferDev X, int base_f, int base_c, int ncomp, int G,
+                                                  int interior_only, const T* __restrict__ rf, T* __restrict__ rc) {
+  const int nzp = gc.nz + 1;
+  const int gci = blockIdx.z / nzp;
+  const int k = blockIdx.z - gci * nzp;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ox = G == 1 ? 0 : c_goff[gci][0], oy = G == 1 ? 0 : c_goff[gci][1], oz = G == 1 ? 0 : c_goff[gci][2];
+  if (!dof_valid(gc, i, j, k, ox, oy, oz)) return;
+  const int64_t cidx = site_index(gc, i, j, k);
+  const int64_t cstride_c = int64_t(G) * gc.arr, cstride_f = int64_t(G) * gf.arr;
+  if (interior_only && dof_boundary(gc, i, j, k, ox, oy, oz)) {
+    for (int c = 0; c < ncomp; ++c) rc[int64_t(base_c + gci) * gc.arr + c * cstride_c + cidx] = T(0);
+    return;
+  }
+  const int t0 = X.rg_start[gci], t1 = X.rg_start[gci + 1];
+  T a[3] = {T(0), T(0), T(0)};
+  for (int t = t0; t < t1; ++t) {
+    const DXTerm tm = X.rterms[t];
+    const int fi = 2 * i + tm.di, fj = 2 * j + tm.dj, fk = 2 * k + tm.dk;
+    if (fi < -1 || fj < -1 || fk < -1 || fi > gf.nx + 1 || fj > gf.ny + 1 || fk > gf.nz + 1) continue;
+    const T w = wsel<T>(X.rw64, X.rw32, t);
+    const int64_t f = int64_t(base_f + tm.arr) * gf.arr + site_index(gf, fi, fj, fk);
+    for (int c = 0; c < ncomp; ++c) a[c] += w * rf[f + c * cstride_f];
+  }
+  for (int c = 0; c < ncomp; ++c) rc[int64_t(base_c + gci) * gc.arr + c * cstride_c + cidx] = a[c];
+}
+
+// ---------------------------------------------------------------- reductions
+template <class T, int MODE>
+__global__ void __launch_bounds__(256) k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b,
+                                                        const double* __restrict__ w, int64_t n,
+                                                        double* __restrict__ partials) {
+  double s = 0.0;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x) {
+    const double va = double(a[q]);
+    if (MODE == RED_SQ) s += va * va;
+    else if (MODE == RED_DOT) s += va * double(b[q]);
+    else if (MODE == RED_WSUM) s += w[q] * va;
+    else s += va;
+  }
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__ partials, int n,
+                                                      double* __restrict__ out) {
+  double s = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) s += partials[q];
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[0] = s;
+  }
+}
+
+// --------------------------------------------------------------- coarse solve
+template <class T>
+__global__ void __launch_bounds__(128) k_coarse(const double* __restrict__ Z, int n, const int64_t* __restrict__ idx,
+                                                const T* __restrict__ b, T* __restrict__ x) {
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) s += Z[int64_t(r) * n + q] * double(b[idx[q]]);
+  __shared__ double sh[4];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) x[idx[r]] = T(sh[0] + sh[1] + sh[2] + sh[3]);
+}
+
+// ------------------------------------------------------------ element-wise
+__global__ void k_cast_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
+    b[q] = float(a[q]);
+}
+__global__ void k_add_f2d(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
+    b[q] += double(a[q]);
+}
+template <class T>
+__global__ void k_axpy(T alpha, const T* __restrict__ x, T* __restrict__ y, int64_t n) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
+    y[q] += alpha * x[q];
+}
+template <class T>
+__global__ void k_xpby(const T* __restrict__ x, T beta, const T* __restrict__ y, T* __restrict__ z, int64_t n) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
+    z[q] = x[q] + beta * y[q];
+}
+__global__ void k_inv(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
+    b[q] = a[q] != 0.0 ? 1.0 / a[q] : 0.0;
+}
+
+inline int lin_blocks(int64_t n) { return int(std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
+}  // namespace
+
+// ============================================================ host wrappers
+template <class T>
+void launch_apply(const Geo& g, const OpDev& op, int mode, const T* x, const T* b, T* y, double alpha,
+                  cudaStream_t s) {
+  dim3 blk(32, 4, 1);
+  if (op.nrows == 0) return;
+  dim3 grd((g.nx + 1 + 31) / 32, (g.ny + 1 + 3) / 4, (g.nz + 1) * op.nrows);
+  ++g_launches;
+  if (mode == MODE_SET) k_apply<T, MODE_SET><<<grd, blk, 0, s>>>(g, op, x, b, y, T(alpha));
+  else if (mode == MODE_RES) k_apply<T, MODE_RES><<<grd, blk, 0, s>>>(g, op, x, b, y, T(alpha));
+  else k_apply<T, MODE_ADD><<<grd, blk, 0, s>>>(g, op, x, b, y, T(alpha));
+}
+
+template <class T>
+void launch_gs(const Geo& g, const OpDev& A, int grp, int colour, double inv_diag, T* u, const T* rhs,
+               cudaStream_t s) {
+  dim3 blk(32, 4, 1);
+  const int ni = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1;
+  dim3 grd((ni + 31) / 32, (g.ny + 1 + 3) / 4, g.nz + 1);
+  ++g_launches;
+  k_gs<T><<<grd, blk, 0, s>>>(g, A, grp, colour, T(inv_diag), u, rhs);
+}
+
+template <class T>
+void launch_pupdate(const Geo& g, T* p, const T* r, const double* inv_mlhat, double inv_omega_inv, cudaStream_t s) {
+  dim3 blk(32, 4, 1);
+  dim3 grd((g.nx + 1 + 31) / 32, (g.ny + 1 + 3) / 4, g.nz + 1);
+  ++g_launches;
+  k_pupdate<T><<<grd, blk, 0, s>>>(g, p, r, inv_mlhat, inv_omega_inv);
+}
+
+template <class T>
+void launch_sub_scalar_p(const Geo& g, T* p, const double* sum, double scale, cudaStream_t s) {
+  dim3 blk(32, 4, 1);
+  dim3 grd((g.nx + 1 + 31) / 32, (g.ny + 1 + 3) / 4, g.nz + 1);
+  ++g_launches;
+  k_sub_scalar_p<T><<<grd, blk, 0, s>>>(g, p, sum, scale);
+}
+
+template <class T>
+void launch_prolong(const Geo& gf, const Geo& gc, const XferDev& X, int base_f, int base_c, int ncomp, int G,
+                    bool interior_only, const T* xc, T* xf, cudaStream_t s) {
+  dim3 blk(32, 4, 1);
+  dim3 grd((gf.nx + 1 + 31) / 32, (gf.ny + 1 + 3) / 4, (gf.nz + 1) * G);
+  ++g_launches;
+  k_prolong<T><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, interior_only ? 1 : 0, xc, xf);
+}
+
+template <class T>
+void launch_restrict(const Geo& gf, const Geo& gc, const XferDev& X, int base_f, int base_c, int ncomp, int G,
+                     bool interior_only, const T* rf, T* rc, cudaStream_t s) {
+  dim3 blk(32, 4, 1);
+  dim3 grd((gc.nx + 1 + 31) / 32, (gc.ny + 1 + 3) / 4, (gc.nz + 1) * G);
+  ++g_launches;
+  k_restrict<T><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, interior_only ? 1 : 0, rf, rc);
+}
+
+template <class T>
+void launch_reduce(int mode, const T* a, const T* b, const double* w, int64_t n, double* partials, int max_blocks,
+                   double* out, cudaStream_t s) {
+  int nb = int(std::min<int64_t>((n + 255) / 256, max_blocks));
+  if (nb < 1) nb = 1;
+  g_launches += 2;
+  switch (mode) {
+    case RED_SQ: k_reduce_partial<T, RED_SQ><<<nb, 256, 0, s>>>(a, b, w, n, partials); break;
+    case RED_DOT: k_reduce_partial<T, RED_DOT><<<nb, 256, 0, s>>>(a, b, w, n, partials); break;
+    case RED_WSUM: k_reduce_partial<T, RED_WSUM><<<nb, 256, 0, s>>>(a, b, w, n, partials); break;
+    default: k_reduce_partial<T, RED_SUM><<<nb, 256, 0, s>>>(a, b, w, n, partials); break;
+  }
+  k_reduce_final<<<1, 256, 0, s>>>(partials, nb, out);
+}
+
+template <class T>
+void launch_coarse(const double* Z, int n, const int64_t* idx, const T* b, T* x, cudaStream_t s) {
+  ++g_launches;
+  k_coarse<T><<<n, 128, 0, s>>>(Z, n, idx, b, x);
+}
+
+void launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s) {
+  ++g_launches;
+  k_cast_d2f<<<lin_blocks(n), 256, 0, s>>>(a, b, n);
+}
+void launch_add_f2d(const float* a, double* b, int64_t n, cudaStream_t s) {
+  ++g_launches;
+  k_add_f2d<<<lin_blocks(n), 256, 0, s>>>(a, b, n);
+}
+template <class T>
+void launch_axpy(double alpha, const T* x, T* y, int64_t n, cudaStream_t s) {
+  ++g_launches;
+  k_axpy<T><<<lin_blocks(n), 256, 0, s>>>(T(alpha), x, y, n);
+}
+template <class T>
+void launch_xpby(const T* x, double beta, const T* y, T* z, int64_t n, cudaStream_t s) {
+  ++g_launches;
+  k_xpby<T><<<lin_blocks(n), 256, 0, s>>>(x, T(beta), y, z, n);
+}
+void launch_inv(const double* a, double* b, int64_t n, cudaStream_t s) {
+  ++g_launches;
+  k_inv<<<lin_blocks(n), 256, 0, s>>>(a, b, n);
+}
+
+#define HHG_INST(T)                                                                                              \
+  template void launch_apply<T>(const Geo&, const OpDev&, int, const T*, const T*, T*, double, cudaStream_t);     \
+  template void launch_gs<T>(const Geo&, const OpDev&, int, int, double, T*, const T*, cudaStream_t);              \
+  template void launch_pupdate<T>(const Geo&, T*, const T*, const double*, double, cudaStream_t);                 \
+  template void launch_sub_scalar_p<T>(const Geo&, T*, const double*, double, cudaStream_t);                      \
+  template void launch_prolong<T>(const Geo&, const Geo&, const XferDev&, int, int, int, int, bool, const T*, T*, \
+                                  cudaStream_t);                                                                  \
+  template void launch_restrict<T>(const Geo&, const Geo&, const XferDev&, int, int, int, int, bool, const T*,    \
+                                   T*, cudaStream_t);                                                             \
+  template void launch_reduce<T>(int, const T*, const T*, const double*, int64_t, double*, int, double*,          \
+                                 cudaStream_t);                                                                   \
+  template void launch_coarse<T>(const double*, int, const int64_t*, const T*, T*, cudaStream_t);                 \
+  template void launch_axpy<T>(double, const T*, T*, int64_t, cudaStream_t);                                      \
+  template void launch_xpby<T>(const T*, double, const T*, T*, int64_t, cudaStream_t);
+HHG_INST(double)
+HHG_INST(float)
+
+}  // namespace hhg

@@ -1,0 +1,1091 @@
+// C ABI of the HHG Stokes library: meshes, problems, workspace binding and
+// the solver drivers (Algorithm 1) issuing the CUDA kernels of kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+using namespace hhg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define HHG_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail(HHG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define HHG_CHECK_LAUNCH()                                                                      \
+  do {                                                                                          \
+    cudaError_t e_ = cudaGetLastError();                                                        \
+    if (e_ != cudaSuccess) return fail(HHG_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define HHG_TRY(expr)          \
+  do {                         \
+    int rc_ = (expr);          \
+    if (rc_ != HHG_OK) return rc_; \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+struct hhg_mesh {
+  int mx, my, mz;
+  double H;
+};
+
+namespace {
+
+// serialised operator of one level
+struct OpHost {
+  std::vector<DRow> rows;
+  std::vector<DTerm> terms;
+  std::vector<double> w64;
+  std::vector<DTermB> bterms;
+  std::vector<double> bw64;
+};
+
+OpHost serialise(const HOperator& op, const Geo& g) {
+  OpHost o;
+  auto lin = [&](const HTerm& t) { return int(t.di + t.dj * g.sx + t.dk * g.sy); };
+  for (const HRow& r : op.rows) {
+    DRow d{};
+    d.out_arr = r.out_arr; d.og = r.og; d.all_rows = r.all_rows ? 1 : 0;
+    d.t0 = int(o.terms.size());
+    int* ns[3] = {&d.n0, &d.n1, &d.n2};
+    for (int s = 0; s < 3; ++s) {
+      *ns[s] = int(r.seg[s].size());
+      for (const HTerm& t : r.seg[s]) { o.terms.push_back({t.in_arr, lin(t)}); o.w64.push_back(t.w); }
+    }
+    d.b0 = int(o.bterms.size());
+    int* ms[3] = {&d.m0, &d.m1, &d.m2};
+    for (int s = 0; s < 3; ++s) {
+      *ms[s] = int(r.bseg[s].size());
+      for (const HTerm& t : r.bseg[s]) {
+        o.bterms.push_back({t.in_arr, lin(t), t.cx, t.cy, t.cz, 0});
+        o.bw64.push_back(t.w);
+      }
+    }
+    o.rows.push_back(d);
+  }
+  return o;
+}
+
+struct Blob {                      // host staging of a device table region
+  std::vector<char> bytes;
+  template <class T>
+  size_t put(const std::vector<T>& v) {
+    size_t off = align256(bytes.size());
+    bytes.resize(off + std::max<size_t>(v.size() * sizeof(T), 1));
+    if (!v.empty()) std::memcpy(bytes.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+struct OpOffsets {
+  size_t rows, terms, w64, w32, bterms, bw64, bw32;
+  int nrows;
+};
+
+struct XferOffsets {
+  size_t pstart, pterms, pw64, pw32, rstart, rterms, rw64, rw32;
+  int order, nclass, ngroups;
+};
+
+struct Level {
+  int l;
+  Geo g;
+  StencilSet st;
+  OpOffsets opoff[OP_COUNT];
+  OpDev op[OP_COUNT];
+  std::vector<double> inv_diag;         // per group 1/diag(A)
+  // workspace offsets (bytes) of the level vectors
+  size_t o_rhs, o_W, o_x64, o_tmp64, o_bw64, o_x32, o_b32, o_tmp32, o_invml, o_ml;
+  double *rhs = nullptr, *W = nullptr, *x64 = nullptr, *tmp64 = nullptr, *bw64 = nullptr;
+  float *x32 = nullptr, *b32 = nullptr, *tmp32 = nullptr;
+  double *inv_mlhat = nullptr, *ml = nullptr;
+  double ml_sum = 0.0;
+  int64_t nvec() const { return (3 * int64_t(g.G) + 1) * g.arr; }
+  int64_t n_dofs() const;
+  bool has_rhs = false;
+};
+
+}  // namespace
+
+struct hhg_problem {
+  hhg_mesh mesh;
+  hhg_problem_desc desc;
+  int G = 1, ov = 1;
+  std::vector<Level> lv;               // levels lc .. L (+ L+1 if error_level)
+  HTransfer tv, tp;
+  XferOffsets xoff_v, xoff_p;
+  XferDev xv{}, xp{};
+  Blob tables;
+  size_t o_tables = 0, o_Z = 0, o_idx = 0, o_part = 0, o_scal = 0, total = 0;
+  int ncoarse = 0;
+  char* ws = nullptr;
+  double* Z = nullptr;
+  int64_t* cidx = nullptr;
+  double* partials = nullptr;
+  double* scal = nullptr;               // device scalars
+  int max_blocks = 1216;
+  cudaStream_t stream = nullptr;
+  bool bound = false;
+  int64_t launches = 0;
+  double wu_counted = 0.0;
+
+  Level& L(int l) { return lv[l - desc.coarse_level]; }
+  int Lmax() const { return desc.L; }
+};
+
+int64_t Level::n_dofs() const {
+  const int64_t np = int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+  const int64_t nv = g.G == 1 ? np : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
+  return 3 * nv + np;
+}
+
+// ===================================================================== misc
+extern "C" int hhg_last_error(char* buf, size_t len) {
+  if (!buf || len == 0) return HHG_EINVAL;
+  std::snprintf(buf, len, "%s", g_err.c_str());
+  return HHG_OK;
+}
+
+// =================================================================== meshes
+extern "C" int hhg_mesh_create_box(int mx, int my, int mz, double H, hhg_mesh** out) {
+  if (!out || mx < 1 || my < 1 || mz < 1 || !(H > 0)) return fail(HHG_EINVAL, "hhg_mesh_create_box: bad box");
+  *out = new hhg_mesh{mx, my, mz, H};
+  return HHG_OK;
+}
+
+extern "C" int hhg_mesh_create(const double* verts, int nv, const int* tets, int nt, hhg_mesh** out) {
+  if (!verts || !tets || !out || nv < 4 || nt < 1) return fail(HHG_EINVAL, "hhg_mesh_create: bad arguments");
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int v = 0; v < nv; ++v)
+    for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], verts[3 * v + d]); hi[d] = std::max(hi[d], verts[3 * v + d]); }
+  for (int d = 0; d < 3; ++d)
+    if (std::fabs(lo[d]) > 1e-12) return fail(HHG_EINVAL, "hhg_mesh_create: the box must start at the origin");
+  // cube side: smallest positive coordinate step
+  double H = 1e300;
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        for (int d = 0; d < 3; ++d) {
+          int va = tets[4 * t + a], vb = tets[4 * t + b];
+          if (va < 0 || va >= nv || vb < 0 || vb >= nv) return fail(HHG_EINVAL, "hhg_mesh_create: vertex id out of range");
+          double dd = std::fabs(verts[3 * va + d] - verts[3 * vb + d]);
+          if (dd > 1e-12) H = std::min(H, dd);
+        }
+  int m[3];
+  for (int d = 0; d < 3; ++d) {
+    m[d] = int(std::lround(hi[d] / H));
+    if (m[d] < 1 || std::fabs(m[d] * H - hi[d]) > 1e-9 * H) return fail(HHG_EINVAL, "hhg_mesh_create: not a box of cubes");
+  }
+  std::set<std::tuple<int, int, int, int, int, int>> seen;   // cube + path
+  for (int t = 0; t < nt; ++t) {
+    int c[4][3];
+    for (int a = 0; a < 4; ++a)
+      for (int d = 0; d < 3; ++d) {
+        double q = verts[3 * tets[4 * t + a] + d] / H;
+        c[a][d] = int(std::lround(q));
+        if (std::fabs(q - c[a][d]) > 1e-9) return fail(HHG_EINVAL, "hhg_mesh_create: vertex off the cube lattice");
+      }
+    int order[4] = {0, 1, 2, 3};
+    std::sort(order, order + 4, [&](int a, int b) { return c[a][0] + c[a][1] + c[a][2] < c[b][0] + c[b][1] + c[b][2]; });
+    int dir[3];
+    for (int s = 0; s < 3; ++s) {
+      int dif[3], nz = 0, which = -1;
+      for (int d = 0; d < 3; ++d) {
+        dif[d] = c[order[s + 1]][d] - c[order[s]][d];
+        if (dif[d] != 0) { ++nz; which = d; }
+      }
+      if (nz != 1 || dif[which] != 1) return fail(HHG_EINVAL, "hhg_mesh_create: tetrahedron is not a Kuhn simplex");
+      dir[s] = which;
+    }
+    if (dir[0] == dir[1] || dir[1] == dir[2] || dir[0] == dir[2])
+      return fail(HHG_EINVAL, "hhg_mesh_create: tetrahedron is not a Kuhn simplex");
+    const int* o = c[order[0]];
+    if (o[0] < 0 || o[1] < 0 || o[2] < 0 || o[0] >= m[0] || o[1] >= m[1] || o[2] >= m[2])
+      return fail(HHG_EINVAL, "hhg_mesh_create: tetrahedron outside the box");
+    seen.insert({o[0], o[1], o[2], dir[0], dir[1], dir[2]});
+  }
+  if (int64_t(seen.size()) != int64_t(6) * m[0] * m[1] * m[2] || nt != int(seen.size()))
+    return fail(HHG_EINVAL, "hhg_mesh_create: the tetrahedra do not tile the box with 6 Kuhn simplices per cube");
+  *out = new hhg_mesh{m[0], m[1], m[2], H};
+  return HHG_OK;
+}
+
+extern "C" int hhg_mesh_destroy(hhg_mesh* mesh) {
+  delete mesh;
+  return HHG_OK;
+}
+
+// ================================================================= problems
+extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* desc, hhg_problem** out) {
+  if (!mesh || !desc || !out) return fail(HHG_EINVAL, "hhg_problem_create: null argument");
+  if (desc->disc != HHG_P1P1_PSPG && desc->disc != HHG_P2P1_TH) return fail(HHG_EINVAL, "unknown discretisation");
+  if (desc->L < 0 || desc->L > 10 || desc->coarse_level < 0 || desc->coarse_level > desc->L)
+    return fail(HHG_EINVAL, "need 0 <= coarse_level <= L <= 10");
+  if (desc->solve != HHG_SOLVE_FP64 && desc->solve != HHG_SOLVE_MIXED) return fail(HHG_EINVAL, "unknown solve mode");
+  auto pb = std::make_unique<hhg_problem>();
+  pb->mesh = *mesh;
+  pb->desc = *desc;
+  pb->ov = desc->disc == HHG_P1P1_PSPG ? 1 : 2;
+  pb->G = pb->ov == 1 ? 1 : 8;
+  const int top = desc->L + (desc->error_level ? 1 : 0);
+  for (int l = desc->coarse_level; l <= top; ++l) {
+    Level lv;
+    lv.l = l;
+    lv.g = make_geo(mesh->mx, mesh->my, mesh->mz, l, pb->G, mesh->H, desc->nu_a);
+    if (int64_t(lv.g.nz + 1) * 25 > 65535 || lv.g.ny + 1 > 65535 * 4)
+      return fail(HHG_EINVAL, "level too large for the launch geometry");
+    lv.st = build_stencils(desc->disc, lv.g.h, desc->nu_a, desc->pspg_rhs != 0);
+    for (int gg = 0; gg < pb->G; ++gg) lv.inv_diag.push_back(1.0 / lv.st.diagA[gg]);
+    pb->lv.push_back(std::move(lv));
+  }
+  pb->tv = build_transfer(pb->ov);
+  pb->tp = build_transfer(1);
+
+  // ---- device table blob
+  Blob& B = pb->tables;
+  for (Level& lv : pb->lv) {
+    for (int o = 0; o < OP_COUNT; ++o) {
+      OpHost h = serialise(lv.st.op[o], lv.g);
+      std::vector<float> w32(h.w64.begin(), h.w64.end()), bw32(h.bw64.begin(), h.bw64.end());
+      OpOffsets& of = lv.opoff[o];
+      of.nrows = int(h.rows.size());
+      of.rows = B.put(h.rows); of.terms = B.put(h.terms); of.w64 = B.put(h.w64); of.w32 = B.put(w32);
+      of.bterms = B.put(h.bterms); of.bw64 = B.put(h.bw64); of.bw32 = B.put(bw32);
+    }
+  }
+  auto put_x = [&](const HTransfer& X, XferOffsets& xo) {
+    std::vector<int> ps(1, 0), rs(1, 0);
+    std::vector<DXTerm> pt, rt;
+    std::vector<double> pw, rw;
+    for (auto& c : X.prol) {
+      for (auto& t : c) { pt.push_back({t.arr, t.di, t.dj, t.dk}); pw.push_back(t.w); }
+      ps.push_back(int(pt.size()));
+    }
+    for (auto& c : X.restr) {
+      for (auto& t : c) { rt.push_back({t.arr, t.di, t.dj, t.dk}); rw.push_back(t.w); }
+      rs.push_back(int(rt.size()));
+    }
+    std::vector<float> pw32(pw.begin(), pw.end()), rw32(rw.begin(), rw.end());
+    xo.order = X.order; xo.nclass = X.nclass; xo.ngroups = int(X.restr.size());
+    xo.pstart = B.put(ps); xo.pterms = B.put(pt); xo.pw64 = B.put(pw); xo.pw32 = B.put(pw32);
+    xo.rstart = B.put(rs); xo.rterms = B.put(rt); xo.rw64 = B.put(rw); xo.rw32 = B.put(rw32);
+  };
+  put_x(pb->tv, pb->xoff_v);
+  put_x(pb->tp, pb->xoff_p);
+
+  // ---- workspace layout
+  size_t off = 0;
+  pb->o_tables = off;
+  off = align256(off + B.bytes.size());
+  const bool mixed = desc->solve == HHG_SOLVE_MIXED;
+  for (Level& lv : pb->lv) {
+    const size_t v64 = align256(size_t(lv.nvec()) * 8), v32 = align256(size_t(lv.nvec()) * 4);
+    const size_t a64 = align256(size_t(lv.g.arr) * 8);
+    lv.o_rhs = off; off += v64;
+    lv.o_W = off; off += v64;
+    lv.o_x64 = off; off += v64;
+    lv.o_tmp64 = off; off += v64;
+    lv.o_bw64 = off; off += v64;
+    if (mixed) {
+      lv.o_x32 = off; off += v32;
+      lv.o_b32 = off; off += v32;
+      lv.o_tmp32 = off; off += v32;
+    }
+    lv.o_invml = off; off += a64;
+    lv.o_ml = off; off += a64;
+  }
+  // coarse system: interior velocity DoFs of the coarse level + all pressure nodes
+  {
+    const Geo& g = pb->lv[0].g;
+    int n = 0;
+    for (int gg = 0; gg < pb->G; ++gg) {
+      const int* o = kGroupOff[gg];
+      for (int k = 0; k <= g.nz - o[2]; ++k)
+        for (int j = 0; j <= g.ny - o[1]; ++j)
+          for (int i = 0; i <= g.nx - o[0]; ++i) {
+            int P[3] = {2 * i + o[0], 2 * j + o[1], 2 * k + o[2]};
+            bool bnd = P[0] == 0 || P[1] == 0 || P[2] == 0 || P[0] == 2 * g.nx || P[1] == 2 * g.ny || P[2] == 2 * g.nz;
+            if (!bnd) ++n;
+          }
+    }
+    n = 3 * n + (g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+    if (n > 6000) return fail(HHG_EINVAL, "coarse level too large for the dense coarse solve");
+    pb->ncoarse = n;
+  }
+  pb->o_Z = off; off += align256(size_t(pb->ncoarse) * pb->ncoarse * 8);
+  pb->o_idx = off; off += align256(size_t(pb->ncoarse) * 8);
+  pb->o_part = off; off += align256(size_t(pb->max_blocks) * 8);
+  pb->o_scal = off; off += align256(64 * 8);
+  pb->total = off;
+  *out = pb.release();
+  return HHG_OK;
+}
+
+extern "C" int hhg_problem_workspace_bytes(const hhg_problem* pb, size_t* bytes) {
+  if (!pb || !bytes) return fail(HHG_EINVAL, "null argument");
+  *bytes = pb->total;
+  return HHG_OK;
+}
+
+extern "C" int hhg_problem_destroy(hhg_problem* pb) {
+  delete pb;
+  return HHG_OK;
+}
+
+extern "C" int hhg_layout(const hhg_problem* pb, int level, hhg_layout_info* info) {
+  if (!pb || !info) return fail(HHG_EINVAL, "null argument");
+  const int top = pb->desc.L + (pb->desc.error_level ? 1 : 0);
+  if (level < pb->desc.coarse_level || level > top) return fail(HHG_EINVAL, "level out of range");
+  const Level& lv = pb->lv[level - pb->desc.coarse_level];
+  const Geo& g = lv.g;
+  info->level = level;
+  info->nx = g.nx; info->ny = g.ny; info->nz = g.nz;
+  info->groups = g.G;
+  info->sx = g.sx; info->sy = g.sy;
+  info->array_elems = g.arr;
+  info->vector_elems = lv.nvec();
+  info->n_pressure_nodes = int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+  info->n_velocity_nodes = g.G == 1 ? info->n_pressure_nodes : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
+  info->n_dofs = 3 * info->n_velocity_nodes + info->n_pressure_nodes;
+  info->h = g.h;
+  return HHG_OK;
+}
+
+// ------------------------------------------------------- layout conversion
+namespace {
+
+// canonical index -> (array, site) for velocity nodes of level geometry g
+template <class F>
+void for_each_velocity_node(const Geo& g, F f) {
+  if (g.G == 1) {
+    int64_t c = 0;
+    for (int k = 0; k <= g.nz; ++k)
+      for (int j = 0; j <= g.ny; ++j)
+        for (int i = 0; i <= g.nx; ++i, ++c)
+          f(c, 0, int64_t(i + 1) + int64_t(j + 1) * g.sx + int64_t(k + 1) * g.sy, i == 0 || j == 0 || k == 0 || i == g.nx || j == g.ny || k == g.nz);
+  } else {
+    int64_t c = 0;
+    for (int K = 0; K <= 2 * g.nz; ++K)
+      for (int J = 0; J <= 2 * g.ny; ++J)
+        for (int I = 0; I <= 2 * g.nx; ++I, ++c) {
+          int gg = group_of_parity(I & 1, J & 1, K & 1);
+          f(c, gg, int64_t((I >> 1) + 1) + int64_t((J >> 1) + 1) * g.sx + int64_t((K >> 1) + 1) * g.sy,
+            I == 0 || J == 0 || K == 0 || I == 2 * g.nx || J == 2 * g.ny || K == 2 * g.nz);
+        }
+  }
+}
+
+template <class F>
+void for_each_pressure_node(const Geo& g, F f) {
+  int64_t c = 0;
+  for (int k = 0; k <= g.nz; ++k)
+    for (int j = 0; j <= g.ny; ++j)
+      for (int i = 0; i <= g.nx; ++i, ++c) f(c, int64_t(i + 1) + int64_t(j + 1) * g.sx + int64_t(k + 1) * g.sy);
+}
+
+void canonical_to_layout(const Level& lv, const double* host, std::vector<double>& out) {
+  const Geo& g = lv.g;
+  out.assign(size_t(lv.nvec()), 0.0);
+  int64_t nvn = g.G == 1 ? int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1)
+                         : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
+  for (int c = 0; c < 3; ++c)
+    for_each_velocity_node(g, [&](int64_t ci, int gg, int64_t site, bool) {
+      out[size_t((c * g.G + gg) * g.arr + site)] = host[c * nvn + ci];
+    });
+  for_each_pressure_node(g, [&](int64_t ci, int64_t site) { out[size_t(3 * g.G * g.arr + site)] = host[3 * nvn + ci]; });
+}
+
+void layout_to_canonical(const Level& lv, const std::vector<double>& in, double* host) {
+  const Geo& g = lv.g;
+  int64_t nvn = g.G == 1 ? int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1)
+                         : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
+  for (int c = 0; c < 3; ++c)
+    for_each_velocity_node(g, [&](int64_t ci, int gg, int64_t site, bool) {
+      host[c * nvn + ci] = in[size_t((c * g.G + gg) * g.arr + site)];
+    });
+  for_each_pressure_node(g, [&](int64_t ci, int64_t site) { host[3 * nvn + ci] = in[size_t(3 * g.G * g.arr + site)]; });
+}
+
+int upload(hhg_problem* pb, const std::vector<double>& h, int prec, void* dev) {
+  if (prec == HHG_FP64) {
+    HHG_CUDA(cudaMemcpyAsync(dev, h.data(), h.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  } else {
+    std::vector<float> f(h.begin(), h.end());
+    HHG_CUDA(cudaMemcpyAsync(dev, f.data(), f.size() * 4, cudaMemcpyHostToDevice, pb->stream));
+    HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  }
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  return HHG_OK;
+}
+
+int check_level(const hhg_problem* pb, int level, bool allow_error_level = false) {
+  if (!pb) return fail(HHG_EINVAL, "null problem");
+  if (!pb->bound) return fail(HHG_ESTATE, "problem has no workspace bound (call hhg_problem_bind)");
+  const int top = pb->desc.L + ((allow_error_level && pb->desc.error_level) ? 1 : 0);
+  if (level < pb->desc.coarse_level || level > top) return fail(HHG_EINVAL, "level out of range");
+  return HHG_OK;
+}
+
+}  // namespace
+
+extern "C" int hhg_vector_from_host(hhg_problem* pb, int level, int prec, const double* host, void* dev) {
+  HHG_TRY(check_level(pb, level, true));
+  if (!host || !dev) return fail(HHG_EINVAL, "null vector");
+  std::vector<double> h;
+  canonical_to_layout(pb->L(level), host, h);
+  return upload(pb, h, prec, dev);
+}
+
+extern "C" int hhg_vector_to_host(hhg_problem* pb, int level, int prec, const void* dev, double* host) {
+  HHG_TRY(check_level(pb, level, true));
+  if (!host || !dev) return fail(HHG_EINVAL, "null vector");
+  const Level& lv = pb->L(level);
+  std::vector<double> h(size_t(lv.nvec()));
+  if (prec == HHG_FP64) {
+    HHG_CUDA(cudaMemcpyAsync(h.data(), dev, h.size() * 8, cudaMemcpyDeviceToHost, pb->stream));
+    HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  } else {
+    std::vector<float> f(h.size());
+    HHG_CUDA(cudaMemcpyAsync(f.data(), dev, f.size() * 4, cudaMemcpyDeviceToHost, pb->stream));
+    HHG_CUDA(cudaStreamSynchronize(pb->stream));
+    std::copy(f.begin(), f.end(), h.begin());
+  }
+  layout_to_canonical(lv, h, host);
+  return HHG_OK;
+}
+
+// ============================================================ solver steps
+namespace {
+
+template <class T> T* vx(Level& lv);
+template <> double* vx<double>(Level& lv) { return lv.x64; }
+template <> float* vx<float>(Level& lv) { return lv.x32; }
+template <class T> T* vb(Level& lv);
+template <> double* vb<double>(Level& lv) { return lv.bw64; }
+template <> float* vb<float>(Level& lv) { return lv.b32; }
+template <class T> T* vt(Level& lv);
+template <> double* vt<double>(Level& lv) { return lv.tmp64; }
+template <> float* vt<float>(Level& lv) { return lv.tmp32; }
+
+int64_t p_offset(const Level& lv) { return 3 * int64_t(lv.g.G) * lv.g.arr; }
+
+// relative cost of one block application (paper's normalisation, Sec. 4.2)
+struct Costs { double A, B, C; };
+Costs block_costs(int ov) {
+  if (ov == 2) return {46.0 / 72, 13.0 / 72, 0.0};
+  return {0.3, 0.3, 0.1};
+}
+
+template <class T>
+int apply_op(hhg_problem* pb, Level& lv, int op, int mode, const T* x, const T* b, T* y, double alpha = 1.0) {
+  launch_apply<T>(lv.g, lv.op[op], mode, x, b, y, alpha, pb->stream);
+  HHG_CHECK_LAUNCH();
+  return HHG_OK;
+}
+
+double level_weight(hhg_problem* pb, const Level& lv) {
+  return double(lv.n_dofs()) / double(pb->L(pb->desc.L).n_dofs());
+}
+
+template <class T>
+int uzawa(hhg_problem* pb, Level& lv, const hhg_params& prm, int sweeps, T* x, const T* b, T* tmp) {
+  const int G = lv.g.G;
+  std::vector<std::pair<int, int>> phases;
+  for (int c = 0; c < 4; ++c) phases.push_back({0, c});
+  for (int gg = 1; gg < G; ++gg) phases.push_back({gg, -1});
+  const Costs cs = block_costs(pb->ov);
+  for (int it = 0; it < sweeps; ++it) {
+    // velocity step (Eq. uzawa-velocity): f' = f - B^T p_k, xi GS sweeps on A u = f'
+    HHG_TRY(apply_op<T>(pb, lv, OP_BT, MODE_RES, x, b, tmp));
+    for (int s = 0; s < prm.xi; ++s) {
+      for (auto& ph : phases) launch_gs<T>(lv.g, lv.op[OP_A], ph.first, ph.second, lv.inv_diag[ph.first], x, tmp, pb->stream);
+      if (prm.ahat == HHG_AHAT_S)
+        for (auto it2 = phases.rbegin(); it2 != phases.rend(); ++it2)
+          launch_gs<T>(lv.g, lv.op[OP_A], it2->first, it2->second, lv.inv_diag[it2->first], x, tmp, pb->stream);
+    }
+    HHG_CHECK_LAUNCH();
+    // pressure step (Eq. uzawa-pressure): p -= S_hat^{-1} (g - B u_{k+1} + C p_k)
+    HHG_TRY(apply_op<T>(pb, lv, OP_BC, MODE_RES, x, b, tmp));
+    const int64_t po = p_offset(lv);
+    launch_pupdate<T>(lv.g, x + po, tmp + po, lv.inv_mlhat, 1.0 / prm.omega_inv, pb->stream);
+    HHG_CHECK_LAUNCH();
+    pb->wu_counted += level_weight(pb, lv) * (prm.xi * (prm.ahat == HHG_AHAT_S ? 2 : 1) * cs.A + 2 * cs.B + cs.C);
+  }
+  return HHG_OK;
+}
+
+template <class T>
+int restrict_to(hhg_problem* pb, int l, const T* rf, T* rc) {
+  Level& f = pb->L(l);
+  Level& c = pb->L(l - 1);
+  launch_restrict<T>(f.g, c.g, pb->xv, 0, 0, 3, pb->G, true, rf, rc, pb->stream);
+  launch_restrict<T>(f.g, c.g, pb->xp, 3 * pb->G, 3 * pb->G, 1, 1, false, rf, rc, pb->stream);
+  HHG_CHECK_LAUNCH();
+  return HHG_OK;
+}
+
+template <class T>
+int prolong_add(hhg_problem* pb, int l, const T* xc, T* xf, bool velocity_interior_only = true) {
+  Level& f = pb->L(l);
+  Level& c = pb->L(l - 1);
+  launch_prolong<T>(f.g, c.g, pb->xv, 0, 0, 3, pb->G, velocity_interior_only, xc, xf, pb->stream);
+  launch_prolong<T>(f.g, c.g, pb->xp, 3 * pb->G, 3 * pb->G, 1, 1, false, xc, xf, pb->stream);
+  HHG_CHECK_LAUNCH();
+  return HHG_OK;
+}
+
+template <class T>
+int coarse_solve(hhg_problem* pb, const T* b, T* x) {
+  Level& lv = pb->lv[0];
+  HHG_CUDA(cudaMemsetAsync(x, 0, size_t(lv.nvec()) * sizeof(T), pb->stream));
+  launch_coarse<T>(pb->Z, pb->ncoarse, pb->cidx, b, x, pb->stream);
+  HHG_CHECK_LAUNCH();
+  return HHG_OK;
+}
+
+template <class T>
+int residual(hhg_problem* pb, Level& lv, const T* x, const T* b, T* r) {
+  HHG_TRY(apply_op<T>(pb, lv, OP_FULL, MODE_RES, x, b, r));
+  pb->wu_counted += level_weight(pb, lv);
+  return HHG_OK;
+}
+
+// VAR-V-CYCLE(l_fine, l, ...) of Algorithm 1
+template <class T>
+int vcycle(hhg_problem* pb, int lf, int l, const hhg_params& prm, T* x, const T* b) {
+  if (l == pb->desc.coarse_level) return coarse_solve<T>(pb, b, x);
+  Level& lv = pb->L(l);
+  Level& lc = pb->L(l - 1);
+  const int extra = (lf - l) * prm.nu_inc;
+  HHG_TRY(uzawa<T>(pb, lv, prm, prm.nu_pre + extra, x, b, vt<T>(lv)));
+  HHG_TRY(residual<T>(pb, lv, x, b, vt<T>(lv)));
+  HHG_TRY(restrict_to<T>(pb, l, vt<T>(lv), vb<T>(lc)));
+  // the coarse correction starts from a zero guess (Algorithm 1)
+  if (l - 1 > pb->desc.coarse_level)
+    HHG_CUDA(cudaMemsetAsync(vx<T>(lc), 0, size_t(lc.nvec()) * sizeof(T), pb->stream));
+  HHG_TRY(vcycle<T>(pb, lf, l - 1, prm, vx<T>(lc), vb<T>(lc)));
+  HHG_TRY(prolong_add<T>(pb, l, vx<T>(lc), x));
+  HHG_TRY(uzawa<T>(pb, lv, prm, prm.nu_post + extra, x, b, vt<T>(lv)));
+  return HHG_OK;
+}
+
+// p <- p - (1^T M_L p / 1^T M_L 1) 1
+int project_pressure(hhg_problem* pb, Level& lv, double* x) {
+  const int64_t po = p_offset(lv);
+  launch_reduce<double>(RED_WSUM, x + po, nullptr, lv.ml, lv.g.arr, pb->partials, pb->max_blocks, pb->scal, pb->stream);
+  launch_sub_scalar_p<double>(lv.g, x + po, pb->scal, 1.0 / lv.ml_sum, pb->stream);
+  HHG_CHECK_LAUNCH();
+  return HHG_OK;
+}
+
+int fmg_interpolate(hhg_problem* pb, int l) {
+  Level& f = pb->L(l);
+  Level& c = pb->L(l - 1);
+  launch_xpby<double>(c.x64, 1.0, c.W, c.tmp64, c.nvec(), pb->stream);
+  HHG_CUDA(cudaMemsetAsync(f.x64, 0, size_t(f.nvec()) * 8, pb->stream));
+  HHG_TRY(prolong_add<double>(pb, l, c.tmp64, f.x64, true));
+  return HHG_OK;
+}
+
+int norms_of(hhg_problem* pb, Level& lv, int prec, const void* r, double* out2) {
+  const int64_t po = p_offset(lv);
+  if (prec == HHG_FP64) {
+    const double* rr = static_cast<const double*>(r);
+    launch_reduce<double>(RED_SQ, rr, nullptr, nullptr, po, pb->partials, pb->max_blocks, pb->scal + 1, pb->stream);
+    launch_reduce<double>(RED_SQ, rr + po, nullptr, nullptr, lv.g.arr, pb->partials, pb->max_blocks, pb->scal + 2, pb->stream);
+  } else {
+    const float* rr = static_cast<const float*>(r);
+    launch_reduce<float>(RED_SQ, rr, nullptr, nullptr, po, pb->partials, pb->max_blocks, pb->scal + 1, pb->stream);
+    launch_reduce<float>(RED_SQ, rr + po, nullptr, nullptr, lv.g.arr, pb->partials, pb->max_blocks, pb->scal + 2, pb->stream);
+  }
+  HHG_CHECK_LAUNCH();
+  double h[2];
+  HHG_CUDA(cudaMemcpyAsync(h, pb->scal + 1, 16, cudaMemcpyDeviceToHost, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  out2[0] = std::sqrt(h[0]);
+  out2[1] = std::sqrt(h[1]);
+  return HHG_OK;
+}
+
+// dense LU with partial pivoting; returns the inverse of A (n x n, row-major)
+bool invert(std::vector<double>& A, int n, std::vector<double>& inv) {
+  std::vector<int> piv(n);
+  for (int i = 0; i < n; ++i) piv[i] = i;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double mx = std::fabs(A[size_t(k) * n + k]);
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[size_t(i) * n + k]) > mx) { mx = std::fabs(A[size_t(i) * n + k]); p = i; }
+    if (mx == 0.0) return false;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[size_t(k) * n + j], A[size_t(p) * n + j]);
+      std::swap(piv[k], piv[p]);
+    }
+    const double d = A[size_t(k) * n + k];
+    for (int i = k + 1; i < n; ++i) {
+      double f = A[size_t(i) * n + k] / d;
+      A[size_t(i) * n + k] = f;
+      if (f != 0.0)
+        for (int j = k + 1; j < n; ++j) A[size_t(i) * n + j] -= f * A[size_t(k) * n + j];
+    }
+  }
+  inv.assign(size_t(n) * n, 0.0);
+  std::vector<double> col(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) col[i] = piv[i] == c ? 1.0 : 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j) col[i] -= A[size_t(i) * n + j] * col[j];
+    for (int i = n - 1; i >= 0; --i) {
+      for (int j = i + 1; j < n; ++j) col[i] -= A[size_t(i) * n + j] * col[j];
+      col[i] /= A[size_t(i) * n + i];
+    }
+    for (int i = 0; i < n; ++i) inv[size_t(i) * n + c] = col[i];
+  }
+  return true;
+}
+
+int build_coarse(hhg_problem* pb) {
+  Level& lv = pb->lv[0];
+  const Geo& g = lv.g;
+  std::vector<int64_t> idx;
+  for (int c = 0; c < 3; ++c)
+    for (int gg = 0; gg < pb->G; ++gg) {
+      const int* o = kGroupOff[gg];
+      for (int k = 0; k <= g.nz - o[2]; ++k)
+        for (int j = 0; j <= g.ny - o[1]; ++j)
+          for (int i = 0; i <= g.nx - o[0]; ++i) {
+            int P[3] = {2 * i + o[0], 2 * j + o[1], 2 * k + o[2]};
+            bool bnd = P[0] == 0 || P[1] == 0 || P[2] == 0 || P[0] == 2 * g.nx || P[1] == 2 * g.ny || P[2] == 2 * g.nz;
+            if (!bnd) idx.push_back(int64_t(c * pb->G + gg) * g.arr + int64_t(i + 1) + int64_t(j + 1) * g.sx + int64_t(k + 1) * g.sy);
+          }
+    }
+  const int nu = int(idx.size());
+  for (int k = 0; k <= g.nz; ++k)
+    for (int j = 0; j <= g.ny; ++j)
+      for (int i = 0; i <= g.nx; ++i)
+        idx.push_back(p_offset(lv) + int64_t(i + 1) + int64_t(j + 1) * g.sx + int64_t(k + 1) * g.sy);
+  const int n = int(idx.size());
+  if (n != pb->ncoarse) return fail(HHG_EINVAL, "internal: coarse size mismatch");
+  std::vector<double> host(size_t(lv.nvec()));
+  std::vector<double> K(size_t(n + 1) * (n + 1), 0.0);
+  const double one = 1.0;
+  for (int jc = 0; jc < n; ++jc) {
+    HHG_CUDA(cudaMemsetAsync(lv.tmp64, 0, size_t(lv.nvec()) * 8, pb->stream));
+    HHG_CUDA(cudaMemcpyAsync(lv.tmp64 + idx[jc], &one, 8, cudaMemcpyHostToDevice, pb->stream));
+    HHG_TRY(apply_op<double>(pb, lv, OP_FULL, MODE_SET, lv.tmp64, nullptr, lv.bw64));
+    HHG_CUDA(cudaMemcpyAsync(host.data(), lv.bw64, host.size() * 8, cudaMemcpyDeviceToHost, pb->stream));
+    HHG_CUDA(cudaStreamSynchronize(pb->stream));
+    for (int r = 0; r < n; ++r) K[size_t(r) * (n + 1) + jc] = host[size_t(idx[r])];
+  }
+  // border with the lumped pressure mass (mean-zero constraint)
+  std::vector<double> ml(size_t(g.arr));
+  HHG_CUDA(cudaMemcpyAsync(ml.data(), lv.ml, ml.size() * 8, cudaMemcpyDeviceToHost, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  for (int r = nu; r < n; ++r) {
+    const double m = ml[size_t(idx[r] - p_offset(lv))];
+    K[size_t(r) * (n + 1) + n] = m;
+    K[size_t(n) * (n + 1) + r] = m;
+  }
+  std::vector<double> inv;
+  if (!invert(K, n + 1, inv)) return fail(HHG_EINVAL, "coarse system is singular (choose a finer coarse level)");
+  std::vector<double> Z(size_t(n) * n);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) Z[size_t(r) * n + c] = inv[size_t(r) * (n + 1) + c];
+  HHG_CUDA(cudaMemcpyAsync(pb->Z, Z.data(), Z.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  HHG_CUDA(cudaMemcpyAsync(pb->cidx, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  return HHG_OK;
+}
+
+}  // namespace
+
+extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, void* stream) {
+  if (!pb || !workspace) return fail(HHG_EINVAL, "null argument");
+  if (bytes < pb->total) return fail(HHG_ENOMEM, "workspace smaller than hhg_problem_workspace_bytes");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(HHG_EINVAL, "workspace must be 256-byte aligned");
+  pb->ws = static_cast<char*>(workspace);
+  pb->stream = static_cast<cudaStream_t>(stream);
+  char* ws = pb->ws;
+  // tables
+  HHG_CUDA(cudaMemcpyAsync(ws + pb->o_tables, pb->tables.bytes.data(), pb->tables.bytes.size(), cudaMemcpyHostToDevice,
+                           pb->stream));
+  char* tb = ws + pb->o_tables;
+  for (Level& lv : pb->lv) {
+    for (int o = 0; o < OP_COUNT; ++o) {
+      const OpOffsets& of = lv.opoff[o];
+      OpDev& d = lv.op[o];
+      d.rows = reinterpret_cast<const DRow*>(tb + of.rows);
+      d.nrows = of.nrows;
+      d.terms = reinterpret_cast<const DTerm*>(tb + of.terms);
+      d.w64 = reinterpret_cast<const double*>(tb + of.w64);
+      d.w32 = reinterpret_cast<const float*>(tb + of.w32);
+      d.bterms = reinterpret_cast<const DTermB*>(tb + of.bterms);
+      d.bw64 = reinterpret_cast<const double*>(tb + of.bw64);
+      d.bw32 = reinterpret_cast<const float*>(tb + of.bw32);
+    }
+    lv.rhs = reinterpret_cast<double*>(ws + lv.o_rhs);
+    lv.W = reinterpret_cast<double*>(ws + lv.o_W);
+    lv.x64 = reinterpret_cast<double*>(ws + lv.o_x64);
+    lv.tmp64 = reinterpret_cast<double*>(ws + lv.o_tmp64);
+    lv.bw64 = reinterpret_cast<double*>(ws + lv.o_bw64);
+    if (pb->desc.solve == HHG_SOLVE_MIXED) {
+      lv.x32 = reinterpret_cast<float*>(ws + lv.o_x32);
+      lv.b32 = reinterpret_cast<float*>(ws + lv.o_b32);
+      lv.tmp32 = reinterpret_cast<float*>(ws + lv.o_tmp32);
+    }
+    lv.inv_mlhat = reinterpret_cast<double*>(ws + lv.o_invml);
+    lv.ml = reinterpret_cast<double*>(ws + lv.o_ml);
+  }
+  auto xdev = [&](const XferOffsets& xo) {
+    XferDev X;
+    X.order = xo.order; X.nclass = xo.nclass; X.ngroups = xo.ngroups;
+    X.pcls_start = reinterpret_cast<const int*>(tb + xo.pstart);
+    X.pterms = reinterpret_cast<const DXTerm*>(tb + xo.pterms);
+    X.pw64 = reinterpret_cast<const double*>(tb + xo.pw64);
+    X.pw32 = reinterpret_cast<const float*>(tb + xo.pw32);
+    X.rg_start = reinterpret_cast<const int*>(tb + xo.rstart);
+    X.rterms = reinterpret_cast<const DXTerm*>(tb + xo.rterms);
+    X.rw64 = reinterpret_cast<const double*>(tb + xo.rw64);
+    X.rw32 = reinterpret_cast<const float*>(tb + xo.rw32);
+    return X;
+  };
+  pb->xv = xdev(pb->xoff_v);
+  pb->xp = xdev(pb->xoff_p);
+  pb->Z = reinterpret_cast<double*>(ws + pb->o_Z);
+  pb->cidx = reinterpret_cast<int64_t*>(ws + pb->o_idx);
+  pb->partials = reinterpret_cast<double*>(ws + pb->o_part);
+  pb->scal = reinterpret_cast<double*>(ws + pb->o_scal);
+  // zero all vectors (halo and padding stay zero for the lifetime of the problem)
+  HHG_CUDA(cudaMemsetAsync(ws + pb->lv[0].o_rhs, 0, pb->o_Z - pb->lv[0].o_rhs, pb->stream));
+  pb->bound = true;
+  // lumped masses: M_L 1 (projection weights) and M_L(1/nu) (S_hat)
+  for (Level& lv : pb->lv) {
+    const int64_t po = p_offset(lv);
+    // ones on all pressure nodes (in tmp64)
+    std::vector<double> ones(size_t(lv.nvec()), 0.0);
+    for_each_pressure_node(lv.g, [&](int64_t, int64_t site) { ones[size_t(po + site)] = 1.0; });
+    HHG_CUDA(cudaMemcpyAsync(lv.tmp64, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+    HHG_TRY(apply_op<double>(pb, lv, OP_ML, MODE_SET, lv.tmp64, nullptr, lv.bw64));
+    HHG_CUDA(cudaMemcpyAsync(lv.ml, lv.bw64 + po, size_t(lv.g.arr) * 8, cudaMemcpyDeviceToDevice, pb->stream));
+    HHG_TRY(apply_op<double>(pb, lv, OP_MLHAT, MODE_SET, lv.tmp64, nullptr, lv.bw64));
+    launch_inv(lv.bw64 + po, lv.inv_mlhat, lv.g.arr, pb->stream);
+    launch_reduce<double>(RED_SUM, lv.ml, nullptr, nullptr, lv.g.arr, pb->partials, pb->max_blocks, pb->scal, pb->stream);
+    HHG_CHECK_LAUNCH();
+    HHG_CUDA(cudaMemcpyAsync(&lv.ml_sum, pb->scal, 8, cudaMemcpyDeviceToHost, pb->stream));
+    HHG_CUDA(cudaStreamSynchronize(pb->stream));
+    HHG_CUDA(cudaMemsetAsync(lv.tmp64, 0, size_t(lv.nvec()) * 8, pb->stream));
+    HHG_CUDA(cudaMemsetAsync(lv.bw64, 0, size_t(lv.nvec()) * 8, pb->stream));
+  }
+  HHG_TRY(build_coarse(pb));
+  Level& c = pb->lv[0];
+  HHG_CUDA(cudaMemsetAsync(c.tmp64, 0, size_t(c.nvec()) * 8, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(c.bw64, 0, size_t(c.nvec()) * 8, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  return HHG_OK;
+}
+
+// ------------------------------------------------------------------- rhs
+extern "C" int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal) {
+  HHG_TRY(check_level(pb, level));
+  if (!f_nodal || !w_nodal) return fail(HHG_EINVAL, "null nodal data");
+  Level& lv = pb->L(level);
+  const Geo& g = lv.g;
+  const int64_t nvn = g.G == 1 ? int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1)
+                               : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
+  std::vector<double> F(size_t(lv.nvec()), 0.0), W(size_t(lv.nvec()), 0.0);
+  for (int c = 0; c < 3; ++c)
+    for_each_velocity_node(g, [&](int64_t ci, int gg, int64_t site, bool bnd) {
+      F[size_t((c * g.G + gg) * g.arr + site)] = f_nodal[c * nvn + ci];
+      if (bnd) W[size_t((c * g.G + gg) * g.arr + site)] = w_nodal[c * nvn + ci];
+    });
+  HHG_CUDA(cudaMemcpyAsync(lv.tmp64, F.data(), F.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  HHG_CUDA(cudaMemcpyAsync(lv.W, W.data(), W.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(lv.rhs, 0, size_t(lv.nvec()) * 8, pb->stream));
+  // f = M f_h - A w_h (interior velocity rows)
+  HHG_TRY(apply_op<double>(pb, lv, OP_MVINT, MODE_SET, lv.tmp64, nullptr, lv.rhs));
+  HHG_TRY(apply_op<double>(pb, lv, OP_A, MODE_ADD, lv.W, nullptr, lv.rhs, -1.0));
+  // g = -B w_h (+ PSPG load), projected to sum zero
+  HHG_TRY(apply_op<double>(pb, lv, OP_B, MODE_ADD, lv.W, nullptr, lv.rhs, -1.0));
+  if (pb->ov == 1 && pb->desc.pspg_rhs) HHG_TRY(apply_op<double>(pb, lv, OP_LOAD, MODE_ADD, lv.tmp64, nullptr, lv.rhs, 1.0));
+  const int64_t po = p_offset(lv);
+  launch_reduce<double>(RED_SUM, lv.rhs + po, nullptr, nullptr, g.arr, pb->partials, pb->max_blocks, pb->scal, pb->stream);
+  launch_sub_scalar_p<double>(g, lv.rhs + po, pb->scal, 1.0 / double((g.nx + 1) * int64_t(g.ny + 1) * (g.nz + 1)), pb->stream);
+  HHG_CHECK_LAUNCH();
+  HHG_CUDA(cudaMemsetAsync(lv.tmp64, 0, size_t(lv.nvec()) * 8, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  lv.has_rhs = true;
+  return HHG_OK;
+}
+
+extern "C" int hhg_level_vector(hhg_problem* pb, int level, int which, void** dev) {
+  HHG_TRY(check_level(pb, level));
+  if (!dev) return fail(HHG_EINVAL, "null output");
+  Level& lv = pb->L(level);
+  if (which == 0) *dev = lv.rhs;
+  else if (which == 1) *dev = lv.W;
+  else if (which == 2) *dev = lv.x64;
+  else return fail(HHG_EINVAL, "unknown level vector");
+  return HHG_OK;
+}
+
+// ---------------------------------------------------------- public steps
+namespace {
+int check_params(const hhg_params* prm) {
+  if (!prm) return fail(HHG_EINVAL, "null params");
+  if (prm->nu_pre < 0 || prm->nu_post < 0 || prm->nu_inc < 0 || prm->kappa < 1 || prm->xi < 1 ||
+      (prm->ahat != HHG_AHAT_F && prm->ahat != HHG_AHAT_S) || !(prm->omega_inv > 0))
+    return fail(HHG_EINVAL, "invalid FMG parameters");
+  return HHG_OK;
+}
+int check_prec(const hhg_problem* pb, int prec) {
+  if (prec == HHG_FP64) return HHG_OK;
+  if (prec == HHG_FP32 && pb->desc.solve == HHG_SOLVE_MIXED) return HHG_OK;
+  return fail(HHG_EINVAL, "FP32 operations need a problem created with HHG_SOLVE_MIXED");
+}
+}  // namespace
+
+extern "C" int hhg_apply(hhg_problem* pb, int level, int op, int prec, const void* x, void* y) {
+  HHG_TRY(check_level(pb, level, op == HHG_OP_MASS));
+  HHG_TRY(check_prec(pb, prec));
+  if (!x || !y) return fail(HHG_EINVAL, "null vector");
+  int id;
+  switch (op) {
+    case HHG_OP_FULL: id = OP_FULL; break;
+    case HHG_OP_A: id = OP_A; break;
+    case HHG_OP_BT: id = OP_BT; break;
+    case HHG_OP_B: id = OP_B; break;
+    case HHG_OP_C: id = OP_C; break;
+    case HHG_OP_MASS: id = OP_MASS; break;
+    default: return fail(HHG_EINVAL, "unknown operator");
+  }
+  Level& lv = pb->L(level);
+  const size_t es = prec == HHG_FP64 ? 8 : 4;
+  if (id != OP_FULL && id != OP_MASS) HHG_CUDA(cudaMemsetAsync(y, 0, size_t(lv.nvec()) * es, pb->stream));
+  if (id == OP_C && pb->ov == 2) return HHG_OK;              // C = 0 for Taylor-Hood
+  if (prec == HHG_FP64)
+    return apply_op<double>(pb, lv, id, MODE_SET, static_cast<const double*>(x), nullptr, static_cast<double*>(y));
+  return apply_op<float>(pb, lv, id, MODE_SET, static_cast<const float*>(x), nullptr, static_cast<float*>(y));
+}
+
+extern "C" int hhg_residual(hhg_problem* pb, int level, int prec, const void* x, const void* b, void* r, double* norms) {
+  HHG_TRY(check_level(pb, level));
+  HHG_TRY(check_prec(pb, prec));
+  if (!x || !b || !r) return fail(HHG_EINVAL, "null vector");
+  Level& lv = pb->L(level);
+  if (prec == HHG_FP64)
+    HHG_TRY(residual<double>(pb, lv, static_cast<const double*>(x), static_cast<const double*>(b), static_cast<double*>(r)));
+  else
+    HHG_TRY(residual<float>(pb, lv, static_cast<const float*>(x), static_cast<const float*>(b), static_cast<float*>(r)));
+  if (norms) HHG_TRY(norms_of(pb, lv, prec, r, norms));
+  return HHG_OK;
+}
+
+extern "C" int hhg_smooth(hhg_problem* pb, int level, const hhg_params* prm, int sweeps, int prec, void* x, const void* b) {
+  HHG_TRY(check_level(pb, level));
+  HHG_TRY(check_params(prm));
+  HHG_TRY(check_prec(pb, prec));
+  if (!x || !b || sweeps < 0) return fail(HHG_EINVAL, "bad smoother arguments");
+  Level& lv = pb->L(level);
+  if (prec == HHG_FP64)
+    return uzawa<double>(pb, lv, *prm, sweeps, static_cast<double*>(x), static_cast<const double*>(b), lv.tmp64);
+  return uzawa<float>(pb, lv, *prm, sweeps, static_cast<float*>(x), static_cast<const float*>(b), lv.tmp32);
+}
+
+extern "C" int hhg_restrict(hhg_problem* pb, int level, int prec, const void* r_fine, void* r_coarse) {
+  HHG_TRY(check_level(pb, level));
+  HHG_TRY(check_prec(pb, prec));
+  if (level <= pb->desc.coarse_level) return fail(HHG_EINVAL, "no coarser level");
+  if (!r_fine || !r_coarse) return fail(HHG_EINVAL, "null vector");
+  if (prec == HHG_FP64) return restrict_to<double>(pb, level, static_cast<const double*>(r_fine), static_cast<double*>(r_coarse));
+  return restrict_to<float>(pb, level, static_cast<const float*>(r_fine), static_cast<float*>(r_coarse));
+}
+
+extern "C" int hhg_prolongate_add(hhg_problem* pb, int level, int prec, const void* x_coarse, void* x_fine) {
+  HHG_TRY(check_level(pb, level));
+  HHG_TRY(check_prec(pb, prec));
+  if (level <= pb->desc.coarse_level) return fail(HHG_EINVAL, "no coarser level");
+  if (!x_coarse || !x_fine) return fail(HHG_EINVAL, "null vector");
+  if (prec == HHG_FP64) return prolong_add<double>(pb, level, static_cast<const double*>(x_coarse), static_cast<double*>(x_fine));
+  return prolong_add<float>(pb, level, static_cast<const float*>(x_coarse), static_cast<float*>(x_fine));
+}
+
+extern "C" int hhg_coarse_solve(hhg_problem* pb, int prec, const void* b, void* x) {
+  HHG_TRY(check_level(pb, pb ? pb->desc.coarse_level : 0));
+  HHG_TRY(check_prec(pb, prec));
+  if (!b || !x) return fail(HHG_EINVAL, "null vector");
+  if (prec == HHG_FP64) return coarse_solve<double>(pb, static_cast<const double*>(b), static_cast<double*>(x));
+  return coarse_solve<float>(pb, static_cast<const float*>(b), static_cast<float*>(x));
+}
+
+extern "C" int hhg_vcycle(hhg_problem* pb, int level, const hhg_params* prm, int prec, void* x, const void* b) {
+  HHG_TRY(check_level(pb, level));
+  HHG_TRY(check_params(prm));
+  HHG_TRY(check_prec(pb, prec));
+  if (!x || !b) return fail(HHG_EINVAL, "null vector");
+  if (prec == HHG_FP64) return vcycle<double>(pb, level, level, *prm, static_cast<double*>(x), static_cast<const double*>(b));
+  return vcycle<float>(pb, level, level, *prm, static_cast<float*>(x), static_cast<const float*>(b));
+}
+
+namespace {
+double model_wu(const hhg_problem* pb, const hhg_params& p) {
+  const Costs c = block_costs(pb->ov);
+  const double wa = p.ahat == HHG_AHAT_S ? 2 * c.A : c.A;
+  const double wp = p.xi * wa + 2 * c.B + c.C;
+  const double wv = (p.nu_pre + p.nu_post) * wp + 1.0;
+  return 8.0 * p.kappa / 7.0 * (8.0 / 7.0 * wv + 16.0 / 49.0 * p.nu_inc * wp);
+}
+}  // namespace
+
+extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats* stats) {
+  HHG_TRY(check_level(pb, pb ? pb->desc.L : 0));
+  HHG_TRY(check_params(prm));
+  for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l)
+    if (!pb->L(l).has_rhs) return fail(HHG_ESTATE, "hhg_set_rhs missing on a level");
+  const int64_t launches0 = g_launches;
+  pb->wu_counted = 0.0;
+  const int lc = pb->desc.coarse_level;
+  Level& c = pb->L(lc);
+  HHG_TRY(coarse_solve<double>(pb, c.rhs, c.x64));
+  HHG_TRY(project_pressure(pb, c, c.x64));
+  for (int l = lc + 1; l <= pb->desc.L; ++l) {
+    Level& lv = pb->L(l);
+    HHG_TRY(fmg_interpolate(pb, l));
+    for (int kk = 0; kk < prm->kappa; ++kk) {
+      if (pb->desc.solve == HHG_SOLVE_FP64) {
+        HHG_TRY(vcycle<double>(pb, l, l, *prm, lv.x64, lv.rhs));
+      } else {
+        // iterative refinement: FP64 residual, FP32 V-cycle on the defect, FP64 update
+        HHG_TRY(residual<double>(pb, lv, lv.x64, lv.rhs, lv.tmp64));
+        launch_cast_d2f(lv.tmp64, lv.b32, lv.nvec(), pb->stream);
+        HHG_CUDA(cudaMemsetAsync(lv.x32, 0, size_t(lv.nvec()) * 4, pb->stream));
+        HHG_TRY(vcycle<float>(pb, l, l, *prm, lv.x32, lv.b32));
+        launch_add_f2d(lv.x32, lv.x64, lv.nvec(), pb->stream);
+        HHG_CHECK_LAUNCH();
+      }
+      HHG_TRY(project_pressure(pb, lv, lv.x64));
+    }
+  }
+  Level& top = pb->L(pb->desc.L);
+  if (x_out) HHG_CUDA(cudaMemcpyAsync(x_out, top.x64, size_t(top.nvec()) * 8, cudaMemcpyDeviceToDevice, pb->stream));
+  if (stats) {
+    stats->wu_model = model_wu(pb, *prm);
+    stats->wu_counted = pb->wu_counted;
+    HHG_TRY(residual<double>(pb, top, top.x64, top.rhs, top.tmp64));
+    double nr[2];
+    HHG_TRY(norms_of(pb, top, HHG_FP64, top.tmp64, nr));
+    stats->res_u = nr[0];
+    stats->res_p = nr[1];
+    stats->kernel_launches = g_launches - launches0;
+    if (!std::isfinite(nr[0]) || !std::isfinite(nr[1])) return fail(HHG_EDIVERGED, "FMG produced a non-finite residual");
+  }
+  return HHG_OK;
+}
+
+extern "C" int hhg_estimate_omega(hhg_problem* pb, int level, int iters, const double* v0, double* omega_inv) {
+  HHG_TRY(check_level(pb, level));
+  if (!v0 || !omega_inv || iters < 1) return fail(HHG_EINVAL, "bad arguments");
+  Level& lv = pb->L(level);
+  const Geo& g = lv.g;
+  const int64_t po = p_offset(lv);
+  std::vector<double> h(size_t(lv.nvec()), 0.0);
+  for_each_pressure_node(g, [&](int64_t ci, int64_t site) { h[size_t(po + site)] = v0[ci]; });
+  double* V1 = lv.tmp64;   // (z_u | v_p)
+  double* V2 = lv.x64;     // (y_u | -v_p)
+  double* Wv = lv.bw64;    // (. | w_p)
+  HHG_CUDA(cudaMemcpyAsync(V1, h.data(), h.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  HHG_TRY(project_pressure(pb, lv, V1));
+  double nr[2];
+  HHG_TRY(norms_of(pb, lv, HHG_FP64, V1, nr));
+  launch_xpby<double>(V1 + po, 1.0 / nr[1] - 1.0, V1 + po, V1 + po, g.arr, pb->stream);
+  std::vector<std::pair<int, int>> phases;
+  for (int c = 0; c < 4; ++c) phases.push_back({0, c});
+  for (int gg = 1; gg < g.G; ++gg) phases.push_back({gg, -1});
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    HHG_TRY(apply_op<double>(pb, lv, OP_BT, MODE_SET, V1, nullptr, V1));          // z = B^T v
+    HHG_CUDA(cudaMemsetAsync(V2, 0, size_t(lv.nvec()) * 8, pb->stream));
+    for (auto& ph : phases) launch_gs<double>(g, lv.op[OP_A], ph.first, ph.second, lv.inv_diag[ph.first], V2, V1, pb->stream);
+    for (auto r = phases.rbegin(); r != phases.rend(); ++r)
+      launch_gs<double>(g, lv.op[OP_A], r->first, r->second, lv.inv_diag[r->first], V2, V1, pb->stream);
+    launch_axpy<double>(-1.0, V1 + po, V2 + po, g.arr, pb->stream);                // V2_p = -v
+    HHG_TRY(apply_op<double>(pb, lv, OP_BC, MODE_SET, V2, nullptr, Wv));           // w = B y + C v
+    launch_xpby<double>(Wv + po, 0.0, Wv + po, Wv + po, g.arr, pb->stream);
+    // w <- M_L(1/nu)^{-1} w : multiply by inv_mlhat through the pressure update
+    // kernel applied to a zero vector: 0 - (w * inv_ml) * (-1)
+    HHG_CUDA(cudaMemsetAsync(V1 + po, 0, size_t(g.arr) * 8, pb->stream));
+    launch_pupdate<double>(g, V1 + po, Wv + po, lv.inv_mlhat, -1.0, pb->stream);
+    HHG_CHECK_LAUNCH();
+    HHG_TRY(norms_of(pb, lv, HHG_FP64, V1, nr));
+    lam = nr[1];
+    if (!(lam > 0) || !std::isfinite(lam)) return fail(HHG_EDIVERGED, "power iteration broke down");
+    launch_xpby<double>(V1 + po, 1.0 / lam - 1.0, V1 + po, V1 + po, g.arr, pb->stream);
+  }
+  HHG_CUDA(cudaMemsetAsync(lv.tmp64, 0, size_t(lv.nvec()) * 8, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(lv.x64, 0, size_t(lv.nvec()) * 8, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(lv.bw64, 0, size_t(lv.nvec()) * 8, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  *omega_inv = lam;
+  return HHG_OK;
+}
+
+extern "C" int hhg_error_norms(hhg_problem* pb, int level, const void* x, const double* u_exact, const double* p_exact,
+                               double* err_u, double* err_p) {
+  HHG_TRY(check_level(pb, level));
+  if (!pb->desc.error_level || level != pb->desc.L) return fail(HHG_EINVAL, "error norms need error_level and level == L");
+  if (!x || !u_exact || !p_exact || !err_u || !err_p) return fail(HHG_EINVAL, "null argument");
+  Level& c = pb->L(level);
+  Level& f = pb->L(level + 1);
+  const Geo& g = f.g;
+  launch_xpby<double>(static_cast<const double*>(x), 1.0, c.W, c.tmp64, c.nvec(), pb->stream);
+  HHG_CUDA(cudaMemsetAsync(f.x64, 0, size_t(f.nvec()) * 8, pb->stream));
+  HHG_TRY(prolong_add<double>(pb, level + 1, c.tmp64, f.x64, false));
+  // exact nodal values on level l+1
+  const int64_t nvn = g.G == 1 ? int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1)
+                               : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
+  const int64_t npn = int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+  std::vector<double> can(size_t(3 * nvn + npn));
+  std::copy(u_exact, u_exact + 3 * nvn, can.begin());
+  std::copy(p_exact, p_exact + npn, can.begin() + 3 * nvn);
+  std::vector<double> h;
+  canonical_to_layout(f, can.data(), h);
+  HHG_CUDA(cudaMemcpyAsync(f.tmp64, h.data(), h.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  launch_xpby<double>(f.tmp64, -1.0, f.x64, f.tmp64, f.nvec(), pb->stream);        // d = x* - I x
+  HHG_TRY(project_pressure(pb, f, f.tmp64));
+  HHG_TRY(apply_op<double>(pb, f, OP_MASS, MODE_SET, f.tmp64, nullptr, f.x64));    // M d
+  const int64_t po = p_offset(f);
+  launch_reduce<double>(RED_DOT, f.tmp64, f.x64, nullptr, po, pb->partials, pb->max_blocks, pb->scal + 3, pb->stream);
+  launch_reduce<double>(RED_DOT, f.tmp64 + po, f.x64 + po, nullptr, g.arr, pb->partials, pb->max_blocks, pb->scal + 4, pb->stream);
+  HHG_CHECK_LAUNCH();
+  double e2[2];
+  HHG_CUDA(cudaMemcpyAsync(e2, pb->scal + 3, 16, cudaMemcpyDeviceToHost, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  *err_u = std::sqrt(std::max(e2[0], 0.0));
+  *err_p = std::sqrt(std::max(e2[1], 0.0));
+  HHG_CUDA(cudaMemsetAsync(c.tmp64, 0, size_t(c.nvec()) * 8, pb->stream));
+  return HHG_OK;
+}

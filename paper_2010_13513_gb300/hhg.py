@@ -1,0 +1,300 @@
+"""Thin ctypes binding of libhhg.so (include/hhg.h).
+
+Argument marshalling only: every step of the solve runs in the library's
+CUDA kernels.  PyTorch provides the device memory (workspace and vectors)
+and the CUDA stream.  There is no CPU fallback: loading fails loudly when
+the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhhg.so")
+
+P1P1 = 1
+P2P1 = 2
+FP64 = 0
+FP32 = 1
+SOLVE_FP64 = 0
+SOLVE_MIXED = 1
+OP = {"FULL": 0, "A": 1, "BT": 2, "B": 3, "C": 4, "MASS": 5}
+AHAT = {"f": 0, "s": 1}
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("disc", C.c_int), ("L", C.c_int), ("coarse_level", C.c_int), ("solve", C.c_int),
+                ("nu_a", C.c_double), ("pspg_rhs", C.c_int), ("error_level", C.c_int)]
+
+
+class LayoutInfo(C.Structure):
+    _fields_ = [("level", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("groups", C.c_int),
+                ("sx", C.c_int), ("sy", C.c_int64), ("array_elems", C.c_int64), ("vector_elems", C.c_int64),
+                ("n_velocity_nodes", C.c_int64), ("n_pressure_nodes", C.c_int64), ("n_dofs", C.c_int64),
+                ("h", C.c_double)]
+
+
+class Params(C.Structure):
+    """The FMG tuple s = (nu_pre, nu_post, nu_inc, kappa, A_hat, xi) and omega^{-1}."""
+    _fields_ = [("nu_pre", C.c_int), ("nu_post", C.c_int), ("nu_inc", C.c_int), ("kappa", C.c_int),
+                ("ahat", C.c_int), ("xi", C.c_int), ("omega_inv", C.c_double)]
+
+    @classmethod
+    def make(cls, nu_pre=3, nu_post=3, nu_inc=0, kappa=1, ahat="s", xi=1, omega_inv=0.5):
+        return cls(nu_pre, nu_post, nu_inc, kappa, AHAT[ahat] if isinstance(ahat, str) else ahat, xi, omega_inv)
+
+
+class Stats(C.Structure):
+    _fields_ = [("wu_model", C.c_double), ("wu_counted", C.c_double), ("res_u", C.c_double),
+                ("res_p", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Loads libhhg.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2010_13513_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    P, VP, I, D, DP = C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double)
+    sig = {
+        "hhg_last_error": [C.c_char_p, C.c_size_t],
+        "hhg_mesh_create": [DP, I, C.POINTER(C.c_int), I, C.POINTER(P)],
+        "hhg_mesh_create_box": [I, I, I, D, C.POINTER(P)],
+        "hhg_mesh_destroy": [P],
+        "hhg_problem_create": [P, C.POINTER(ProblemDesc), C.POINTER(P)],
+        "hhg_problem_workspace_bytes": [P, C.POINTER(C.c_size_t)],
+        "hhg_problem_bind": [P, VP, C.c_size_t, VP],
+        "hhg_problem_destroy": [P],
+        "hhg_layout": [P, I, C.POINTER(LayoutInfo)],
+        "hhg_vector_from_host": [P, I, I, DP, VP],
+        "hhg_vector_to_host": [P, I, I, VP, DP],
+        "hhg_set_rhs": [P, I, DP, DP],
+        "hhg_level_vector": [P, I, I, C.POINTER(VP)],
+        "hhg_apply": [P, I, I, I, VP, VP],
+        "hhg_residual": [P, I, I, VP, VP, VP, DP],
+        "hhg_smooth": [P, I, C.POINTER(Params), I, I, VP, VP],
+        "hhg_restrict": [P, I, I, VP, VP],
+        "hhg_prolongate_add": [P, I, I, VP, VP],
+        "hhg_coarse_solve": [P, I, VP, VP],
+        "hhg_vcycle": [P, I, C.POINTER(Params), I, VP, VP],
+        "hhg_fmg_solve": [P, C.POINTER(Params), VP, C.POINTER(Stats)],
+        "hhg_estimate_omega": [P, I, I, DP, DP],
+        "hhg_error_norms": [P, I, VP, DP, DP, DP, DP],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C ABI entry points declared in include/hhg.h."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "hhg.h")
+    with open(hdr) as f:
+        return sorted(set(re.findall(r"^int (hhg_\w+)\(", f.read(), flags=re.M)))
+
+
+class HHGError(RuntimeError):
+    pass
+
+
+def _check(rc, what=""):
+    if rc != 0:
+        buf = C.create_string_buffer(1024)
+        load().hhg_last_error(buf, 1024)
+        raise HHGError(f"{what} failed ({rc}): {buf.value.decode()}")
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Mesh:
+    def __init__(self, handle):
+        self.h = handle
+
+    @classmethod
+    def box(cls, mx, my, mz, H=1.0):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.hhg_mesh_create_box(mx, my, mz, H, C.byref(h)), "hhg_mesh_create_box")
+        return cls(h)
+
+    @classmethod
+    def from_tets(cls, verts, tets):
+        lib = load()
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tets, dtype=np.int32)
+        h = C.c_void_p()
+        _check(lib.hhg_mesh_create(_dp(v), v.shape[0], t.ctypes.data_as(C.POINTER(C.c_int)), t.shape[0],
+                                   C.byref(h)), "hhg_mesh_create")
+        return cls(h)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hhg_mesh_destroy(self.h)
+            self.h = None
+
+
+class Problem:
+    """A level hierarchy coarse_level..L of one Stokes problem on one GPU."""
+
+    def __init__(self, mesh: Mesh, disc="P1P1", L=4, coarse_level=0, solve="fp64", nu_a=0.0, pspg_rhs=True,
+                 error_level=False, device="cuda", stream=None):
+        lib = load()
+        self.disc = disc
+        self.L, self.lc = L, coarse_level
+        self.solve = solve
+        d = ProblemDesc(P1P1 if disc == "P1P1" else P2P1, L, coarse_level,
+                        SOLVE_MIXED if solve == "mixed" else SOLVE_FP64, float(nu_a), int(pspg_rhs), int(error_level))
+        h = C.c_void_p()
+        _check(lib.hhg_problem_create(mesh.h, C.byref(d), C.byref(h)), "hhg_problem_create")
+        self.h = h
+        self.mesh = mesh
+        nbytes = C.c_size_t()
+        _check(lib.hhg_problem_workspace_bytes(h, C.byref(nbytes)), "hhg_problem_workspace_bytes")
+        self.device = torch.device(device)
+        self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _check(lib.hhg_problem_bind(h, C.c_void_p(self._ws_ptr), nbytes.value, C.c_void_p(self.stream.cuda_stream)),
+               "hhg_problem_bind")
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hhg_problem_destroy(self.h)
+            self.h = None
+
+    # -------------------------------------------------------------- layout
+    def layout(self, level):
+        info = LayoutInfo()
+        _check(load().hhg_layout(self.h, level, C.byref(info)), "hhg_layout")
+        return info
+
+    def new_vector(self, level, prec=FP64):
+        n = self.layout(level).vector_elems
+        return torch.zeros(n, dtype=torch.float64 if prec == FP64 else torch.float32, device=self.device)
+
+    def to_device(self, level, host, prec=FP64, out=None):
+        host = np.ascontiguousarray(host, dtype=np.float64)
+        out = self.new_vector(level, prec) if out is None else out
+        _check(load().hhg_vector_from_host(self.h, level, prec, _dp(host), _ptr(out)), "hhg_vector_from_host")
+        return out
+
+    def to_host(self, level, dev, prec=None):
+        prec = (FP64 if dev.dtype == torch.float64 else FP32) if prec is None else prec
+        info = self.layout(level)
+        host = np.zeros(3 * info.n_velocity_nodes + info.n_pressure_nodes)
+        _check(load().hhg_vector_to_host(self.h, level, prec, _ptr(dev), _dp(host)), "hhg_vector_to_host")
+        return host
+
+    def level_vector(self, level, which):
+        """Library-owned FP64 vector as a torch view: 'rhs', 'W' or 'x'."""
+        p = C.c_void_p()
+        _check(load().hhg_level_vector(self.h, level, {"rhs": 0, "W": 1, "x": 2}[which], C.byref(p)),
+               "hhg_level_vector")
+        n = self.layout(level).vector_elems
+        off = (p.value - self.workspace.data_ptr()) // 8
+        assert (p.value - self.workspace.data_ptr()) % 8 == 0
+        return self.workspace.view(torch.float64)[off:off + n] if (self.workspace.data_ptr() % 8 == 0) else None
+
+    # ------------------------------------------------------------------ rhs
+    def set_rhs(self, level, f_nodal, w_nodal):
+        f = np.ascontiguousarray(f_nodal, dtype=np.float64)
+        w = np.ascontiguousarray(w_nodal, dtype=np.float64)
+        _check(load().hhg_set_rhs(self.h, level, _dp(f), _dp(w)), "hhg_set_rhs")
+
+    # ---------------------------------------------------------------- steps
+    @staticmethod
+    def _prec(t):
+        return FP64 if t.dtype == torch.float64 else FP32
+
+    def apply(self, level, op, x, y):
+        _check(load().hhg_apply(self.h, level, OP[op], self._prec(x), _ptr(x), _ptr(y)), "hhg_apply")
+
+    def residual(self, level, x, b, r, norms=False):
+        nr = np.zeros(2)
+        _check(load().hhg_residual(self.h, level, self._prec(x), _ptr(x), _ptr(b), _ptr(r),
+                                   _dp(nr) if norms else None), "hhg_residual")
+        return (float(nr[0]), float(nr[1])) if norms else None
+
+    def smooth(self, level, prm, sweeps, x, b):
+        _check(load().hhg_smooth(self.h, level, C.byref(prm), sweeps, self._prec(x), _ptr(x), _ptr(b)),
+               "hhg_smooth")
+
+    def restrict(self, level, rf, rc):
+        _check(load().hhg_restrict(self.h, level, self._prec(rf), _ptr(rf), _ptr(rc)), "hhg_restrict")
+
+    def prolongate_add(self, level, xc, xf):
+        _check(load().hhg_prolongate_add(self.h, level, self._prec(xc), _ptr(xc), _ptr(xf)), "hhg_prolongate_add")
+
+    def coarse_solve(self, b, x):
+        _check(load().hhg_coarse_solve(self.h, self._prec(b), _ptr(b), _ptr(x)), "hhg_coarse_solve")
+
+    def vcycle(self, level, prm, x, b):
+        _check(load().hhg_vcycle(self.h, level, C.byref(prm), self._prec(x), _ptr(x), _ptr(b)), "hhg_vcycle")
+
+    def fmg_solve(self, prm, x_out=None, stats=True):
+        st = Stats()
+        _check(load().hhg_fmg_solve(self.h, C.byref(prm), _ptr(x_out), C.byref(st) if stats else None),
+               "hhg_fmg_solve")
+        return st if stats else None
+
+    def estimate_omega(self, level, v0, iters=100):
+        v = np.ascontiguousarray(v0, dtype=np.float64)
+        out = C.c_double()
+        _check(load().hhg_estimate_omega(self.h, level, iters, _dp(v), C.byref(out)), "hhg_estimate_omega")
+        return out.value
+
+    def error_norms(self, level, x, u_exact, p_exact):
+        u = np.ascontiguousarray(u_exact, dtype=np.float64)
+        p = np.ascontiguousarray(p_exact, dtype=np.float64)
+        eu, ep = C.c_double(), C.c_double()
+        _check(load().hhg_error_norms(self.h, level, _ptr(x), _dp(u), _dp(p), C.byref(eu), C.byref(ep)),
+               "hhg_error_norms")
+        return eu.value, ep.value
+
+
+# --------------------------------------------------------------- helpers
+def velocity_coords(info):
+    """Canonical velocity node coordinates of a level (P1 lattice or doubled lattice)."""
+    if info.groups == 1:
+        n, hh = (info.nx + 1, info.ny + 1, info.nz + 1), info.h
+    else:
+        n, hh = (2 * info.nx + 1, 2 * info.ny + 1, 2 * info.nz + 1), info.h / 2
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    return np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1) * hh
+
+
+def pressure_coords(info):
+    k, j, i = np.meshgrid(np.arange(info.nz + 1), np.arange(info.ny + 1), np.arange(info.nx + 1), indexing="ij")
+    return np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1) * info.h
+
+
+def set_workload_rhs(pb: Problem, workload, levels=None):
+    """Evaluates the workload's forcing and Dirichlet data at the nodes of
+    every level and hands them to hhg_set_rhs (the assembly runs on the GPU)."""
+    levels = range(pb.lc, pb.L + 1) if levels is None else levels
+    for l in levels:
+        info = pb.layout(l)
+        X = velocity_coords(info)
+        f = workload.forcing(X)
+        w = workload.dirichlet(X)
+        pb.set_rhs(l, f.T.ravel(), w.T.ravel())

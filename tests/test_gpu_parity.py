@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Tolerances (FP64): 1e-12 relative per operator application and smoother
+step, 1e-10 relative per V-cycle / FMG solve.  Boxes are chosen to span
+several thread blocks and ragged tails (non-cubic boxes, odd extents).
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import OMEGA_INV, curl_workload, lib_problem, oracle_hierarchy, random_vector, rel
+
+pytestmark = pytest.mark.gpu
+
+APPLY_CASES = [
+    ("P1P1", (1, 1, 1), 3, 0.0),
+    ("P1P1", (2, 1, 3), 2, 0.0),
+    ("P1P1", (1, 2, 1), 3, 1.7),
+    ("P2P1", (1, 1, 1), 3, 0.0),
+    ("P2P1", (2, 1, 1), 2, 0.0),
+    ("P2P1", (1, 1, 2), 2, 1.1),
+]
+
+
+@pytest.mark.parametrize("disc,box,L,nu_a", APPLY_CASES)
+def test_apply_parity(disc, box, L, nu_a):
+    pb = lib_problem(box, L, disc, lc=1, nu_a=nu_a)
+    hy = oracle_hierarchy(box, L, disc, lc=1, nu_a=nu_a)
+    lev = hy.lv[L]
+    x = random_vector(lev, 0)
+    xd = pb.to_device(L, x)
+    y = pb.new_vector(L)
+    for op in ("FULL", "A", "BT", "B", "C"):
+        pb.apply(L, op, xd, y)
+        ref = lev.apply(x) if op == "FULL" else lev.apply_block(op, x)
+        got = pb.to_host(L, y)
+        if np.linalg.norm(ref) == 0:
+            assert np.abs(got).max() == 0
+        else:
+            assert rel(got, ref) < 1e-12, (op, rel(got, ref))
+    # mass matrix including Dirichlet rows, on a vector with boundary values
+    xf = random_vector(lev, 1, zero_dirichlet=False)
+    pb.apply(L, "MASS", pb.to_device(L, xf), y)
+    assert rel(pb.to_host(L, y), lev.apply_block("MASS", xf)) < 1e-12
+
+
+@pytest.mark.parametrize("disc,box,L,lc", [("P1P1", (1, 1, 1), 3, 0), ("P2P1", (1, 2, 1), 3, 1)])
+def test_rhs_parity(disc, box, L, lc):
+    wl = curl_workload() if box == (1, 1, 1) else __import__("hhg_inputs").Workload("modes", seed=3, box=box)
+    pb = lib_problem(box, L, disc, lc=lc, workload=wl)
+    hy = oracle_hierarchy(box, L, disc, lc=lc, workload=wl)
+    for l in range(lc, L + 1):
+        got = pb.to_host(l, pb.level_vector(l, "rhs"))
+        assert rel(got, hy.rhs[l]) < 1e-12, (l, rel(got, hy.rhs[l]))
+        gotW = pb.to_host(l, pb.level_vector(l, "W"))
+        assert rel(gotW, hy.W[l]) < 1e-14 or np.linalg.norm(hy.W[l]) == 0
+
+
+@pytest.mark.parametrize("disc,nu_a", [("P1P1", 0.0), ("P2P1", 0.0), ("P1P1", 1.5)])
+def test_residual_and_norms(disc, nu_a):
+    box, L = (1, 1, 2), 2
+    pb = lib_problem(box, L, disc, lc=1, nu_a=nu_a)
+    hy = oracle_hierarchy(box, L, disc, lc=1, nu_a=nu_a)
+    lev = hy.lv[L]
+    x, b = random_vector(lev, 2), random_vector(lev, 3)
+    r = pb.new_vector(L)
+    nr = pb.residual(L, pb.to_device(L, x), pb.to_device(L, b), r, norms=True)
+    ref = lev.residual(x, b)
+    assert rel(pb.to_host(L, r), ref) < 1e-12
+    assert np.allclose(nr, lev.norms(ref), rtol=1e-12)
+
+
+@pytest.mark.parametrize("disc,ahat,xi,nu_a", [("P1P1", "s", 1, 0.0), ("P1P1", "f", 2, 1.2), ("P2P1", "f", 3, 0.0),
+                                               ("P2P1", "s", 1, 0.0)])
+def test_uzawa_parity(disc, ahat, xi, nu_a):
+    from oracle.stokes import Params
+    from paper_2010_13513_gb300.hhg import Params as LParams
+    box, L = (2, 1, 1), 2
+    pb = lib_problem(box, L, disc, lc=1, nu_a=nu_a)
+    hy = oracle_hierarchy(box, L, disc, lc=1, nu_a=nu_a)
+    lev = hy.lv[L]
+    x, b = random_vector(lev, 4), random_vector(lev, 5)
+    om = OMEGA_INV[disc]
+    xd = pb.to_device(L, x)
+    pb.smooth(L, LParams.make(ahat=ahat, xi=xi, omega_inv=om), 2, xd, pb.to_device(L, b))
+    prm = Params(ahat=ahat, xi=xi, omega_inv=om)
+    ref = lev.uzawa(lev.uzawa(x, b, prm), b, prm)
+    assert rel(pb.to_host(L, xd), ref) < 1e-12
+
+
+@pytest.mark.parametrize("disc,box", [("P1P1", (2, 1, 1)), ("P2P1", (1, 1, 2)), ("P2P1", (1, 1, 1))])
+def test_transfer_parity(disc, box):
+    L = 2
+    pb = lib_problem(box, L, disc, lc=1)
+    hy = oracle_hierarchy(box, L, disc, lc=1)
+    fine, coarse = hy.lv[2], hy.lv[1]
+    xc = random_vector(coarse, 6)
+    xf = random_vector(fine, 7)
+    xfd = pb.to_device(2, xf)
+    pb.prolongate_add(2, pb.to_device(1, xc), xfd)
+    assert rel(pb.to_host(2, xfd), xf + hy.prolongate(2, xc)) < 1e-13
+    rc = pb.new_vector(1)
+    pb.restrict(2, pb.to_device(2, xf), rc)
+    assert rel(pb.to_host(1, rc), hy.restrict(2, xf)) < 1e-13
+
+
+@pytest.mark.parametrize("disc,lc", [("P1P1", 0), ("P1P1", 1), ("P2P1", 1)])
+def test_coarse_solve_parity(disc, lc):
+    box = (1, 1, 1)
+    wl = curl_workload()
+    pb = lib_problem(box, lc, disc, lc=lc, workload=wl)
+    hy = oracle_hierarchy(box, lc, disc, lc=lc, workload=wl)
+    b = hy.rhs[lc]
+    x = pb.new_vector(lc)
+    pb.coarse_solve(pb.to_device(lc, b), x)
+    assert rel(pb.to_host(lc, x), hy.coarse_solve(b)) < 1e-11
+
+
+@pytest.mark.parametrize("disc,L,lc,nu_a", [("P1P1", 3, 0, 0.0), ("P2P1", 3, 1, 0.0), ("P1P1", 3, 1, 2.0)])
+def test_vcycle_parity(disc, L, lc, nu_a):
+    from oracle.stokes import Params
+    from paper_2010_13513_gb300.hhg import Params as LParams
+    box = (1, 1, 1)
+    wl = curl_workload(nu_a)
+    pb = lib_problem(box, L, disc, lc=lc, nu_a=nu_a, workload=wl)
+    hy = oracle_hierarchy(box, L, disc, lc=lc, nu_a=nu_a, workload=wl)
+    om = OMEGA_INV[disc]
+    s = dict(nu_pre=2, nu_post=1, nu_inc=1, kappa=1, ahat="f", xi=2, omega_inv=om)
+    x = random_vector(hy.lv[L], 8)
+    xd = pb.to_device(L, x)
+    b = pb.level_vector(L, "rhs")
+    # dirty the library's coarse work vectors first (a previous solve)
+    pb.fmg_solve(LParams.make(**s), None, stats=False)
+    pb.vcycle(L, LParams.make(**s), xd, b)
+    ref = hy.vcycle(L, L, x, hy.rhs[L], Params(**s))
+    assert rel(pb.to_host(L, xd), ref) < 1e-10
+
+
+FMG_CASES = [
+    # the P1-P1 PSPG workload on the 6-tetrahedron cube, level 4, V(3,3)
+    ("P1P1", (1, 1, 1), 4, 0, 0.0, dict(nu_pre=3, nu_post=3, nu_inc=0, kappa=1, ahat="s", xi=1)),
+    ("P2P1", (1, 1, 1), 3, 1, 0.0, dict(nu_pre=1, nu_post=3, nu_inc=2, kappa=1, ahat="f", xi=3)),
+    ("P1P1", (2, 2, 2), 2, 0, 1.8, dict(nu_pre=2, nu_post=2, nu_inc=1, kappa=2, ahat="f", xi=1)),
+]
+
+
+@pytest.mark.parametrize("disc,box,L,lc,nu_a,s", FMG_CASES)
+def test_fmg_parity(disc, box, L, lc, nu_a, s):
+    from oracle.stokes import Params
+    from paper_2010_13513_gb300.hhg import Params as LParams
+    wl = curl_workload(nu_a)
+    pb = lib_problem(box, L, disc, lc=lc, nu_a=nu_a, workload=wl)
+    hy = oracle_hierarchy(box, L, disc, lc=lc, nu_a=nu_a, workload=wl)
+    om = OMEGA_INV[disc]
+    x = pb.new_vector(L)
+    st = pb.fmg_solve(LParams.make(**s, omega_inv=om), x)
+    ref = hy.fmg(Params(**s, omega_inv=om))
+    got = pb.to_host(L, x)
+    assert rel(got, ref) < 1e-10, rel(got, ref)
+    lev = hy.lv[L]
+    assert np.allclose([st.res_u, st.res_p], lev.norms(lev.residual(ref, hy.rhs[L])), rtol=1e-6)
+    assert st.kernel_launches > 0
+
+
+def test_omega_estimate_parity():
+    box, L = (1, 1, 1), 3
+    pb = lib_problem(box, L, "P1P1", lc=1)
+    hy = oracle_hierarchy(box, L, "P1P1", lc=1)
+    v0 = np.random.default_rng(0).uniform(-1, 1, hy.lv[L].np)
+    got = pb.estimate_omega(L, v0, iters=30)
+    ref = hy.estimate_omega_inv(v0, iters=30)
+    assert abs(got / ref - 1) < 1e-10
+
+
+@pytest.mark.parametrize("disc,L,lc", [("P1P1", 3, 0), ("P2P1", 2, 1)])
+def test_error_norms_parity(disc, L, lc):
+    from paper_2010_13513_gb300.hhg import pressure_coords, velocity_coords
+    from oracle.stokes import StokesLevel
+    box = (1, 1, 1)
+    wl = curl_workload()
+    pb = lib_problem(box, L, disc, lc=lc, workload=wl, error_level=True)
+    hy = oracle_hierarchy(box, L, disc, lc=lc, workload=wl)
+    x = random_vector(hy.lv[L], 9) * 0.01
+    info = pb.layout(L + 1)
+    ue = wl.exact_velocity(velocity_coords(info)).T.ravel()
+    pe = wl.exact_pressure(pressure_coords(info))
+    got = pb.error_norms(L, pb.to_device(L, x), ue, pe)
+    ref = hy.error_norms(x)
+    assert np.allclose(got, ref, rtol=1e-11)
+
+
+def test_mixed_precision_close_to_fp64_oracle():
+    """FP32 V-cycles inside FP64 refinement: reported error against the FP64
+    oracle (no parity claim); it must be far below the discretisation error."""
+    from oracle.stokes import Params
+    from paper_2010_13513_gb300.hhg import Params as LParams
+    box, L, lc = (1, 1, 1), 4, 0
+    wl = curl_workload()
+    s = dict(nu_pre=3, nu_post=3, nu_inc=0, kappa=1, ahat="s", xi=1, omega_inv=0.5)
+    pb = lib_problem(box, L, "P1P1", lc=lc, solve="mixed", workload=wl)
+    hy = oracle_hierarchy(box, L, "P1P1", lc=lc, workload=wl)
+    x = pb.new_vector(L)
+    pb.fmg_solve(LParams.make(**s), x)
+    ref = hy.fmg(Params(**s))
+    err = rel(pb.to_host(L, x), ref)
+    print(f"mixed-precision FMG vs FP64 oracle: relative difference {err:.3e}")
+    assert err < 1e-5
+
+
+def test_fp32_kernels_track_fp64():
+    """FP32 apply of the same operator: relative difference at FP32 rounding."""
+    box, L = (1, 1, 1), 3
+    pb = lib_problem(box, L, "P2P1", lc=1, solve="mixed")
+    hy = oracle_hierarchy(box, L, "P2P1", lc=1)
+    lev = hy.lv[L]
+    x = random_vector(lev, 10)
+    y = pb.new_vector(L, prec=1)
+    pb.apply(L, "FULL", pb.to_device(L, x, prec=1), y)
+    assert rel(pb.to_host(L, y), lev.apply(x)) < 1e-5
+
+
+def test_invalid_arguments_raise():
+    from paper_2010_13513_gb300 import hhg
+    pb = lib_problem((1, 1, 1), 2, "P1P1", lc=0)
+    with pytest.raises(hhg.HHGError):
+        pb.apply(7, "FULL", pb.new_vector(2), pb.new_vector(2))
+    with pytest.raises(hhg.HHGError):
+        pb.fmg_solve(hhg.Params.make())             # no rhs set

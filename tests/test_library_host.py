@@ -1,0 +1,108 @@
+"""Host-side checks of the C ABI library that need no GPU: it loads, exports
+every entry point declared in include/hhg.h, validates macro meshes and
+problem descriptions, and reports layouts and workspace sizes."""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from hhg_inputs import kuhn_box_macro_mesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hhg():
+    from paper_2010_13513_gb300 import build, hhg as mod
+    if not os.path.exists(mod.LIB_PATH):
+        build.build()
+    mod.load()
+    return mod
+
+
+def test_exports_every_declared_symbol(hhg):
+    out = subprocess.run(["nm", "-D", "--defined-only", hhg.LIB_PATH], capture_output=True, text=True).stdout
+    syms = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    declared = hhg.exported_symbols()
+    assert len(declared) >= 20
+    missing = [s for s in declared if s not in syms]
+    assert not missing, missing
+
+
+def _create(hhg, verts, tets):
+    lib = hhg.load()
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tets, dtype=np.int32)
+    h = C.c_void_p()
+    rc = lib.hhg_mesh_create(v.ctypes.data_as(C.POINTER(C.c_double)), v.shape[0],
+                             t.ctypes.data_as(C.POINTER(C.c_int)), t.shape[0], C.byref(h))
+    if rc == 0:
+        lib.hhg_mesh_destroy(h)
+    return rc
+
+
+@pytest.mark.parametrize("box", [(1, 1, 1), (2, 2, 2), (1, 2, 3)])
+def test_mesh_accepts_kuhn_boxes(hhg, box):
+    v, t = kuhn_box_macro_mesh(*box, H=0.5)
+    assert _create(hhg, v, t) == 0
+
+
+def test_mesh_rejects_other_meshes(hhg):
+    v, t = kuhn_box_macro_mesh(1, 1, 1)
+    assert _create(hhg, v, t[:5]) == -1                   # missing tetrahedron
+    t2 = t.copy()
+    t2[0] = [0, 1, 2, 4]                                    # corner simplex, not Kuhn
+    assert _create(hhg, v, t2) == -1
+    assert _create(hhg, v + 0.25, t) == -1                  # box not at the origin
+    buf = C.create_string_buffer(256)
+    hhg.load().hhg_last_error(buf, 256)
+    assert b"origin" in buf.value
+
+
+def _problem(hhg, disc, L, lc, solve=0, err=0, box=(1, 1, 1)):
+    lib = hhg.load()
+    mesh = C.c_void_p()
+    assert lib.hhg_mesh_create_box(*box, 1.0, C.byref(mesh)) == 0
+    d = hhg.ProblemDesc(disc, L, lc, solve, 0.0, 1, err)
+    pb = C.c_void_p()
+    rc = lib.hhg_problem_create(mesh, C.byref(d), C.byref(pb))
+    return rc, pb, mesh
+
+
+def test_problem_layout_and_workspace(hhg):
+    lib = hhg.load()
+    rc, pb, mesh = _problem(hhg, hhg.P2P1, 3, 1, solve=1, err=1)
+    assert rc == 0
+    info = hhg.LayoutInfo()
+    assert lib.hhg_layout(pb, 3, C.byref(info)) == 0
+    assert (info.nx, info.groups) == (8, 8)
+    assert info.n_velocity_nodes == 17 ** 3 and info.n_pressure_nodes == 9 ** 3
+    assert info.n_dofs == 3 * 17 ** 3 + 9 ** 3
+    assert info.vector_elems == 25 * info.array_elems and info.array_elems % 64 == 0
+    assert lib.hhg_layout(pb, 4, C.byref(info)) == 0          # error level
+    assert lib.hhg_layout(pb, 5, C.byref(info)) == -1
+    nbytes = C.c_size_t()
+    assert lib.hhg_problem_workspace_bytes(pb, C.byref(nbytes)) == 0
+    assert nbytes.value > 0 and nbytes.value % 256 == 0
+    # steps before binding a workspace are refused
+    assert lib.hhg_apply(pb, 3, 0, 0, C.c_void_p(256), C.c_void_p(512)) == -7
+    lib.hhg_problem_destroy(pb)
+    lib.hhg_mesh_destroy(mesh)
+
+
+def test_problem_rejects_bad_descriptions(hhg):
+    assert _problem(hhg, 7, 3, 0)[0] == -1
+    assert _problem(hhg, hhg.P1P1, 3, 4)[0] == -1
+    assert _problem(hhg, hhg.P1P1, 3, 0, solve=5)[0] == -1
+
+
+def test_bind_rejects_small_or_misaligned_workspace(hhg):
+    lib = hhg.load()
+    rc, pb, mesh = _problem(hhg, hhg.P1P1, 2, 0)
+    assert rc == 0
+    assert lib.hhg_problem_bind(pb, C.c_void_p(256), 16, None) == -2
+    assert lib.hhg_problem_bind(pb, C.c_void_p(257), 1 << 40, None) == -1
+    lib.hhg_problem_destroy(pb)
+    lib.hhg_mesh_destroy(mesh)

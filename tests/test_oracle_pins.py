@@ -474,3 +474,19 @@ def test_omega_estimate_near_paper():
     v0 = np.random.default_rng(0).uniform(-1, 1, hy.lv[4].np)
     om = hy.estimate_omega_inv(v0, iters=100)
     assert abs(om / ref - 1) < 0.10, om
+
+
+@pytest.mark.parametrize("disc,nu_a", [("P1P1", 0.0), ("P2P1", 0.0), ("P1P1", 1.3), ("P2P1", 0.7)])
+def test_sampled_rows_match_assembled(disc, nu_a):
+    """The single-row evaluator used at full problem sizes equals the
+    assembled operator (its own element loop, Eq. stokes-discrete)."""
+    from oracle.sampled import sample_rows
+    lev = StokesLevel((1, 2, 1), 0.5, 2, disc, nu_a=nu_a)
+    x = np.random.default_rng(0).uniform(-1, 1, lev.size)
+    y = lev.apply(x * np.concatenate([np.tile(lev.vint, 3), np.ones(lev.np)]))
+    rng = np.random.default_rng(1)
+    rows = [(int(f), int(rng.integers(0, lev.nv if f < 3 else lev.np))) for f in rng.integers(0, 4, 80)]
+    xs = x * np.concatenate([np.tile(lev.vint, 3), np.ones(lev.np)])
+    ys, ya = sample_rows((1, 2, 1), 0.5, 2, disc, xs, rows, nu_a, with_abs=True)
+    ref = np.array([y[f * lev.nv + n] if f < 3 else y[3 * lev.nv + n] for f, n in rows])
+    assert np.all(np.abs(ys - ref) <= 1e-14 * (ya + 1e-300) + 1e-300)
