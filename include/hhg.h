@@ -200,6 +200,10 @@ int hhg_vcycle(hhg_problem* pb, int level, const hhg_params* prm, int prec, void
  * x_out (device, may be NULL to keep it only in the workspace).  stats may be
  * NULL; if given, residual norms are computed (synchronises). */
 int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats* stats);
+/* Whether hhg_fmg_solve records its kernel sequence once per parameter tuple
+ * as a CUDA graph and replays it (default on).  Graphs are used only when the
+ * bound stream is a created stream (not the legacy default stream). */
+int hhg_set_graph_mode(hhg_problem* pb, int on);
 /* omega^{-1}: `iters` power iterations on M_L^{-1}(C + B A_s^{-1} B^T)
  * (Eq. omega-eigenvalue-problem) from the host start vector v0 (canonical
  * pressure order). */

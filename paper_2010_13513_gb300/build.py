@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhhg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "stencils.cpp", "problem.cpp"]
+SOURCES = ["kernels.cu", "fast.cu", "stencils.cpp", "problem.cpp"]
 
 
 def _nvcc():
@@ -34,7 +34,7 @@ def _compile(src, verbose):
     nvcc = _nvcc()
     obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include")]
+           "-I", os.path.join(ROOT, "include"), "-I", OUT]
     if src.endswith(".cu"):
         cmd += ARCH + ["-lineinfo", "--expt-relaxed-constexpr"]
         if verbose:
@@ -47,8 +47,29 @@ def _compile(src, verbose):
     return obj, r.stderr
 
 
+def _generate_structure():
+    """Compiles and runs the stencil-structure generator (host C++), which
+    writes the compile-time row term counts used by fast.cu."""
+    exe = os.path.join(OUT, "gen_structure")
+    cxx = shutil.which("g++") or shutil.which("c++")
+    cmd = [cxx, "-O1", "-std=c++17", "-I", os.path.join(ROOT, "include"), os.path.join(CSRC, "gen_structure.cpp"),
+           os.path.join(CSRC, "stencils.cpp"), "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"generator build failed: {' '.join(cmd)}\n{r.stderr}")
+    r = subprocess.run([exe], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"generator failed: {r.stderr}")
+    path = os.path.join(OUT, "structure.inc")
+    old = open(path).read() if os.path.exists(path) else None
+    if old != r.stdout:
+        with open(path, "w") as f:
+            f.write(r.stdout)
+
+
 def build(verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
+    _generate_structure()
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     objs = [o for o, _ in results]

@@ -1,0 +1,228 @@
+// Specialised stencil kernels for the hot operators of the V-cycle:
+// the Gauss-Seidel phases of the inexact Uzawa velocity step, and the
+// FULL / B^T / (B, -C) row evaluations (apply or residual mode).
+//
+// The term count of every row is a compile-time constant (generated at build
+// time from the stencil builder, structure.inc), so each row is one fully
+// unrolled sequence of independent loads and FMAs.  The weights and the
+// linear offsets of the level (array * array_stride + di + dj*sx + dk*sy) are
+// __grid_constant__ kernel parameters: every term reads its weight and offset
+// from the constant bank, not from memory.  Rows on the domain boundary
+// (pressure rows of the box faces) take the per-cube path of the generic
+// tables; Dirichlet velocity rows are zero.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <type_traits>
+
+#include "fast.h"
+#include "kernels.h"
+#include "structure.inc"
+
+namespace hhg {
+namespace {
+
+__constant__ int f_goff[8][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
+
+__device__ __forceinline__ int64_t fsite(const Geo& g, int i, int j, int k) {
+  return int64_t(i + 1) + int64_t(j + 1) * g.sx + int64_t(k + 1) * g.sy;
+}
+
+template <class T> __device__ __forceinline__ T bw(const OpDev& op, int t);
+template <> __device__ __forceinline__ double bw<double>(const OpDev& op, int t) { return __ldg(op.bw64 + t); }
+template <> __device__ __forceinline__ float bw<float>(const OpDev& op, int t) { return __ldg(op.bw32 + t); }
+
+// per-cube evaluation of a boundary row r of the generic tables
+template <class T>
+__device__ __noinline__ void boundary_row(const Geo& g, const OpDev& op, int r, int i, int j, int k, const T* x,
+                                          int64_t idx, T acc[3]) {
+  const DRow row = op.rows[r];
+  int t = row.b0;
+  const int ms[3] = {row.m0, row.m1, row.m2};
+  for (int s = 0; s < 3; ++s) {
+    T a = T(0);
+    for (int e = 0; e < ms[s]; ++e, ++t) {
+      const DTermB tm = op.bterms[t];
+      const int qx = i + tm.cx, qy = j + tm.cy, qz = k + tm.cz;
+      if (qx < 0 || qy < 0 || qz < 0 || qx >= g.nx || qy >= g.ny || qz >= g.nz) continue;
+      a += bw<T>(op, t) * x[int64_t(tm.arr) * g.arr + idx + tm.off];
+    }
+    acc[s] = a;
+  }
+}
+
+template <class S, int R, class F>
+__device__ __forceinline__ void dispatch(int r, F&& f) {
+  if constexpr (R < S::R) {
+    if (r == R) f(std::integral_constant<int, R>{});
+    else dispatch<S, R + 1>(r, f);
+  }
+}
+
+// ------------------------------------------------------------- row kernels
+template <int DISC, int VARNU, int OP, class T, int MODE>
+__global__ void __launch_bounds__(128)
+    k_rows_fast(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, T alpha, OpDev op,
+                const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP>::N> tab) {
+  using S = gen::S<DISC, VARNU, OP>;
+  const int nzp = g.nz + 1;
+  const int r = blockIdx.z / nzp;
+  const int k = blockIdx.z - r * nzp;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  dispatch<S, 0>(r, [&](auto rc) {
+    constexpr int R = decltype(rc)::value;
+    constexpr gen::RowS rw = S::rows[R];
+    const int ox = f_goff[rw.og][0], oy = f_goff[rw.og][1], oz = f_goff[rw.og][2];
+    if (i > g.nx - ox || j > g.ny - oy || k > g.nz - oz) return;
+    const int64_t idx = fsite(g, i, j, k);
+    T* yo = y + int64_t(rw.out) * g.arr + idx;
+    const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
+    const bool bnd = Px == 0 || Py == 0 || Pz == 0 || Px == 2 * g.nx || Py == 2 * g.ny || Pz == 2 * g.nz;
+    T acc[3];
+    if (!bnd) {
+      const T* xs = x + idx;
+      T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+      for (int t = 0; t < rw.n0; ++t) a0 += tab.w[rw.t0 + t] * xs[tab.off[rw.t0 + t]];
+#pragma unroll
+      for (int t = 0; t < rw.n1; ++t) a1 += tab.w[rw.t0 + rw.n0 + t] * xs[tab.off[rw.t0 + rw.n0 + t]];
+#pragma unroll
+      for (int t = 0; t < rw.n2; ++t) a2 += tab.w[rw.t0 + rw.n0 + rw.n1 + t] * xs[tab.off[rw.t0 + rw.n0 + rw.n1 + t]];
+      acc[0] = a0; acc[1] = a1; acc[2] = a2;
+    } else if (rw.all) {
+      boundary_row<T>(g, op, R, i, j, k, x, idx, acc);
+    } else {
+      if (MODE != MODE_ADD) *yo = T(0);
+      return;
+    }
+    T v = acc[0];
+    if (VARNU) {
+      const T e = T(exp(g.nu_ah * k));
+      v += e * acc[1] + acc[2] / e;
+    } else {
+      v += acc[1] + acc[2];
+    }
+    if (MODE == MODE_SET) *yo = v;
+    else if (MODE == MODE_RES) *yo = b[int64_t(rw.out) * g.arr + idx] - v;
+    else *yo += alpha * v;
+  });
+}
+
+// -------------------------------------------------- Gauss-Seidel phase kernel
+template <int DISC, int VARNU, int GRP, class T>
+__global__ void __launch_bounds__(128)
+    k_gs_fast(Geo g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag, int colour,
+              const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP_A>::N> tab) {
+  using S = gen::S<DISC, VARNU, OP_A>;
+  constexpr gen::RowS rw = S::rows[GRP];       // component-0 row of the group; all terms in segment 1
+  static_assert(rw.n0 == 0 && rw.n2 == 0, "A rows carry only nu-scaled terms");
+  const int k = blockIdx.z;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  constexpr int ox = GRP == 1 || GRP == 4 || GRP == 5 || GRP == 7;
+  constexpr int oy = GRP == 2 || GRP == 4 || GRP == 6 || GRP == 7;
+  constexpr int oz = GRP == 3 || GRP == 5 || GRP == 6 || GRP == 7;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (colour >= 0) i = 4 * i + (((colour - j - k) % 4) + 4) % 4;
+  const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
+  if (Px <= 0 || Py <= 0 || Pz <= 0 || Px >= 2 * g.nx || Py >= 2 * g.ny || Pz >= 2 * g.nz) return;
+  const int64_t idx = fsite(g, i, j, k);
+  const int64_t cs = int64_t(g.G) * g.arr;
+  const T* us = u + idx;
+  T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+  for (int t = 1; t < rw.n1; ++t) {            // the diagonal is the first term
+    const T w = tab.w[rw.t0 + t];
+    const int o = tab.off[rw.t0 + t];
+    a0 += w * us[o];
+    a1 += w * us[o + cs];
+    a2 += w * us[o + 2 * cs];
+  }
+  T einv = T(1);
+  if (VARNU) einv = T(exp(-g.nu_ah * k));
+  const int64_t o0 = int64_t(GRP) * g.arr + idx;
+  u[o0] = (rhs[o0] * einv - a0) * inv_diag;
+  u[o0 + cs] = (rhs[o0 + cs] * einv - a1) * inv_diag;
+  u[o0 + 2 * cs] = (rhs[o0 + 2 * cs] * einv - a2) * inv_diag;
+}
+
+}  // namespace
+
+// ================================================================= launchers
+template <int DISC, int VARNU, int OP, class T>
+void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, const T* x, const T* b, T* y,
+                      double alpha, cudaStream_t s) {
+  using S = gen::S<DISC, VARNU, OP>;
+  using Tab = FastTab<T, S::N>;
+  const Tab& tb = *static_cast<const Tab*>(tab);
+  dim3 blk(32, 4, 1);
+  dim3 grd((g.nx + 1 + 31) / 32, (g.ny + 1 + 3) / 4, (g.nz + 1) * S::R);
+  ++g_launches;
+  if (mode == MODE_SET) k_rows_fast<DISC, VARNU, OP, T, MODE_SET><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
+  else if (mode == MODE_RES) k_rows_fast<DISC, VARNU, OP, T, MODE_RES><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
+  else k_rows_fast<DISC, VARNU, OP, T, MODE_ADD><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
+}
+
+template <int DISC, int VARNU, class T>
+void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u, const T* rhs,
+                    cudaStream_t s) {
+  using S = gen::S<DISC, VARNU, OP_A>;
+  using Tab = FastTab<T, S::N>;
+  const Tab& tb = *static_cast<const Tab*>(tab);
+  dim3 blk(32, 4, 1);
+  const int ni = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1;
+  dim3 grd((ni + 31) / 32, (g.ny + 1 + 3) / 4, g.nz + 1);
+  ++g_launches;
+  switch (grp) {
+    case 0: k_gs_fast<DISC, VARNU, 0, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
+    case 1: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 1, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
+    case 2: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 2, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
+    case 3: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 3, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
+    case 4: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 4, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
+    case 5: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 5, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
+    case 6: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 6, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
+    case 7: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 7, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
+    default: break;
+  }
+}
+
+int fast_terms(int disc, int varnu, int op) {
+#define HHG_N(D, V, O) if (disc == D && varnu == V && op == O) return gen::S<D, V, O>::N;
+  HHG_N(1, 0, OP_FULL) HHG_N(1, 0, OP_A) HHG_N(1, 0, OP_BT) HHG_N(1, 0, OP_BC)
+  HHG_N(1, 1, OP_FULL) HHG_N(1, 1, OP_A) HHG_N(1, 1, OP_BT) HHG_N(1, 1, OP_BC)
+  HHG_N(2, 0, OP_FULL) HHG_N(2, 0, OP_A) HHG_N(2, 0, OP_BT) HHG_N(2, 0, OP_BC)
+  HHG_N(2, 1, OP_FULL) HHG_N(2, 1, OP_A) HHG_N(2, 1, OP_BT) HHG_N(2, 1, OP_BC)
+#undef HHG_N
+  return -1;
+}
+
+// run-time dispatch over (disc, varnu, op)
+template <class T>
+void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode, const T* x,
+               const T* b, T* y, double alpha, cudaStream_t s) {
+#define HHG_R(D, V, O) \
+  if (disc == D && varnu == V && op == O) return launch_rows_fast<D, V, O, T>(g, od, tab, mode, x, b, y, alpha, s);
+  HHG_R(1, 0, OP_FULL) HHG_R(1, 0, OP_BT) HHG_R(1, 0, OP_BC)
+  HHG_R(1, 1, OP_FULL) HHG_R(1, 1, OP_BT) HHG_R(1, 1, OP_BC)
+  HHG_R(2, 0, OP_FULL) HHG_R(2, 0, OP_BT) HHG_R(2, 0, OP_BC)
+  HHG_R(2, 1, OP_FULL) HHG_R(2, 1, OP_BT) HHG_R(2, 1, OP_BC)
+#undef HHG_R
+}
+
+template <class T>
+void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
+             const T* rhs, cudaStream_t s) {
+  if (disc == 1 && !varnu) launch_gs_fast<1, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, s);
+  else if (disc == 1) launch_gs_fast<1, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, s);
+  else if (!varnu) launch_gs_fast<2, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, s);
+  else launch_gs_fast<2, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, s);
+}
+
+template void fast_rows<double>(int, int, int, const Geo&, const OpDev&, const void*, int, const double*, const double*,
+                                double*, double, cudaStream_t);
+template void fast_rows<float>(int, int, int, const Geo&, const OpDev&, const void*, int, const float*, const float*,
+                               float*, double, cudaStream_t);
+template void fast_gs<double>(int, int, const Geo&, const void*, int, int, double, double*, const double*, cudaStream_t);
+template void fast_gs<float>(int, int, const Geo&, const void*, int, int, double, float*, const float*, cudaStream_t);
+
+}  // namespace hhg

@@ -1,0 +1,34 @@
+// Specialised stencil kernels (fast.cu): compile-time row structure,
+// weights and linear offsets passed as __grid_constant__ parameters.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace hhg {
+
+// weights and linear offsets (array * array_stride + di + dj sx + dk sy) of
+// the interior terms of one operator on one level, in table order
+template <class T, int N>
+struct FastTab {
+  T w[N];
+  int off[N];
+};
+
+// number of interior terms of a specialised operator (-1 if none)
+int fast_terms(int disc, int varnu, int op);
+
+// rows of OP_FULL / OP_BT / OP_BC (mode: MODE_SET / MODE_RES / MODE_ADD);
+// `tab` points to a host FastTab<T, fast_terms(...)>
+template <class T>
+void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode, const T* x,
+               const T* b, T* y, double alpha, cudaStream_t s);
+
+// one Gauss-Seidel phase (group, colour) on the three velocity components;
+// `tab` points to a host FastTab<T, fast_terms(disc, varnu, OP_A)>
+template <class T>
+void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
+             const T* rhs, cudaStream_t s);
+
+}  // namespace hhg

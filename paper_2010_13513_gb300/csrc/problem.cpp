@@ -13,6 +13,7 @@
 #include <tuple>
 #include <vector>
 
+#include "fast.h"
 #include "internal.h"
 #include "kernels.h"
 
@@ -119,6 +120,9 @@ struct Level {
   OpOffsets opoff[OP_COUNT];
   OpDev op[OP_COUNT];
   std::vector<double> inv_diag;         // per group 1/diag(A)
+  // parameter blocks of the specialised kernels (FastTab<T, N> images)
+  std::vector<char> ftab64[OP_COUNT], ftab32[OP_COUNT];
+  bool has_fast[OP_COUNT] = {};
   // workspace offsets (bytes) of the level vectors
   size_t o_rhs, o_W, o_x64, o_tmp64, o_bw64, o_x32, o_b32, o_tmp32, o_invml, o_ml;
   double *rhs = nullptr, *W = nullptr, *x64 = nullptr, *tmp64 = nullptr, *bw64 = nullptr;
@@ -153,6 +157,14 @@ struct hhg_problem {
   bool bound = false;
   int64_t launches = 0;
   double wu_counted = 0.0;
+  // CUDA graphs of whole FMG solves, keyed by the parameter tuple
+  bool use_graphs = true;
+  struct Graph { cudaGraphExec_t exec; int64_t kernels; double wu; };
+  std::map<std::tuple<int, int, int, int, int, int, double>, Graph> graphs;
+
+  ~hhg_problem() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+  }
 
   Level& L(int l) { return lv[l - desc.coarse_level]; }
   int Lmax() const { return desc.L; }
@@ -266,11 +278,32 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
   pb->tv = build_transfer(pb->ov);
   pb->tp = build_transfer(1);
 
-  // ---- device table blob
+  // ---- device table blob and specialised-kernel parameter blocks
   Blob& B = pb->tables;
+  const int varnu = desc->nu_a != 0.0 ? 1 : 0;
   for (Level& lv : pb->lv) {
     for (int o = 0; o < OP_COUNT; ++o) {
       OpHost h = serialise(lv.st.op[o], lv.g);
+      const int N = fast_terms(desc->disc, varnu, o);
+      if (N >= 0) {
+        if (N != int(h.terms.size())) return fail(HHG_EINVAL, "internal: specialised kernel structure mismatch");
+        auto image = [&](auto zero, std::vector<char>& out) {
+          using T = decltype(zero);
+          const size_t bytes = (size_t(N) * (sizeof(T) + 4) + 7) / 8 * 8;
+          out.assign(bytes, 0);
+          T* w = reinterpret_cast<T*>(out.data());
+          int* off = reinterpret_cast<int*>(out.data() + size_t(N) * sizeof(T));
+          for (int t = 0; t < N; ++t) {
+            const int64_t lin = int64_t(h.terms[t].arr) * lv.g.arr + h.terms[t].off;
+            if (lin > INT32_MAX || lin < INT32_MIN) return false;
+            w[t] = T(h.w64[t]);
+            off[t] = int(lin);
+          }
+          return true;
+        };
+        if (!image(0.0, lv.ftab64[o]) || !image(0.0f, lv.ftab32[o])) return fail(HHG_EINVAL, "level too large for 32-bit offsets");
+        lv.has_fast[o] = true;
+      }
       std::vector<float> w32(h.w64.begin(), h.w64.end()), bw32(h.bw64.begin(), h.bw64.end());
       OpOffsets& of = lv.opoff[o];
       of.nrows = int(h.rows.size());
@@ -501,9 +534,17 @@ Costs block_costs(int ov) {
   return {0.3, 0.3, 0.1};
 }
 
+template <class T> const void* ftab(Level& lv, int op);
+template <> const void* ftab<double>(Level& lv, int op) { return lv.ftab64[op].data(); }
+template <> const void* ftab<float>(Level& lv, int op) { return lv.ftab32[op].data(); }
+
 template <class T>
 int apply_op(hhg_problem* pb, Level& lv, int op, int mode, const T* x, const T* b, T* y, double alpha = 1.0) {
-  launch_apply<T>(lv.g, lv.op[op], mode, x, b, y, alpha, pb->stream);
+  if (lv.has_fast[op] && op != OP_A)
+    fast_rows<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, op, lv.g, lv.op[op], ftab<T>(lv, op), mode, x, b, y,
+                 alpha, pb->stream);
+  else
+    launch_apply<T>(lv.g, lv.op[op], mode, x, b, y, alpha, pb->stream);
   HHG_CHECK_LAUNCH();
   return HHG_OK;
 }
@@ -522,11 +563,13 @@ int uzawa(hhg_problem* pb, Level& lv, const hhg_params& prm, int sweeps, T* x, c
   for (int it = 0; it < sweeps; ++it) {
     // velocity step (Eq. uzawa-velocity): f' = f - B^T p_k, xi GS sweeps on A u = f'
     HHG_TRY(apply_op<T>(pb, lv, OP_BT, MODE_RES, x, b, tmp));
+    const int disc = pb->desc.disc, varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
+    const void* tabA = ftab<T>(lv, OP_A);
     for (int s = 0; s < prm.xi; ++s) {
-      for (auto& ph : phases) launch_gs<T>(lv.g, lv.op[OP_A], ph.first, ph.second, lv.inv_diag[ph.first], x, tmp, pb->stream);
+      for (auto& ph : phases) fast_gs<T>(disc, varnu, lv.g, tabA, ph.first, ph.second, lv.inv_diag[ph.first], x, tmp, pb->stream);
       if (prm.ahat == HHG_AHAT_S)
         for (auto it2 = phases.rbegin(); it2 != phases.rend(); ++it2)
-          launch_gs<T>(lv.g, lv.op[OP_A], it2->first, it2->second, lv.inv_diag[it2->first], x, tmp, pb->stream);
+          fast_gs<T>(disc, varnu, lv.g, tabA, it2->first, it2->second, lv.inv_diag[it2->first], x, tmp, pb->stream);
     }
     HHG_CHECK_LAUNCH();
     // pressure step (Eq. uzawa-pressure): p -= S_hat^{-1} (g - B u_{k+1} + C p_k)
@@ -961,12 +1004,9 @@ double model_wu(const hhg_problem* pb, const hhg_params& p) {
 }
 }  // namespace
 
-extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats* stats) {
-  HHG_TRY(check_level(pb, pb ? pb->desc.L : 0));
-  HHG_TRY(check_params(prm));
-  for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l)
-    if (!pb->L(l).has_rhs) return fail(HHG_ESTATE, "hhg_set_rhs missing on a level");
-  const int64_t launches0 = g_launches;
+namespace {
+// the kernel sequence of one FMG solve (Algorithm 1); no host synchronisation
+int fmg_core(hhg_problem* pb, const hhg_params* prm) {
   pb->wu_counted = 0.0;
   const int lc = pb->desc.coarse_level;
   Level& c = pb->L(lc);
@@ -990,6 +1030,51 @@ extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out
       HHG_TRY(project_pressure(pb, lv, lv.x64));
     }
   }
+  return HHG_OK;
+}
+
+bool capturable(cudaStream_t s) {
+  return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+}  // namespace
+
+extern "C" int hhg_set_graph_mode(hhg_problem* pb, int on) {
+  if (!pb) return fail(HHG_EINVAL, "null problem");
+  pb->use_graphs = on != 0;
+  return HHG_OK;
+}
+
+extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats* stats) {
+  HHG_TRY(check_level(pb, pb ? pb->desc.L : 0));
+  HHG_TRY(check_params(prm));
+  for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l)
+    if (!pb->L(l).has_rhs) return fail(HHG_ESTATE, "hhg_set_rhs missing on a level");
+  int64_t kernels = 0;
+  if (pb->use_graphs && capturable(pb->stream)) {
+    auto key = std::make_tuple(prm->nu_pre, prm->nu_post, prm->nu_inc, prm->kappa, prm->ahat, prm->xi, prm->omega_inv);
+    auto it = pb->graphs.find(key);
+    if (it == pb->graphs.end()) {
+      const int64_t l0 = g_launches;
+      HHG_CUDA(cudaStreamBeginCapture(pb->stream, cudaStreamCaptureModeThreadLocal));
+      int rc = fmg_core(pb, prm);
+      cudaGraph_t graph = nullptr;
+      cudaError_t ec = cudaStreamEndCapture(pb->stream, &graph);
+      if (rc != HHG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+      if (ec != cudaSuccess) return fail(HHG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+      cudaGraphExec_t exec;
+      cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) return fail(HHG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+      it = pb->graphs.emplace(key, hhg_problem::Graph{exec, g_launches - l0, pb->wu_counted}).first;
+    }
+    HHG_CUDA(cudaGraphLaunch(it->second.exec, pb->stream));
+    kernels = it->second.kernels;
+    pb->wu_counted = it->second.wu;
+  } else {
+    const int64_t l0 = g_launches;
+    HHG_TRY(fmg_core(pb, prm));
+    kernels = g_launches - l0;
+  }
   Level& top = pb->L(pb->desc.L);
   if (x_out) HHG_CUDA(cudaMemcpyAsync(x_out, top.x64, size_t(top.nvec()) * 8, cudaMemcpyDeviceToDevice, pb->stream));
   if (stats) {
@@ -1000,7 +1085,7 @@ extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out
     HHG_TRY(norms_of(pb, top, HHG_FP64, top.tmp64, nr));
     stats->res_u = nr[0];
     stats->res_p = nr[1];
-    stats->kernel_launches = g_launches - launches0;
+    stats->kernel_launches = kernels;
     if (!std::isfinite(nr[0]) || !std::isfinite(nr[1])) return fail(HHG_EDIVERGED, "FMG produced a non-finite residual");
   }
   return HHG_OK;

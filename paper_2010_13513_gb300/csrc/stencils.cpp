@@ -233,6 +233,11 @@ void accumulate_block(BlockAcc& acc, int out_order, int og, int in_order, int in
         }
 }
 
+// Terms that cancel exactly for a constant viscosity (e.g. the diagonal
+// directions of the P1 Laplacian) are dropped; with a variable viscosity every
+// structural term is kept, so the term list never depends on the values.
+bool g_drop_zeros = true;
+
 void flush_block(const BlockAcc& acc, HRow& row, int seg, bool self_first, int self_arr, bool with_boundary) {
   double mx = 0.0;
   for (auto& kv : acc.merged) mx = std::max(mx, std::fabs(kv.second));
@@ -240,7 +245,7 @@ void flush_block(const BlockAcc& acc, HRow& row, int seg, bool self_first, int s
   for (auto& kv : acc.cube) mxc = std::max(mxc, std::fabs(kv.second));
   std::vector<HTerm> terms;
   for (auto& kv : acc.merged) {
-    if (std::fabs(kv.second) <= 1e-12 * mx) continue;     // exact cancellations (e.g. P1 diagonals)
+    if (g_drop_zeros && std::fabs(kv.second) <= 1e-12 * mx) continue;
     HTerm t{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first), 0, 0, 0,
             kv.second};
     terms.push_back(t);
@@ -253,7 +258,7 @@ void flush_block(const BlockAcc& acc, HRow& row, int seg, bool self_first, int s
   row.seg[seg].insert(row.seg[seg].end(), terms.begin(), terms.end());
   if (!with_boundary) return;
   for (auto& kv : acc.cube) {
-    if (std::fabs(kv.second) <= 1e-12 * mxc) continue;
+    if (g_drop_zeros && std::fabs(kv.second) <= 1e-12 * mxc) continue;
     HTerm t{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
             std::get<4>(kv.first), std::get<5>(kv.first), std::get<6>(kv.first), kv.second};
     row.bseg[seg].push_back(t);
@@ -267,6 +272,7 @@ StencilSet build_stencils(int disc, double h, double nu_a, bool pspg_rhs) {
   const int G = ov == 1 ? 1 : 8;
   const int parr = 3 * G;
   const double nu_ah = nu_a * h;
+  g_drop_zeros = nu_a == 0.0;
   ElemMats E[6];
   for (int s = 0; s < 6; ++s) E[s] = element_matrices(kuhn_tet(s), ov, h);
   const int nv = E[0].nv;

@@ -88,6 +88,7 @@ def load():
         "hhg_vcycle": [P, I, C.POINTER(Params), I, VP, VP],
         "hhg_fmg_solve": [P, C.POINTER(Params), VP, C.POINTER(Stats)],
         "hhg_estimate_omega": [P, I, I, DP, DP],
+        "hhg_set_graph_mode": [P, I],
         "hhg_error_norms": [P, I, VP, DP, DP, DP, DP],
     }
     for name, args in sig.items():
@@ -170,10 +171,11 @@ class Problem:
         nbytes = C.c_size_t()
         _check(lib.hhg_problem_workspace_bytes(h, C.byref(nbytes)), "hhg_problem_workspace_bytes")
         self.device = torch.device(device)
-        self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.stream(self.stream):
+            self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) // 256 * 256
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         _check(lib.hhg_problem_bind(h, C.c_void_p(self._ws_ptr), nbytes.value, C.c_void_p(self.stream.cuda_stream)),
                "hhg_problem_bind")
 
@@ -190,7 +192,8 @@ class Problem:
 
     def new_vector(self, level, prec=FP64):
         n = self.layout(level).vector_elems
-        return torch.zeros(n, dtype=torch.float64 if prec == FP64 else torch.float32, device=self.device)
+        with torch.cuda.stream(self.stream):
+            return torch.zeros(n, dtype=torch.float64 if prec == FP64 else torch.float32, device=self.device)
 
     def to_device(self, level, host, prec=FP64, out=None):
         host = np.ascontiguousarray(host, dtype=np.float64)
@@ -256,6 +259,9 @@ class Problem:
         _check(load().hhg_fmg_solve(self.h, C.byref(prm), _ptr(x_out), C.byref(st) if stats else None),
                "hhg_fmg_solve")
         return st if stats else None
+
+    def set_graph_mode(self, on):
+        _check(load().hhg_set_graph_mode(self.h, int(on)), "hhg_set_graph_mode")
 
     def estimate_omega(self, level, v0, iters=100):
         v = np.ascontiguousarray(v0, dtype=np.float64)

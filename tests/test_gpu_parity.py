@@ -227,3 +227,24 @@ def test_invalid_arguments_raise():
         pb.apply(7, "FULL", pb.new_vector(2), pb.new_vector(2))
     with pytest.raises(hhg.HHGError):
         pb.fmg_solve(hhg.Params.make())             # no rhs set
+
+
+def test_fmg_graph_replay_matches_direct_launches():
+    """The CUDA-graph replay of a whole FMG solve issues the same kernels as
+    the direct launches: results are bitwise equal, repeatedly."""
+    from paper_2010_13513_gb300 import hhg
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pb = lib_problem((1, 1, 1), 3, "P2P1", lc=1, solve="mixed", workload=curl_workload())
+    assert pb.stream == stream
+    prm = hhg.Params.make(1, 3, 2, 1, "f", 3, 0.3)
+    xg = pb.new_vector(3)
+    st1 = pb.fmg_solve(prm, xg)                  # records and replays the graph
+    st2 = pb.fmg_solve(prm, xg)                  # replays the cached graph
+    pb.set_graph_mode(False)
+    xd = pb.new_vector(3)
+    st3 = pb.fmg_solve(prm, xd)
+    stream.synchronize()
+    assert torch.equal(xg, xd)
+    assert st1.kernel_launches == st2.kernel_launches == st3.kernel_launches
+    assert st1.res_u == st3.res_u and st1.res_p == st3.res_p
