@@ -215,6 +215,27 @@ int hhg_estimate_omega(hhg_problem* pb, int level, int iters, const double* v0, 
 int hhg_error_norms(hhg_problem* pb, int level, const void* x, const double* u_exact,
                     const double* p_exact, double* err_u, double* err_p);
 
+/* ------------------------------------------------- allocation-free utility */
+/* Euclidean norms of the two parts of a block vector x (device pointer,
+ * element type `prec`): norms[0] = ||x[0 .. n_velocity)||_2 and norms[1] =
+ * ||x[n_velocity .. n_velocity + n_pressure)||_2, written to `norms` (device
+ * pointer to 2 doubles) on `stream` (cudaStream_t).  With x a residual from
+ * hhg_residual and n_velocity = 3 * groups * array_elems, n_pressure =
+ * array_elems (hhg_layout), these are the residual norms hhg_residual reports.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (allocator or pool callbacks, hosts that own
+ * every allocation).  It allocates nothing: its partial sums live in a
+ * 16 KB __device__ array of the library that every GPU loading the library
+ * holds until exit.  Each part may hold at most 2^31 - 1 elements (larger
+ * sizes return HHG_EINVAL).  The first call on a device looks the array up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialised by
+ * the caller.  Every call writes all partial sums it reads, so nothing needs
+ * clearing between calls. */
+int hhg_block_norms_noalloc(const void* x, int prec, int64_t n_velocity, int64_t n_pressure, double* norms,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,11 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
+namespace hhg {
+// records an error message for hhg_last_error (used by other translation units)
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace hhg
+
 struct hhg_mesh {
   int mx, my, mz;
   double H;

@@ -90,6 +90,7 @@ def load():
         "hhg_estimate_omega": [P, I, I, DP, DP],
         "hhg_set_graph_mode": [P, I],
         "hhg_error_norms": [P, I, VP, DP, DP, DP, DP],
+        "hhg_block_norms_noalloc": [VP, I, C.c_int64, C.c_int64, VP, VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
