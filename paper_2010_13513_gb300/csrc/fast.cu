@@ -32,13 +32,15 @@ template <class T> __device__ __forceinline__ T bw(const OpDev& op, int t);
 template <> __device__ __forceinline__ double bw<double>(const OpDev& op, int t) { return __ldg(op.bw64 + t); }
 template <> __device__ __forceinline__ float bw<float>(const OpDev& op, int t) { return __ldg(op.bw32 + t); }
 
-// per-cube evaluation of a boundary row r of the generic tables
+// per-cube evaluation of a boundary row r of the generic tables: returns the
+// three segment sums
 template <class T>
-__device__ __noinline__ void boundary_row(const Geo& g, const OpDev& op, int r, int i, int j, int k, const T* x,
-                                          int64_t idx, T acc[3]) {
+__device__ __forceinline__ void boundary_row(const Geo& g, const OpDev& op, int r, int i, int j, int k, const T* x,
+                                          int64_t idx, T& s0, T& s1, T& s2) {
   const DRow row = op.rows[r];
   int t = row.b0;
   const int ms[3] = {row.m0, row.m1, row.m2};
+  T acc[3] = {T(0), T(0), T(0)};
   for (int s = 0; s < 3; ++s) {
     T a = T(0);
     for (int e = 0; e < ms[s]; ++e, ++t) {
@@ -49,6 +51,7 @@ __device__ __noinline__ void boundary_row(const Geo& g, const OpDev& op, int r, 
     }
     acc[s] = a;
   }
+  s0 = acc[0]; s1 = acc[1]; s2 = acc[2];
 }
 
 template <class S, int R, class F>
@@ -59,70 +62,146 @@ __device__ __forceinline__ void dispatch(int r, F&& f) {
   }
 }
 
+// sum of w[t] * xs[off[t]] for t in [T0, T0 + N): one fully unrolled chain
+template <int T0, int N, class T, class Tab>
+__device__ __forceinline__ T seg_sum(const Tab& tab, const T* __restrict__ xs) {
+  T a = T(0);
+#pragma unroll
+  for (int t = 0; t < N; ++t) a += tab.w[T0 + t] * __ldg(xs + tab.off[T0 + t]);
+  return a;
+}
+
+// launch shape of the row kernel: threads per block and k planes per thread
+#ifndef HHG_ROW_THREADS
+#define HHG_ROW_THREADS 128
+#endif
+#ifndef HHG_ROW_KPLANES
+#define HHG_ROW_KPLANES 2
+#endif
+constexpr int kRowThreads = HHG_ROW_THREADS;
+constexpr int kKPlanes = HHG_ROW_KPLANES;
+
 // ------------------------------------------------------------- row kernels
+// grid: x over the (i, j) plane of sites (flat, i fastest), y = groups of
+// kKPlanes planes, z = row.  The row is the slowest grid dimension, so the
+// blocks resident at the same time run the same (fully unrolled) row code.
+template <int DISC, int VARNU, int OP, class T, int MODE, int OUT, int OG, int ALL, int T0, int N0, int N1, int N2,
+          class Tab>
+__device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restrict__ x, const T* __restrict__ b,
+                                         T* __restrict__ y, T alpha, const OpDev& op, const Tab& tab) {
+  constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
+  constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
+  constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
+  const int w = g.nx + 1 - ox;                       // sites per i row of this group
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = q / w;
+  const int i = q - j * w;
+  if (j > g.ny - oy) return;
+  const int k0 = blockIdx.y * kKPlanes;
+  const bool bij = 2 * i + ox == 0 || 2 * i + ox == 2 * g.nx || 2 * j + oy == 0 || 2 * j + oy == 2 * g.ny;
+#pragma unroll 1
+  for (int k = k0; k < k0 + kKPlanes && k <= g.nz - oz; ++k) {
+    const int64_t idx = fsite(g, i, j, k);
+    T* yo = y + int64_t(OUT) * g.arr + idx;
+    const bool bnd = bij || 2 * k + oz == 0 || 2 * k + oz == 2 * g.nz;
+    T a0, a1, a2;
+    if (!bnd) {
+      const T* xs = x + idx;
+      a0 = seg_sum<T0, N0, T>(tab, xs);
+      a1 = seg_sum<T0 + N0, N1, T>(tab, xs);
+      a2 = seg_sum<T0 + N0 + N1, N2, T>(tab, xs);
+    } else if (ALL) {
+      continue;                                      // written by k_rows_faces
+    } else {
+      if (MODE != MODE_ADD) *yo = T(0);
+      continue;
+    }
+    T v = a0;
+    if (VARNU) {
+      const T e = T(exp(g.nu_ah * k));
+      v += e * a1 + a2 / e;
+    } else {
+      v += a1 + a2;
+    }
+    if (MODE == MODE_SET) *yo = v;
+    else if (MODE == MODE_RES) *yo = b[int64_t(OUT) * g.arr + idx] - v;
+    else *yo += alpha * v;
+  }
+}
+
 template <int DISC, int VARNU, int OP, class T, int MODE>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kRowThreads)
     k_rows_fast(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, T alpha, OpDev op,
                 const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP>::N> tab) {
   using S = gen::S<DISC, VARNU, OP>;
-  const int nzp = g.nz + 1;
-  const int r = blockIdx.z / nzp;
-  const int k = blockIdx.z - r * nzp;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  dispatch<S, 0>(r, [&](auto rc) {
+  dispatch<S, 0>(int(blockIdx.z), [&](auto rc) {
     constexpr int R = decltype(rc)::value;
     constexpr gen::RowS rw = S::rows[R];
-    const int ox = f_goff[rw.og][0], oy = f_goff[rw.og][1], oz = f_goff[rw.og][2];
-    if (i > g.nx - ox || j > g.ny - oy || k > g.nz - oz) return;
-    const int64_t idx = fsite(g, i, j, k);
-    T* yo = y + int64_t(rw.out) * g.arr + idx;
-    const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
-    const bool bnd = Px == 0 || Py == 0 || Pz == 0 || Px == 2 * g.nx || Py == 2 * g.ny || Pz == 2 * g.nz;
-    T acc[3];
-    if (!bnd) {
-      const T* xs = x + idx;
-      T a0 = T(0), a1 = T(0), a2 = T(0);
-#pragma unroll
-      for (int t = 0; t < rw.n0; ++t) a0 += tab.w[rw.t0 + t] * xs[tab.off[rw.t0 + t]];
-#pragma unroll
-      for (int t = 0; t < rw.n1; ++t) a1 += tab.w[rw.t0 + rw.n0 + t] * xs[tab.off[rw.t0 + rw.n0 + t]];
-#pragma unroll
-      for (int t = 0; t < rw.n2; ++t) a2 += tab.w[rw.t0 + rw.n0 + rw.n1 + t] * xs[tab.off[rw.t0 + rw.n0 + rw.n1 + t]];
-      acc[0] = a0; acc[1] = a1; acc[2] = a2;
-    } else if (rw.all) {
-      boundary_row<T>(g, op, R, i, j, k, x, idx, acc);
-    } else {
-      if (MODE != MODE_ADD) *yo = T(0);
-      return;
-    }
-    T v = acc[0];
-    if (VARNU) {
-      const T e = T(exp(g.nu_ah * k));
-      v += e * acc[1] + acc[2] / e;
-    } else {
-      v += acc[1] + acc[2];
-    }
-    if (MODE == MODE_SET) *yo = v;
-    else if (MODE == MODE_RES) *yo = b[int64_t(rw.out) * g.arr + idx] - v;
-    else *yo += alpha * v;
+    eval_row<DISC, VARNU, OP, T, MODE, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, x, b, y, alpha, op,
+                                                                                          tab);
   });
 }
 
-// -------------------------------------------------- Gauss-Seidel phase kernel
-template <int DISC, int VARNU, int GRP, class T>
+// Rows that exist on the domain boundary (pressure rows) at boundary sites:
+// per-cube terms of the generic tables.  The thread index enumerates the six
+// faces of the box of vertex sites: z = 0, nz (full planes), y = 0, ny (without
+// the z faces), x = 0, nx (without the y and z faces).
+template <class T, int MODE, int VARNU>
 __global__ void __launch_bounds__(128)
-    k_gs_fast(Geo g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag, int colour,
-              const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP_A>::N> tab) {
-  using S = gen::S<DISC, VARNU, OP_A>;
-  constexpr gen::RowS rw = S::rows[GRP];       // component-0 row of the group; all terms in segment 1
-  static_assert(rw.n0 == 0 && rw.n2 == 0, "A rows carry only nu-scaled terms");
-  const int k = blockIdx.z;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    k_rows_faces(Geo g, int row, int out, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y,
+                 T alpha, OpDev op) {
+  int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t fz = int64_t(g.nx + 1) * (g.ny + 1);
+  const int64_t fy = int64_t(g.nx + 1) * (g.nz - 1);
+  const int64_t fx = int64_t(g.ny - 1) * (g.nz - 1);
+  int i, j, k;
+  if (q < 2 * fz) {
+    k = q < fz ? 0 : g.nz;
+    q %= fz;
+    j = int(q / (g.nx + 1));
+    i = int(q % (g.nx + 1));
+  } else if ((q -= 2 * fz) < 2 * fy) {
+    j = q < fy ? 0 : g.ny;
+    q %= fy;
+    k = 1 + int(q / (g.nx + 1));
+    i = int(q % (g.nx + 1));
+  } else if ((q -= 2 * fy) < 2 * fx) {
+    i = q < fx ? 0 : g.nx;
+    q %= fx;
+    k = 1 + int(q / (g.ny - 1));
+    j = 1 + int(q % (g.ny - 1));
+  } else {
+    return;
+  }
+  const int64_t idx = fsite(g, i, j, k);
+  T a0, a1, a2;
+  boundary_row<T>(g, op, row, i, j, k, x, idx, a0, a1, a2);
+  T v = a0;
+  if (VARNU) {
+    const T e = T(exp(g.nu_ah * k));
+    v += e * a1 + a2 / e;
+  } else {
+    v += a1 + a2;
+  }
+  T* yo = y + int64_t(out) * g.arr + idx;
+  if (MODE == MODE_SET) *yo = v;
+  else if (MODE == MODE_RES) *yo = b[int64_t(out) * g.arr + idx] - v;
+  else *yo += alpha * v;
+}
+
+// -------------------------------------------------- Gauss-Seidel phase kernel
+// grid: x over the (i', j) plane (i' = i, or i / 4 for a vertex colour), z = k
+template <int DISC, int VARNU, int GRP, class T, int T0, int N1, class Tab>
+__device__ __forceinline__ void gs_site(const Geo& g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag,
+                                        int colour, const Tab& tab) {
   constexpr int ox = GRP == 1 || GRP == 4 || GRP == 5 || GRP == 7;
   constexpr int oy = GRP == 2 || GRP == 4 || GRP == 6 || GRP == 7;
   constexpr int oz = GRP == 3 || GRP == 5 || GRP == 6 || GRP == 7;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.z;
+  const int w = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1 - ox;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = q / w;
+  int i = q - j * w;
   if (colour >= 0) i = 4 * i + (((colour - j - k) % 4) + 4) % 4;
   const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
   if (Px <= 0 || Py <= 0 || Pz <= 0 || Px >= 2 * g.nx || Py >= 2 * g.ny || Pz >= 2 * g.nz) return;
@@ -131,12 +210,12 @@ __global__ void __launch_bounds__(128)
   const T* us = u + idx;
   T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
-  for (int t = 1; t < rw.n1; ++t) {            // the diagonal is the first term
-    const T w = tab.w[rw.t0 + t];
-    const int o = tab.off[rw.t0 + t];
-    a0 += w * us[o];
-    a1 += w * us[o + cs];
-    a2 += w * us[o + 2 * cs];
+  for (int t = 1; t < N1; ++t) {               // the diagonal is the first term
+    const T wt = tab.w[T0 + t];
+    const int o = tab.off[T0 + t];
+    a0 += wt * us[o];
+    a1 += wt * us[o + cs];
+    a2 += wt * us[o + 2 * cs];
   }
   T einv = T(1);
   if (VARNU) einv = T(exp(-g.nu_ah * k));
@@ -144,6 +223,16 @@ __global__ void __launch_bounds__(128)
   u[o0] = (rhs[o0] * einv - a0) * inv_diag;
   u[o0 + cs] = (rhs[o0 + cs] * einv - a1) * inv_diag;
   u[o0 + 2 * cs] = (rhs[o0 + 2 * cs] * einv - a2) * inv_diag;
+}
+
+template <int DISC, int VARNU, int GRP, class T>
+__global__ void __launch_bounds__(128)
+    k_gs_fast(Geo g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag, int colour,
+              const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP_A>::N> tab) {
+  using S = gen::S<DISC, VARNU, OP_A>;
+  constexpr gen::RowS rw = S::rows[GRP];       // component-0 row of the group; all terms in segment 1
+  static_assert(rw.n0 == 0 && rw.n2 == 0, "A rows carry only nu-scaled terms");
+  gs_site<DISC, VARNU, GRP, T, rw.t0, rw.n1>(g, u, rhs, inv_diag, colour, tab);
 }
 
 }  // namespace
@@ -155,12 +244,25 @@ void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, 
   using S = gen::S<DISC, VARNU, OP>;
   using Tab = FastTab<T, S::N>;
   const Tab& tb = *static_cast<const Tab*>(tab);
-  dim3 blk(32, 4, 1);
-  dim3 grd((g.nx + 1 + 31) / 32, (g.ny + 1 + 3) / 4, (g.nz + 1) * S::R);
+  dim3 blk(kRowThreads, 1, 1);
+  const int plane = (g.nx + 1) * (g.ny + 1);
+  dim3 grd((plane + kRowThreads - 1) / kRowThreads, (g.nz + 1 + kKPlanes - 1) / kKPlanes, S::R);
   ++g_launches;
   if (mode == MODE_SET) k_rows_fast<DISC, VARNU, OP, T, MODE_SET><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
   else if (mode == MODE_RES) k_rows_fast<DISC, VARNU, OP, T, MODE_RES><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
   else k_rows_fast<DISC, VARNU, OP, T, MODE_ADD><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
+  // boundary sites of the rows that exist there (vertex sites only: pressure rows)
+  const int64_t nface = 2 * int64_t(g.nx + 1) * (g.ny + 1) + 2 * int64_t(g.nx + 1) * (g.nz - 1) +
+                        2 * int64_t(g.ny - 1) * (g.nz - 1);
+  for (int r = 0; r < S::R; ++r) {
+    if (!S::rows[r].all) continue;
+    ++g_launches;
+    const int nb = int((nface + 127) / 128);
+    const int out = S::rows[r].out;
+    if (mode == MODE_SET) k_rows_faces<T, MODE_SET, VARNU><<<nb, 128, 0, s>>>(g, r, out, x, b, y, T(alpha), op);
+    else if (mode == MODE_RES) k_rows_faces<T, MODE_RES, VARNU><<<nb, 128, 0, s>>>(g, r, out, x, b, y, T(alpha), op);
+    else k_rows_faces<T, MODE_ADD, VARNU><<<nb, 128, 0, s>>>(g, r, out, x, b, y, T(alpha), op);
+  }
 }
 
 template <int DISC, int VARNU, class T>
@@ -169,9 +271,10 @@ void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double i
   using S = gen::S<DISC, VARNU, OP_A>;
   using Tab = FastTab<T, S::N>;
   const Tab& tb = *static_cast<const Tab*>(tab);
-  dim3 blk(32, 4, 1);
+  dim3 blk(128, 1, 1);
   const int ni = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1;
-  dim3 grd((ni + 31) / 32, (g.ny + 1 + 3) / 4, g.nz + 1);
+  const int plane = ni * (g.ny + 1);
+  dim3 grd((plane + 127) / 128, 1, g.nz + 1);
   ++g_launches;
   switch (grp) {
     case 0: k_gs_fast<DISC, VARNU, 0, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
