@@ -180,7 +180,9 @@ int hhg_level_vector(hhg_problem* pb, int level, int which, void** dev);
 
 /* ---------------------------------------------------------- hot-path steps */
 /* y = Op x on level l (Eq. stokes-discrete blocks); Dirichlet velocity rows
- * of y are 0 except for HHG_OP_MASS. */
+ * of y are 0 except for HHG_OP_MASS.  For HHG_OP_FULL, x must be in lifting
+ * form (Dirichlet velocity entries 0, as in every solver vector); the other
+ * operators accept any x. */
 int hhg_apply(hhg_problem* pb, int level, int op, int prec, const void* x, void* y);
 /* r = b - calA x; if norms != NULL, norms[0] = ||r_u||_2, norms[1] = ||r_p||_2
  * (synchronises). */

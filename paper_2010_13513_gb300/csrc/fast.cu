@@ -2,6 +2,9 @@
 // the Gauss-Seidel phases of the inexact Uzawa velocity step, and the
 // FULL / B^T / (B, -C) row evaluations (apply or residual mode).
 //
+// Inputs must have zero Dirichlet velocity entries (the lifting form used by
+// the solver): boundary pressure rows then use the merged B stencil.
+//
 // The term count of every row is a compile-time constant (generated at build
 // time from the stencil builder, structure.inc), so each row is one fully
 // unrolled sequence of independent loads and FMAs.  The weights and the
@@ -52,6 +55,21 @@ __device__ __forceinline__ void boundary_row(const Geo& g, const OpDev& op, int 
     acc[s] = a;
   }
   s0 = acc[0]; s1 = acc[1]; s2 = acc[2];
+}
+
+// per-cube evaluation of the third segment (C terms) of a boundary row
+template <class T>
+__device__ __forceinline__ T boundary_seg2(const Geo& g, const OpDev& op, int r, int i, int j, int k, const T* x,
+                                           int64_t idx) {
+  const DRow row = op.rows[r];
+  T a = T(0);
+  for (int t = row.b0 + row.m0 + row.m1; t < row.b0 + row.m0 + row.m1 + row.m2; ++t) {
+    const DTermB tm = op.bterms[t];
+    const int qx = i + tm.cx, qy = j + tm.cy, qz = k + tm.cz;
+    if (qx < 0 || qy < 0 || qz < 0 || qx >= g.nx || qy >= g.ny || qz >= g.nz) continue;
+    a += bw<T>(op, t) * x[int64_t(tm.arr) * g.arr + idx + tm.off];
+  }
+  return a;
 }
 
 template <class S, int R, class F>
@@ -111,7 +129,14 @@ __device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restric
       a1 = seg_sum<T0 + N0, N1, T>(tab, xs);
       a2 = seg_sum<T0 + N0 + N1, N2, T>(tab, xs);
     } else if (ALL) {
-      continue;                                      // written by k_rows_faces
+      // boundary pressure row: with zero Dirichlet velocity entries the merged
+      // B terms are exact (every tetrahedron containing an interior velocity
+      // DoF lies inside the domain; boundary and halo velocity values are 0);
+      // only the C terms need the per-cube restriction to the domain
+      const T* xs = x + idx;
+      a0 = seg_sum<T0, N0, T>(tab, xs);
+      a1 = seg_sum<T0 + N0, N1, T>(tab, xs);
+      a2 = N2 > 0 ? boundary_seg2<T>(g, op, R, i, j, k, x, idx) : T(0);
     } else {
       if (MODE != MODE_ADD) *yo = T(0);
       continue;
@@ -140,53 +165,6 @@ __global__ void __launch_bounds__(kRowThreads)
     eval_row<DISC, VARNU, OP, T, MODE, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, x, b, y, alpha, op,
                                                                                           tab);
   });
-}
-
-// Rows that exist on the domain boundary (pressure rows) at boundary sites:
-// per-cube terms of the generic tables.  The thread index enumerates the six
-// faces of the box of vertex sites: z = 0, nz (full planes), y = 0, ny (without
-// the z faces), x = 0, nx (without the y and z faces).
-template <class T, int MODE, int VARNU>
-__global__ void __launch_bounds__(128)
-    k_rows_faces(Geo g, int row, int out, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y,
-                 T alpha, OpDev op) {
-  int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const int64_t fz = int64_t(g.nx + 1) * (g.ny + 1);
-  const int64_t fy = int64_t(g.nx + 1) * (g.nz - 1);
-  const int64_t fx = int64_t(g.ny - 1) * (g.nz - 1);
-  int i, j, k;
-  if (q < 2 * fz) {
-    k = q < fz ? 0 : g.nz;
-    q %= fz;
-    j = int(q / (g.nx + 1));
-    i = int(q % (g.nx + 1));
-  } else if ((q -= 2 * fz) < 2 * fy) {
-    j = q < fy ? 0 : g.ny;
-    q %= fy;
-    k = 1 + int(q / (g.nx + 1));
-    i = int(q % (g.nx + 1));
-  } else if ((q -= 2 * fy) < 2 * fx) {
-    i = q < fx ? 0 : g.nx;
-    q %= fx;
-    k = 1 + int(q / (g.ny - 1));
-    j = 1 + int(q % (g.ny - 1));
-  } else {
-    return;
-  }
-  const int64_t idx = fsite(g, i, j, k);
-  T a0, a1, a2;
-  boundary_row<T>(g, op, row, i, j, k, x, idx, a0, a1, a2);
-  T v = a0;
-  if (VARNU) {
-    const T e = T(exp(g.nu_ah * k));
-    v += e * a1 + a2 / e;
-  } else {
-    v += a1 + a2;
-  }
-  T* yo = y + int64_t(out) * g.arr + idx;
-  if (MODE == MODE_SET) *yo = v;
-  else if (MODE == MODE_RES) *yo = b[int64_t(out) * g.arr + idx] - v;
-  else *yo += alpha * v;
 }
 
 // -------------------------------------------------- Gauss-Seidel phase kernel
@@ -251,18 +229,6 @@ void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, 
   if (mode == MODE_SET) k_rows_fast<DISC, VARNU, OP, T, MODE_SET><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
   else if (mode == MODE_RES) k_rows_fast<DISC, VARNU, OP, T, MODE_RES><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
   else k_rows_fast<DISC, VARNU, OP, T, MODE_ADD><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
-  // boundary sites of the rows that exist there (vertex sites only: pressure rows)
-  const int64_t nface = 2 * int64_t(g.nx + 1) * (g.ny + 1) + 2 * int64_t(g.nx + 1) * (g.nz - 1) +
-                        2 * int64_t(g.ny - 1) * (g.nz - 1);
-  for (int r = 0; r < S::R; ++r) {
-    if (!S::rows[r].all) continue;
-    ++g_launches;
-    const int nb = int((nface + 127) / 128);
-    const int out = S::rows[r].out;
-    if (mode == MODE_SET) k_rows_faces<T, MODE_SET, VARNU><<<nb, 128, 0, s>>>(g, r, out, x, b, y, T(alpha), op);
-    else if (mode == MODE_RES) k_rows_faces<T, MODE_RES, VARNU><<<nb, 128, 0, s>>>(g, r, out, x, b, y, T(alpha), op);
-    else k_rows_faces<T, MODE_ADD, VARNU><<<nb, 128, 0, s>>>(g, r, out, x, b, y, T(alpha), op);
-  }
 }
 
 template <int DISC, int VARNU, class T>
