@@ -206,6 +206,10 @@ int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats
  * as a CUDA graph and replays it (default on).  Graphs are used only when the
  * bound stream is a created stream (not the legacy default stream). */
 int hhg_set_graph_mode(hhg_problem* pb, int on);
+/* Whether the smoother runs all phases of a small level (at most 5^3
+ * lattice sites) in one thread-block-cluster launch (default on) or one
+ * launch per phase.  Both give the same iterates. */
+int hhg_set_small_level_mode(hhg_problem* pb, int on);
 /* omega^{-1}: `iters` power iterations on M_L^{-1}(C + B A_s^{-1} B^T)
  * (Eq. omega-eigenvalue-problem) from the host start vector v0 (canonical
  * pressure order). */

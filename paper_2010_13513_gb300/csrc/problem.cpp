@@ -16,6 +16,7 @@
 #include "fast.h"
 #include "internal.h"
 #include "kernels.h"
+#include "small.h"
 
 using namespace hhg;
 
@@ -128,6 +129,9 @@ struct Level {
   // parameter blocks of the specialised kernels (FastTab<T, N> images)
   std::vector<char> ftab64[OP_COUNT], ftab32[OP_COUNT];
   bool has_fast[OP_COUNT] = {};
+  // parameter block of the cluster-resident smoother (small levels only)
+  std::vector<char> stab64, stab32;
+  bool small = false;
   // workspace offsets (bytes) of the level vectors
   size_t o_rhs, o_W, o_x64, o_tmp64, o_bw64, o_x32, o_b32, o_tmp32, o_invml, o_ml;
   double *rhs = nullptr, *W = nullptr, *x64 = nullptr, *tmp64 = nullptr, *bw64 = nullptr;
@@ -164,6 +168,7 @@ struct hhg_problem {
   double wu_counted = 0.0;
   // CUDA graphs of whole FMG solves, keyed by the parameter tuple
   bool use_graphs = true;
+  bool use_cluster = true;       // cluster-resident smoother on small levels
   struct Graph { cudaGraphExec_t exec; int64_t kernels; double wu; };
   std::map<std::tuple<int, int, int, int, int, int, double>, Graph> graphs;
 
@@ -335,6 +340,22 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
   };
   put_x(pb->tv, pb->xoff_v);
   put_x(pb->tp, pb->xoff_p);
+  // small levels: tables of the cluster-resident smoother
+  for (Level& lv : pb->lv) {
+    const int64_t sites = int64_t(lv.g.nx + 1) * (lv.g.ny + 1) * (lv.g.nz + 1);
+    if (sites > kSmallLevelSites) continue;
+    auto pack = [&](int prec, const std::vector<char>* src, std::vector<char>& out) {
+      out.assign(small_tabs_bytes(desc->disc, varnu, prec), 0);
+      const int ops[3] = {OP_A, OP_BT, OP_BC};
+      for (int w = 0; w < 3; ++w) {
+        const size_t off = small_tabs_offset(desc->disc, varnu, prec, w);
+        std::memcpy(out.data() + off, src[ops[w]].data(), src[ops[w]].size());
+      }
+    };
+    pack(HHG_FP64, lv.ftab64, lv.stab64);
+    pack(HHG_FP32, lv.ftab32, lv.stab32);
+    lv.small = true;
+  }
 
   // ---- workspace layout
   size_t off = 0;
@@ -558,9 +579,29 @@ double level_weight(hhg_problem* pb, const Level& lv) {
   return double(lv.n_dofs()) / double(pb->L(pb->desc.L).n_dofs());
 }
 
+template <class T> const void* stab(Level& lv);
+template <> const void* stab<double>(Level& lv) { return lv.stab64.data(); }
+template <> const void* stab<float>(Level& lv) { return lv.stab32.data(); }
+
 template <class T>
 int uzawa(hhg_problem* pb, Level& lv, const hhg_params& prm, int sweeps, T* x, const T* b, T* tmp) {
   const int G = lv.g.G;
+  if (sweeps <= 0) return HHG_OK;
+  if (lv.small && pb->use_cluster) {
+    // all phases of all sweeps in one cluster launch
+    SmallArgs a{};
+    a.iterations = sweeps;
+    a.xi = prm.xi;
+    a.ahat = prm.ahat;
+    a.inv_omega_inv = 1.0 / prm.omega_inv;
+    for (int gg = 0; gg < G; ++gg) a.inv_diag[gg] = lv.inv_diag[gg];
+    if (uzawa_cluster<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, lv.g, x, b, tmp, lv.inv_mlhat, a,
+                         lv.op[OP_BC], stab<T>(lv), pb->stream) != 0)
+      return fail(HHG_ECUDA, std::string("cluster smoother launch: ") + cudaGetErrorString(cudaGetLastError()));
+    const Costs cs = block_costs(pb->ov);
+    pb->wu_counted += sweeps * level_weight(pb, lv) * (prm.xi * (prm.ahat == HHG_AHAT_S ? 2 : 1) * cs.A + 2 * cs.B + cs.C);
+    return HHG_OK;
+  }
   std::vector<std::pair<int, int>> phases;
   for (int c = 0; c < 4; ++c) phases.push_back({0, c});
   for (int gg = 1; gg < G; ++gg) phases.push_back({gg, -1});
@@ -1046,6 +1087,14 @@ bool capturable(cudaStream_t s) {
 extern "C" int hhg_set_graph_mode(hhg_problem* pb, int on) {
   if (!pb) return fail(HHG_EINVAL, "null problem");
   pb->use_graphs = on != 0;
+  return HHG_OK;
+}
+
+extern "C" int hhg_set_small_level_mode(hhg_problem* pb, int on) {
+  if (!pb) return fail(HHG_EINVAL, "null problem");
+  pb->use_cluster = on != 0;
+  for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
+  pb->graphs.clear();
   return HHG_OK;
 }
 

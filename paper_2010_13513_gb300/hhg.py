@@ -89,6 +89,7 @@ def load():
         "hhg_fmg_solve": [P, C.POINTER(Params), VP, C.POINTER(Stats)],
         "hhg_estimate_omega": [P, I, I, DP, DP],
         "hhg_set_graph_mode": [P, I],
+        "hhg_set_small_level_mode": [P, I],
         "hhg_error_norms": [P, I, VP, DP, DP, DP, DP],
         "hhg_block_norms_noalloc": [VP, I, C.c_int64, C.c_int64, VP, VP],
     }
@@ -263,6 +264,9 @@ class Problem:
 
     def set_graph_mode(self, on):
         _check(load().hhg_set_graph_mode(self.h, int(on)), "hhg_set_graph_mode")
+
+    def set_small_level_mode(self, on):
+        _check(load().hhg_set_small_level_mode(self.h, int(on)), "hhg_set_small_level_mode")
 
     def estimate_omega(self, level, v0, iters=100):
         v = np.ascontiguousarray(v0, dtype=np.float64)

@@ -248,3 +248,20 @@ def test_fmg_graph_replay_matches_direct_launches():
     assert torch.equal(xg, xd)
     assert st1.kernel_launches == st2.kernel_launches == st3.kernel_launches
     assert st1.res_u == st3.res_u and st1.res_p == st3.res_p
+
+
+@pytest.mark.parametrize("disc,L,lc,solve,ahat", [("P2P1", 4, 1, "mixed", "f"), ("P1P1", 4, 0, "fp64", "s"),
+                                                  ("P1P1", 3, 1, "mixed", "s")])
+def test_cluster_smoother_matches_per_phase_launches(disc, L, lc, solve, ahat):
+    """Small levels run all smoother phases in one thread-block-cluster launch;
+    the iterates equal those of one launch per phase."""
+    from paper_2010_13513_gb300 import hhg
+    pb = lib_problem((1, 1, 1), L, disc, lc=lc, solve=solve, workload=curl_workload())
+    prm = hhg.Params.make(1, 3, 2, 1, ahat, 2, OMEGA_INV[disc])
+    x1 = pb.new_vector(L)
+    pb.fmg_solve(prm, x1, stats=False)
+    pb.set_small_level_mode(False)
+    x2 = pb.new_vector(L)
+    pb.fmg_solve(prm, x2, stats=False)
+    torch.cuda.synchronize()
+    assert rel(x1.cpu().numpy(), x2.cpu().numpy()) < 1e-13
