@@ -280,6 +280,7 @@ def main():
 
     # ---------------- set-up (not timed): hierarchy, rhs on all levels, omega
     pb, wl = make_problem("mixed", error_level=(rank == 0 and not args.profile_region))
+    shapes = pb.autotune(reps=5)
     if args.profile_region:
         prm = hhg.Params.make(**PARAMS, omega_inv=0.32)
         x = pb.new_vector(L)
@@ -323,6 +324,7 @@ def main():
 
     # FP64-only GPU solve of the same workload (same tuple, same omega)
     pb64, _ = make_problem("fp64")
+    pb64.autotune(reps=3)
     x64 = pb64.new_vector(L)
     t64 = statistics.mean(time_steps(pb64, prm, x64, max(3, args.steps // 2), 2, pb64.stream)) * 1e-3
     mixed_vs_fp64 = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
@@ -345,6 +347,7 @@ def main():
                    "gamma_u": acc[0], "gamma_p": acc[1], "disc_accuracy": bool(acc[0] <= 2 and acc[1] <= 2),
                    "err_fmg": acc[2], "err_disc": acc[3], "disc_solve_cycles": acc[4],
                    "wu_model": st.wu_model, "wu_counted": st.wu_counted,
+                   "launch_shapes": {str(k): v for k, v in shapes.items()},
                    "fp64_gpu_ms_per_step": t64 * 1e3, "mixed_speedup_vs_fp64_gpu": t64 / t_step,
                    "mixed_vs_fp64_rel_diff": mixed_vs_fp64},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",

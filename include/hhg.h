@@ -93,6 +93,7 @@ extern "C" {
 
 typedef struct hhg_mesh hhg_mesh;
 typedef struct hhg_problem hhg_problem;
+typedef struct hhg_batch hhg_batch;
 
 typedef struct {
     int disc;            /* HHG_P1P1_PSPG or HHG_P2P1_TH                                  */
@@ -202,6 +203,30 @@ int hhg_vcycle(hhg_problem* pb, int level, const hhg_params* prm, int prec, void
  * x_out (device, may be NULL to keep it only in the workspace).  stats may be
  * NULL; if given, residual norms are computed (synchronises). */
 int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats* stats);
+/* Per-level autotuner of the launch shapes (threads per block and k planes
+ * per thread of the stencil-row kernels, threads per block of the
+ * Gauss-Seidel kernels): every candidate is timed `reps` times with CUDA
+ * events on the problem's stream in the precision of the V-cycles, the
+ * fastest is kept.  Uses only the library's scratch vectors (tmp, b); cached
+ * graphs are dropped.  shapes_out (optional) receives 3 ints per level
+ * (coarse .. L).  Synchronises. */
+int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
+
+/* ------------------------------------------------------------------ batches */
+/* A batch of n independent problems (each bound, with its rhs set on every
+ * level; a problem may belong to one batch at a time).  The handles are
+ * borrowed: the problems must outlive the batch.  The batch owns n CUDA
+ * streams and events (no device memory). */
+int hhg_batch_create(hhg_problem* const* problems, int n, hhg_batch** out);
+int hhg_batch_destroy(hhg_batch* batch);
+/* FMG (Algorithm 1) of every problem of the batch, params[i] for problem i.
+ * The first call (and every call with different parameters) records one CUDA
+ * graph in which every problem's FMG is an independent branch; the graph is
+ * launched on `stream` (cudaStream_t, must not be the legacy default stream).
+ * Each problem's solution ends in its workspace (hhg_level_vector(.., L, 2)).
+ * *kernels (optional) receives the kernel count of the graph.  Asynchronous. */
+int hhg_batch_fmg_solve(hhg_batch* batch, const hhg_params* params, void* stream, int64_t* kernels);
+
 /* Whether hhg_fmg_solve records its kernel sequence once per parameter tuple
  * as a CUDA graph and replays it (default on).  Graphs are used only when the
  * bound stream is a created stream (not the legacy default stream). */

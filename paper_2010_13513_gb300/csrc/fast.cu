@@ -89,24 +89,17 @@ __device__ __forceinline__ T seg_sum(const Tab& tab, const T* __restrict__ xs) {
   return a;
 }
 
-// launch shape of the row kernel: threads per block and k planes per thread
-#ifndef HHG_ROW_THREADS
-#define HHG_ROW_THREADS 128
-#endif
-#ifndef HHG_ROW_KPLANES
-#define HHG_ROW_KPLANES 2
-#endif
-constexpr int kRowThreads = HHG_ROW_THREADS;
-constexpr int kKPlanes = HHG_ROW_KPLANES;
+// launch shapes (threads per block, k planes per thread) are run-time
+// parameters chosen per level by the autotuner (hhg_autotune)
 
 // ------------------------------------------------------------- row kernels
 // grid: x over the (i, j) plane of sites (flat, i fastest), y = groups of
-// kKPlanes planes, z = row.  The row is the slowest grid dimension, so the
+// kp planes, z = row.  The row is the slowest grid dimension, so the
 // blocks resident at the same time run the same (fully unrolled) row code.
 template <int DISC, int VARNU, int OP, class T, int MODE, int OUT, int OG, int ALL, int T0, int N0, int N1, int N2,
           class Tab>
 __device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restrict__ x, const T* __restrict__ b,
-                                         T* __restrict__ y, T alpha, const OpDev& op, const Tab& tab) {
+                                         T* __restrict__ y, T alpha, const OpDev& op, const Tab& tab, int kp) {
   constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
   constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
   constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
@@ -115,10 +108,10 @@ __device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restric
   const int j = q / w;
   const int i = q - j * w;
   if (j > g.ny - oy) return;
-  const int k0 = blockIdx.y * kKPlanes;
+  const int k0 = blockIdx.y * kp;
   const bool bij = 2 * i + ox == 0 || 2 * i + ox == 2 * g.nx || 2 * j + oy == 0 || 2 * j + oy == 2 * g.ny;
 #pragma unroll 1
-  for (int k = k0; k < k0 + kKPlanes && k <= g.nz - oz; ++k) {
+  for (int k = k0; k < k0 + kp && k <= g.nz - oz; ++k) {
     const int64_t idx = fsite(g, i, j, k);
     T* yo = y + int64_t(OUT) * g.arr + idx;
     const bool bnd = bij || 2 * k + oz == 0 || 2 * k + oz == 2 * g.nz;
@@ -155,15 +148,15 @@ __device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restric
 }
 
 template <int DISC, int VARNU, int OP, class T, int MODE>
-__global__ void __launch_bounds__(kRowThreads)
-    k_rows_fast(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, T alpha, OpDev op,
+__global__ void __launch_bounds__(256)
+    k_rows_fast(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, T alpha, OpDev op, int kp,
                 const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP>::N> tab) {
   using S = gen::S<DISC, VARNU, OP>;
   dispatch<S, 0>(int(blockIdx.z), [&](auto rc) {
     constexpr int R = decltype(rc)::value;
     constexpr gen::RowS rw = S::rows[R];
     eval_row<DISC, VARNU, OP, T, MODE, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, x, b, y, alpha, op,
-                                                                                          tab);
+                                                                                          tab, kp);
   });
 }
 
@@ -204,7 +197,7 @@ __device__ __forceinline__ void gs_site(const Geo& g, T* __restrict__ u, const T
 }
 
 template <int DISC, int VARNU, int GRP, class T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
     k_gs_fast(Geo g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag, int colour,
               const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP_A>::N> tab) {
   using S = gen::S<DISC, VARNU, OP_A>;
@@ -218,29 +211,31 @@ __global__ void __launch_bounds__(128)
 // ================================================================= launchers
 template <int DISC, int VARNU, int OP, class T>
 void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, const T* x, const T* b, T* y,
-                      double alpha, cudaStream_t s) {
+                      double alpha, const Shape& sh, cudaStream_t s) {
   using S = gen::S<DISC, VARNU, OP>;
   using Tab = FastTab<T, S::N>;
   const Tab& tb = *static_cast<const Tab*>(tab);
-  dim3 blk(kRowThreads, 1, 1);
+  const int nt = sh.row_threads, kp = sh.row_kplanes;
+  dim3 blk(nt, 1, 1);
   const int plane = (g.nx + 1) * (g.ny + 1);
-  dim3 grd((plane + kRowThreads - 1) / kRowThreads, (g.nz + 1 + kKPlanes - 1) / kKPlanes, S::R);
+  dim3 grd((plane + nt - 1) / nt, (g.nz + 1 + kp - 1) / kp, S::R);
   ++g_launches;
-  if (mode == MODE_SET) k_rows_fast<DISC, VARNU, OP, T, MODE_SET><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
-  else if (mode == MODE_RES) k_rows_fast<DISC, VARNU, OP, T, MODE_RES><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
-  else k_rows_fast<DISC, VARNU, OP, T, MODE_ADD><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, tb);
+  if (mode == MODE_SET) k_rows_fast<DISC, VARNU, OP, T, MODE_SET><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+  else if (mode == MODE_RES) k_rows_fast<DISC, VARNU, OP, T, MODE_RES><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+  else k_rows_fast<DISC, VARNU, OP, T, MODE_ADD><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
 }
 
 template <int DISC, int VARNU, class T>
 void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u, const T* rhs,
-                    cudaStream_t s) {
+                    const Shape& sh, cudaStream_t s) {
   using S = gen::S<DISC, VARNU, OP_A>;
   using Tab = FastTab<T, S::N>;
   const Tab& tb = *static_cast<const Tab*>(tab);
-  dim3 blk(128, 1, 1);
+  const int nt = sh.gs_threads;
+  dim3 blk(nt, 1, 1);
   const int ni = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1;
   const int plane = ni * (g.ny + 1);
-  dim3 grd((plane + 127) / 128, 1, g.nz + 1);
+  dim3 grd((plane + nt - 1) / nt, 1, g.nz + 1);
   ++g_launches;
   switch (grp) {
     case 0: k_gs_fast<DISC, VARNU, 0, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
@@ -268,9 +263,9 @@ int fast_terms(int disc, int varnu, int op) {
 // run-time dispatch over (disc, varnu, op)
 template <class T>
 void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode, const T* x,
-               const T* b, T* y, double alpha, cudaStream_t s) {
+               const T* b, T* y, double alpha, const Shape& sh, cudaStream_t s) {
 #define HHG_R(D, V, O) \
-  if (disc == D && varnu == V && op == O) return launch_rows_fast<D, V, O, T>(g, od, tab, mode, x, b, y, alpha, s);
+  if (disc == D && varnu == V && op == O) return launch_rows_fast<D, V, O, T>(g, od, tab, mode, x, b, y, alpha, sh, s);
   HHG_R(1, 0, OP_FULL) HHG_R(1, 0, OP_BT) HHG_R(1, 0, OP_BC)
   HHG_R(1, 1, OP_FULL) HHG_R(1, 1, OP_BT) HHG_R(1, 1, OP_BC)
   HHG_R(2, 0, OP_FULL) HHG_R(2, 0, OP_BT) HHG_R(2, 0, OP_BC)
@@ -280,18 +275,20 @@ void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const
 
 template <class T>
 void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
-             const T* rhs, cudaStream_t s) {
-  if (disc == 1 && !varnu) launch_gs_fast<1, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, s);
-  else if (disc == 1) launch_gs_fast<1, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, s);
-  else if (!varnu) launch_gs_fast<2, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, s);
-  else launch_gs_fast<2, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, s);
+             const T* rhs, const Shape& sh, cudaStream_t s) {
+  if (disc == 1 && !varnu) launch_gs_fast<1, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, s);
+  else if (disc == 1) launch_gs_fast<1, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, s);
+  else if (!varnu) launch_gs_fast<2, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, s);
+  else launch_gs_fast<2, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, s);
 }
 
 template void fast_rows<double>(int, int, int, const Geo&, const OpDev&, const void*, int, const double*, const double*,
-                                double*, double, cudaStream_t);
+                                double*, double, const Shape&, cudaStream_t);
 template void fast_rows<float>(int, int, int, const Geo&, const OpDev&, const void*, int, const float*, const float*,
-                               float*, double, cudaStream_t);
-template void fast_gs<double>(int, int, const Geo&, const void*, int, int, double, double*, const double*, cudaStream_t);
-template void fast_gs<float>(int, int, const Geo&, const void*, int, int, double, float*, const float*, cudaStream_t);
+                               float*, double, const Shape&, cudaStream_t);
+template void fast_gs<double>(int, int, const Geo&, const void*, int, int, double, double*, const double*, const Shape&,
+                              cudaStream_t);
+template void fast_gs<float>(int, int, const Geo&, const void*, int, int, double, float*, const float*, const Shape&,
+                             cudaStream_t);
 
 }  // namespace hhg

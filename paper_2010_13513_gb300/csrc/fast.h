@@ -16,6 +16,13 @@ struct FastTab {
   int off[N];
 };
 
+// launch shape of the specialised kernels on one level (autotuned)
+struct Shape {
+  int row_threads = 128;   // threads per block of the row kernels (64 / 128 / 256)
+  int row_kplanes = 2;     // k planes per thread of the row kernels
+  int gs_threads = 128;    // threads per block of the Gauss-Seidel kernels
+};
+
 // number of interior terms of a specialised operator (-1 if none)
 int fast_terms(int disc, int varnu, int op);
 
@@ -23,12 +30,12 @@ int fast_terms(int disc, int varnu, int op);
 // `tab` points to a host FastTab<T, fast_terms(...)>
 template <class T>
 void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode, const T* x,
-               const T* b, T* y, double alpha, cudaStream_t s);
+               const T* b, T* y, double alpha, const Shape& sh, cudaStream_t s);
 
 // one Gauss-Seidel phase (group, colour) on the three velocity components;
 // `tab` points to a host FastTab<T, fast_terms(disc, varnu, OP_A)>
 template <class T>
 void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
-             const T* rhs, cudaStream_t s);
+             const T* rhs, const Shape& sh, cudaStream_t s);
 
 }  // namespace hhg

@@ -132,6 +132,7 @@ struct Level {
   // parameter block of the cluster-resident smoother (small levels only)
   std::vector<char> stab64, stab32;
   bool small = false;
+  Shape shape;                          // launch shapes of the specialised kernels
   // workspace offsets (bytes) of the level vectors
   size_t o_rhs, o_W, o_x64, o_tmp64, o_bw64, o_x32, o_b32, o_tmp32, o_invml, o_ml;
   double *rhs = nullptr, *W = nullptr, *x64 = nullptr, *tmp64 = nullptr, *bw64 = nullptr;
@@ -568,7 +569,7 @@ template <class T>
 int apply_op(hhg_problem* pb, Level& lv, int op, int mode, const T* x, const T* b, T* y, double alpha = 1.0) {
   if (lv.has_fast[op] && op != OP_A)
     fast_rows<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, op, lv.g, lv.op[op], ftab<T>(lv, op), mode, x, b, y,
-                 alpha, pb->stream);
+                 alpha, lv.shape, pb->stream);
   else
     launch_apply<T>(lv.g, lv.op[op], mode, x, b, y, alpha, pb->stream);
   HHG_CHECK_LAUNCH();
@@ -612,10 +613,12 @@ int uzawa(hhg_problem* pb, Level& lv, const hhg_params& prm, int sweeps, T* x, c
     const int disc = pb->desc.disc, varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
     const void* tabA = ftab<T>(lv, OP_A);
     for (int s = 0; s < prm.xi; ++s) {
-      for (auto& ph : phases) fast_gs<T>(disc, varnu, lv.g, tabA, ph.first, ph.second, lv.inv_diag[ph.first], x, tmp, pb->stream);
+      for (auto& ph : phases)
+        fast_gs<T>(disc, varnu, lv.g, tabA, ph.first, ph.second, lv.inv_diag[ph.first], x, tmp, lv.shape, pb->stream);
       if (prm.ahat == HHG_AHAT_S)
         for (auto it2 = phases.rbegin(); it2 != phases.rend(); ++it2)
-          fast_gs<T>(disc, varnu, lv.g, tabA, it2->first, it2->second, lv.inv_diag[it2->first], x, tmp, pb->stream);
+          fast_gs<T>(disc, varnu, lv.g, tabA, it2->first, it2->second, lv.inv_diag[it2->first], x, tmp, lv.shape,
+                     pb->stream);
     }
     HHG_CHECK_LAUNCH();
     // pressure step (Eq. uzawa-pressure): p -= S_hat^{-1} (g - B u_{k+1} + C p_k)
@@ -1142,6 +1145,177 @@ extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out
     stats->kernel_launches = kernels;
     if (!std::isfinite(nr[0]) || !std::isfinite(nr[1])) return fail(HHG_EDIVERGED, "FMG produced a non-finite residual");
   }
+  return HHG_OK;
+}
+
+// ================================================================ autotuner
+namespace {
+template <class T>
+int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
+  cudaEvent_t e0, e1;
+  HHG_CUDA(cudaEventCreate(&e0));
+  HHG_CUDA(cudaEventCreate(&e1));
+  auto time_it = [&](auto&& fn) {
+    for (int r = 0; r < 2; ++r) fn();
+    cudaEventRecord(e0, pb->stream);
+    for (int r = 0; r < reps; ++r) fn();
+    cudaEventRecord(e1, pb->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  const int disc = pb->desc.disc, varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
+  // row kernels: FULL residual
+  const int threads[3] = {64, 128, 256}, planes[3] = {1, 2, 4};
+  float best = 1e30f;
+  Shape bestS = lv.shape;
+  for (int t : threads)
+    for (int kp : planes) {
+      Shape sh = lv.shape;
+      sh.row_threads = t;
+      sh.row_kplanes = kp;
+      const float ms = time_it([&] {
+        fast_rows<T>(disc, varnu, OP_FULL, lv.g, lv.op[OP_FULL], ftab<T>(lv, OP_FULL), MODE_RES, xa, xa, xb, 1.0, sh,
+                     pb->stream);
+      });
+      if (ms < best) { best = ms; bestS.row_threads = t; bestS.row_kplanes = kp; }
+    }
+  // Gauss-Seidel kernels: one forward sweep
+  best = 1e30f;
+  for (int t : threads) {
+    Shape sh = bestS;
+    sh.gs_threads = t;
+    const float ms = time_it([&] {
+      for (int c = 0; c < 4; ++c) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), 0, c, 1.0, xb, xa, sh, pb->stream);
+      for (int gg = 1; gg < lv.g.G; ++gg) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), gg, -1, 1.0, xb, xa, sh, pb->stream);
+    });
+    if (ms < best) { best = ms; bestS.gs_threads = t; }
+  }
+  lv.shape = bestS;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HHG_CUDA(cudaMemsetAsync(xa, 0, size_t(lv.nvec()) * sizeof(T), pb->stream));
+  HHG_CUDA(cudaMemsetAsync(xb, 0, size_t(lv.nvec()) * sizeof(T), pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  return HHG_OK;
+}
+}  // namespace
+
+extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
+  HHG_TRY(check_level(pb, pb ? pb->desc.L : 0));
+  if (reps < 1) return fail(HHG_EINVAL, "reps must be positive");
+  const bool mixed = pb->desc.solve == HHG_SOLVE_MIXED;
+  for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l) {
+    Level& lv = pb->L(l);
+    if (mixed) HHG_TRY(tune_level<float>(pb, lv, reps, lv.tmp32, lv.b32));
+    else HHG_TRY(tune_level<double>(pb, lv, reps, lv.tmp64, lv.bw64));
+    if (shapes_out) {
+      int* o = shapes_out + 3 * (l - pb->desc.coarse_level);
+      o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
+    }
+  }
+  for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
+  pb->graphs.clear();
+  return HHG_OK;
+}
+
+// ================================================================== batches
+struct hhg_batch {
+  std::vector<hhg_problem*> pbs;
+  std::vector<cudaStream_t> streams;      // one capture stream per problem
+  std::vector<cudaEvent_t> events;        // join events
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<hhg_params> key;            // parameters the graph was recorded with
+  int64_t kernels = 0;
+  ~hhg_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto e : events) cudaEventDestroy(e);
+    for (auto s : streams) cudaStreamDestroy(s);
+    if (fork) cudaEventDestroy(fork);
+  }
+};
+
+extern "C" int hhg_batch_create(hhg_problem* const* problems, int n, hhg_batch** out) {
+  if (!problems || n < 1 || !out) return fail(HHG_EINVAL, "hhg_batch_create: bad arguments");
+  auto bt = std::make_unique<hhg_batch>();
+  for (int i = 0; i < n; ++i) {
+    hhg_problem* pb = problems[i];
+    if (!pb || !pb->bound) return fail(HHG_ESTATE, "hhg_batch_create: every problem must be bound");
+    for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l)
+      if (!pb->L(l).has_rhs) return fail(HHG_ESTATE, "hhg_batch_create: hhg_set_rhs missing on a level");
+    for (hhg_problem* q : bt->pbs)
+      if (q == pb) return fail(HHG_EINVAL, "hhg_batch_create: a problem appears twice");
+    bt->pbs.push_back(pb);
+    cudaStream_t s;
+    HHG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    bt->streams.push_back(s);
+    cudaEvent_t e;
+    HHG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    bt->events.push_back(e);
+  }
+  HHG_CUDA(cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming));
+  *out = bt.release();
+  return HHG_OK;
+}
+
+extern "C" int hhg_batch_destroy(hhg_batch* bt) {
+  delete bt;
+  return HHG_OK;
+}
+
+namespace {
+bool same_params(const std::vector<hhg_params>& a, const hhg_params* b) {
+  for (size_t i = 0; i < a.size(); ++i)
+    if (a[i].nu_pre != b[i].nu_pre || a[i].nu_post != b[i].nu_post || a[i].nu_inc != b[i].nu_inc ||
+        a[i].kappa != b[i].kappa || a[i].ahat != b[i].ahat || a[i].xi != b[i].xi || a[i].omega_inv != b[i].omega_inv)
+      return false;
+  return true;
+}
+}  // namespace
+
+extern "C" int hhg_batch_fmg_solve(hhg_batch* bt, const hhg_params* params, void* stream, int64_t* kernels) {
+  if (!bt || !params) return fail(HHG_EINVAL, "hhg_batch_fmg_solve: null argument");
+  const int n = int(bt->pbs.size());
+  for (int i = 0; i < n; ++i) HHG_TRY(check_params(&params[i]));
+  cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+  if (!bt->exec || !same_params(bt->key, params)) {
+    if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
+    // record every problem's FMG on its own branch of one graph
+    cudaStream_t cap = bt->streams[0];
+    const int64_t l0 = g_launches;
+    HHG_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    int rc = HHG_OK;
+    cudaError_t ce = cudaEventRecord(bt->fork, cap);
+    for (int i = 0; i < n && rc == HHG_OK && ce == cudaSuccess; ++i) {
+      hhg_problem* pb = bt->pbs[i];
+      if (i > 0) ce = cudaStreamWaitEvent(bt->streams[i], bt->fork, 0);
+      if (ce != cudaSuccess) break;
+      cudaStream_t keep = pb->stream;
+      pb->stream = bt->streams[i];
+      rc = fmg_core(pb, &params[i]);
+      pb->stream = keep;
+      if (i > 0 && rc == HHG_OK) {
+        ce = cudaEventRecord(bt->events[i], bt->streams[i]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, bt->events[i], 0);
+      }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+    if (rc != HHG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(HHG_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    cudaError_t ei = cudaGraphInstantiate(&bt->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(HHG_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(ei));
+    bt->key.assign(params, params + n);
+    bt->kernels = g_launches - l0;
+  }
+  HHG_CUDA(cudaGraphLaunch(bt->exec, s0));
+  if (kernels) *kernels = bt->kernels;
   return HHG_OK;
 }
 

@@ -92,6 +92,10 @@ def load():
         "hhg_set_small_level_mode": [P, I],
         "hhg_error_norms": [P, I, VP, DP, DP, DP, DP],
         "hhg_block_norms_noalloc": [VP, I, C.c_int64, C.c_int64, VP, VP],
+        "hhg_batch_create": [C.POINTER(P), I, C.POINTER(P)],
+        "hhg_autotune": [P, I, C.POINTER(C.c_int)],
+        "hhg_batch_destroy": [P],
+        "hhg_batch_fmg_solve": [P, C.POINTER(Params), VP, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -265,6 +269,13 @@ class Problem:
     def set_graph_mode(self, on):
         _check(load().hhg_set_graph_mode(self.h, int(on)), "hhg_set_graph_mode")
 
+    def autotune(self, reps=5):
+        """Per-level launch shapes; returns {level: (row_threads, row_kplanes, gs_threads)}."""
+        n = self.L - self.lc + 1
+        out = (C.c_int * (3 * n))()
+        _check(load().hhg_autotune(self.h, reps, out), "hhg_autotune")
+        return {self.lc + i: tuple(out[3 * i:3 * i + 3]) for i in range(n)}
+
     def set_small_level_mode(self, on):
         _check(load().hhg_set_small_level_mode(self.h, int(on)), "hhg_set_small_level_mode")
 
@@ -281,6 +292,31 @@ class Problem:
         _check(load().hhg_error_norms(self.h, level, _ptr(x), _dp(u), _dp(p), C.byref(eu), C.byref(ep)),
                "hhg_error_norms")
         return eu.value, ep.value
+
+
+class Batch:
+    """Independent problems solved by one CUDA graph with one branch per problem."""
+
+    def __init__(self, problems):
+        lib = load()
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        h = C.c_void_p()
+        _check(lib.hhg_batch_create(arr, len(self.problems), C.byref(h)), "hhg_batch_create")
+        self.h = h
+
+    def fmg_solve(self, params, stream=None):
+        stream = stream if stream is not None else torch.cuda.current_stream()
+        prm = (Params * len(params))(*params)
+        k = C.c_int64()
+        _check(load().hhg_batch_fmg_solve(self.h, prm, C.c_void_p(stream.cuda_stream), C.byref(k)),
+               "hhg_batch_fmg_solve")
+        return k.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hhg_batch_destroy(self.h)
+            self.h = None
 
 
 # --------------------------------------------------------------- helpers

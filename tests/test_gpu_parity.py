@@ -265,3 +265,49 @@ def test_cluster_smoother_matches_per_phase_launches(disc, L, lc, solve, ahat):
     pb.fmg_solve(prm, x2, stats=False)
     torch.cuda.synchronize()
     assert rel(x1.cpu().numpy(), x2.cpu().numpy()) < 1e-13
+
+
+def test_batch_graph_matches_individual_solves():
+    """A batch of uneven problems (P1-P1 / P2-P1, different boxes and
+    levels) solved by one graph with one branch per problem gives exactly the
+    individual FMG results."""
+    from hhg_inputs import Workload
+    from paper_2010_13513_gb300 import hhg
+    stream = torch.cuda.Stream()
+    specs = [("P1P1", (1, 1, 1), 3, 0, "fp64"), ("P2P1", (2, 1, 1), 3, 1, "mixed"),
+             ("P1P1", (1, 2, 2), 2, 0, "mixed"), ("P2P1", (1, 1, 1), 2, 1, "fp64")]
+    pbs, prms, refs = [], [], []
+    with torch.cuda.stream(stream):
+        for i, (disc, box, L, lc, solve) in enumerate(specs):
+            wl = Workload("modes", seed=100 + i, box=box, H=1.0 / max(box))
+            pb = lib_problem(box, L, disc, lc=lc, solve=solve, workload=wl)
+            prm = hhg.Params.make(1, 2, 1, 1, "f", 2, OMEGA_INV[disc])
+            x = pb.new_vector(L)
+            pb.fmg_solve(prm, x, stats=False)
+            pbs.append(pb)
+            prms.append(prm)
+            refs.append(x.clone())
+        batch = hhg.Batch(pbs)
+        for rep in range(2):
+            k = batch.fmg_solve(prms, stream)
+        stream.synchronize()
+    assert k > 0
+    for pb, ref in zip(pbs, refs):
+        got = pb.level_vector(pb.L, "x")
+        assert torch.equal(got, ref)
+
+
+def test_autotune_keeps_results():
+    from paper_2010_13513_gb300 import hhg
+    pb = lib_problem((1, 1, 1), 4, "P2P1", lc=1, solve="mixed", workload=curl_workload())
+    prm = hhg.Params.make(1, 3, 2, 1, "f", 3, 0.3)
+    x1 = pb.new_vector(4)
+    pb.fmg_solve(prm, x1, stats=False)
+    shapes = pb.autotune(reps=2)
+    assert set(shapes) == {1, 2, 3, 4}
+    for t, kp, gs in shapes.values():
+        assert t in (64, 128, 256) and kp in (1, 2, 4) and gs in (64, 128, 256)
+    x2 = pb.new_vector(4)
+    pb.fmg_solve(prm, x2, stats=False)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)
