@@ -221,6 +221,86 @@ def cpu_baseline(prm_dict, level=CPU_SAMPLE_LEVEL):
             "sample": f"{w['disc']} 6-tet cube level {level} ({dofs} DoF), FMG {n}x, {dt:.2f} s each, single-threaded numpy/scipy"}
 
 
+def run_batched(args):
+    """The batched workload: 64 independent problems (Kuhn boxes {1,2}^3,
+    levels 3..6, P1-P1 / P2-P1, random smooth forcing, zero Dirichlet data)
+    solved by one CUDA graph with one branch per problem, against the same
+    problems solved one after another (each with its own graph)."""
+    import torch
+    from hhg_inputs import Workload, batched_problem_list
+    from paper_2010_13513_gb300 import hhg
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    specs = batched_problem_list(0)
+    pbs, prms, dofs = [], [], 0
+    t_setup = time.perf_counter()
+    for sp in specs:
+        lc = 0 if sp["disc"] == "P1P1" else 1
+        H = 1.0 / max(sp["box"])
+        pb = hhg.Problem(hhg.Mesh.box(*sp["box"], H), disc=sp["disc"], L=sp["level"], coarse_level=lc, solve="mixed")
+        hhg.set_workload_rhs(pb, Workload("modes", seed=sp["seed"], box=sp["box"], H=H))
+        pb.autotune(reps=2)
+        info = pb.layout(sp["level"])
+        om = pb.estimate_omega(sp["level"], np.random.default_rng(sp["seed"]).uniform(-1, 1, info.n_pressure_nodes), 30)
+        s = dict(nu_pre=2, nu_post=3, nu_inc=2, kappa=1, ahat="s", xi=1) if sp["disc"] == "P1P1" else PARAMS
+        prms.append(hhg.Params.make(**s, omega_inv=om))
+        pbs.append(pb)
+        dofs += info.n_dofs
+    t_setup = time.perf_counter() - t_setup
+    batch = hhg.Batch(pbs)
+    kernels = batch.fmg_solve(prms, stream)
+    for pb, prm in zip(pbs, prms):
+        pb.fmg_solve(prm, None, stats=False)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(reps):
+            fn()
+        e.record(stream)
+        e.synchronize()
+        return s.elapsed_time(e) / reps * 1e-3
+
+    sampler = ClockSampler(0)
+    t_batch = timed(lambda: batch.fmg_solve(prms, stream), args.steps)
+    t_seq = timed(lambda: [pb.fmg_solve(prm, None, stats=False) for pb, prm in zip(pbs, prms)], max(1, args.steps // 2))
+    clocks = sampler.stop()
+    # accuracy of a few problems: delta against the discrete solution (Eq. relative-error)
+    deltas = []
+    for idx in (0, 1, 2):
+        pb, prm = pbs[idx], prms[idx]
+        L = pb.L
+        x = pb.level_vector(L, "x").clone()
+        xs = x.clone()
+        b = pb.level_vector(L, "rhs")
+        r = pb.new_vector(L)
+        for _ in range(300):
+            pb.vcycle(L, prm, xs, b)
+            if max(pb.residual(L, xs, b, r, norms=True)) < 1e-12:
+                break
+        info = pb.layout(L)
+        po = 3 * info.groups * info.array_elems
+        du = float(torch.linalg.norm(x[:po] - xs[:po]) / torch.linalg.norm(xs[:po]))
+        dp = float(torch.linalg.norm(x[po:] - xs[po:]) / torch.linalg.norm(xs[po:]))
+        deltas.append({"problem": idx, "disc": specs[idx]["disc"], "level": specs[idx]["level"], "delta_u": du,
+                       "delta_p": dp})
+    line = {"metric": "batched FMG-solved Stokes DoF/s", "value": dofs / t_batch, "unit": "DoF/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "64 independent Stokes problems: Kuhn boxes {1,2}^3, levels 3..6, P1-P1 and P2-P1, "
+                                   "random smooth forcing (8 sine modes per component), zero Dirichlet data",
+                       "dofs": dofs, "problems": len(pbs), "graph_kernels": kernels, "setup_s": t_setup,
+                       "sequential_ms": t_seq * 1e3, "batch_speedup_vs_sequential": t_seq / t_batch,
+                       "accuracy": deltas},
+            "clocks": clocks}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -257,11 +337,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hhg", choices=["hhg", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="p2-l6", choices=["p2-l6", "batched"])
     ap.add_argument("--profile-region", action="store_true",
                     help="only set-up, warm-up and the timed FMG steps, bracketed by cudaProfilerStart/Stop")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import torch
     import torch.distributed as dist
