@@ -103,6 +103,9 @@ typedef struct {
     double nu_a;         /* viscosity nu = exp(nu_a * z); 0 gives nu = 1                  */
     int pspg_rhs;        /* 1: consistent PSPG load term in g (P1-P1 only)                */
     int error_level;     /* 1: also set up level L+1 for hhg_error_norms                   */
+    int nn_hidden;       /* learned coarse correction: hidden width (0 = none)             */
+    int nn_samples;      /* training pairs held in the workspace                           */
+    int nn_batch;        /* training mini-batch                                            */
 } hhg_problem_desc;
 
 typedef struct {
@@ -211,6 +214,58 @@ int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats
  * graphs are dropped.  shapes_out (optional) receives 3 ints per level
  * (coarse .. L).  Synchronises. */
 int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
+
+/* ------------------------------------------- learned coarse-grid correction */
+/* Not in the paper: a small MLP  y = W3 relu(W2 relu(W1 x + b1) + b2) + b3
+ * (hidden width nn_hidden) maps the coarse defect, restricted to the coarse
+ * unknowns and scaled to unit norm, to the scaled coarse correction.  It is
+ * trained on the GPU by the library's own forward/backward kernels and Adam
+ * on pairs (r, Z r) whose targets come from the plain coarse solver Z.  In the
+ * V-cycle it replaces the coarse solve only when its residual passes the gate
+ * ||b - calA_c x_nn|| <= theta ||b||; otherwise the plain solve runs. */
+typedef struct {
+    int epochs, batch;
+    double lr;
+    int n_train;               /* pairs used (<= nn_samples; the rest validates) */
+    uint64_t seed;             /* counter-based generator of the random defects */
+    int recorded;              /* 1: the defects recorded by hhg_coarse_nn_record come first, random
+                                  defects fill the remaining samples; 0: random defects only */
+    double smooth_frac;        /* probability of a smooth defect (random low-wavenumber sine modes per
+                                  field, like restricted V-cycle residuals); the rest uniform random */
+} hhg_nn_cfg;
+
+typedef struct {
+    int n;                     /* coarse unknowns (network input/output width)  */
+    int64_t n_params;
+    double loss_first, loss_last;      /* mean squared error, training set      */
+    double val_rel_err;        /* mean ||y - t|| / ||t|| on the validation pairs */
+    double train_ms;
+} hhg_nn_report;
+
+/* network width n and parameter count of a problem created with nn_hidden > 0 */
+int hhg_coarse_nn_size(const hhg_problem* pb, int* n, int64_t* n_params);
+/* parameters, flat FP32 [W1 (h x n), b1, W2 (h x h), b2, W3 (n x h), b3],
+ * row-major; host arrays */
+int hhg_coarse_nn_set_params(hhg_problem* pb, const float* params);
+int hhg_coarse_nn_get_params(hhg_problem* pb, float* params);
+/* loss and gradients (same flat order) of the mean squared error over a batch
+ * X, T (B x n, host, B <= nn_batch) at the current parameters */
+int hhg_coarse_nn_grad(hhg_problem* pb, const float* X, const float* T, int B, double* loss, float* grads);
+/* trains from the current parameters: nn_samples random unit defects (pressure
+ * part with zero lumped-mass mean) from cfg->seed, targets by the plain
+ * coarse solve; the last nn_samples - n_train pairs validate.  Synchronises. */
+int hhg_coarse_nn_train(hhg_problem* pb, const hhg_nn_cfg* cfg, hhg_nn_report* report);
+/* While on, every coarse solve appends its defect (restricted to the coarse
+ * unknowns, scaled to unit norm) to the training samples, up to nn_samples
+ * (turning it on restarts the count).  *recorded (optional) receives the
+ * count.  Drops cached graphs. */
+int hhg_coarse_nn_record(hhg_problem* pb, int on, int64_t* recorded);
+/* mode 0: plain coarse solve; 1: learned correction gated by theta; 2: learned
+ * correction always; 3: no coarse correction at all (2 and 3 are comparison
+ * modes for measurements).  Drops cached graphs. */
+int hhg_coarse_nn_enable(hhg_problem* pb, int mode, double theta);
+/* accepted / rejected learned corrections since the last call (resets) */
+int hhg_coarse_nn_counts(hhg_problem* pb, int64_t* accepted, int64_t* rejected);
 
 /* ------------------------------------------------------------------ batches */
 /* A batch of n independent problems (each bound, with its rhs set on every

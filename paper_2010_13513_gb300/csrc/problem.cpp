@@ -16,6 +16,7 @@
 #include "fast.h"
 #include "internal.h"
 #include "kernels.h"
+#include "nn.h"
 #include "small.h"
 
 using namespace hhg;
@@ -170,6 +171,21 @@ struct hhg_problem {
   // CUDA graphs of whole FMG solves, keyed by the parameter tuple
   bool use_graphs = true;
   bool use_cluster = true;       // cluster-resident smoother on small levels
+  // learned coarse correction
+  int nn_n = 0, nn_h = 0, nn_S = 0, nn_B = 0, nn_mode = 0;
+  int64_t nn_P = 0;
+  double nn_theta = 0.1;
+  size_t o_nn = 0;
+  float *nn_params = nullptr, *nn_grads = nullptr, *nn_m = nullptr, *nn_v = nullptr, *nn_Z = nullptr;
+  float *nn_X = nullptr, *nn_T = nullptr, *nn_H1 = nullptr, *nn_H2 = nullptr, *nn_Y = nullptr, *nn_dY = nullptr;
+  float *nn_dH1 = nullptr, *nn_dH2 = nullptr, *nn_xin = nullptr, *nn_h1 = nullptr, *nn_h2 = nullptr, *nn_y = nullptr;
+  double *nn_mlp = nullptr, *nn_scal = nullptr, *nn_part = nullptr;
+  float* nn_xyz = nullptr;       // coordinates and field of each coarse unknown (float4)
+  unsigned long long* nn_counts = nullptr;
+  int nn_step = 0;
+  bool nn_recording = false;     // coarse solves append their defects to the samples
+  double nn_tscale = 1.0;        // training targets are multiplied by this (unit RMS)
+
   struct Graph { cudaGraphExec_t exec; int64_t kernels; double wu; };
   std::map<std::tuple<int, int, int, int, int, int, double>, Graph> graphs;
 
@@ -401,6 +417,17 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
   pb->o_idx = off; off += align256(size_t(pb->ncoarse) * 8);
   pb->o_part = off; off += align256(size_t(pb->max_blocks) * 8);
   pb->o_scal = off; off += align256(64 * 8);
+  if (desc->nn_hidden > 0) {
+    if (desc->nn_samples < 2 || desc->nn_batch < 1) return fail(HHG_EINVAL, "nn_samples >= 2 and nn_batch >= 1 needed");
+    const int n = pb->ncoarse, h = desc->nn_hidden;
+    pb->nn_n = n; pb->nn_h = h; pb->nn_S = desc->nn_samples; pb->nn_B = desc->nn_batch;
+    pb->nn_P = int64_t(h) * n + h + int64_t(h) * h + h + int64_t(n) * h + n;
+    const int64_t B = std::max(desc->nn_batch, 1);
+    const int64_t floats = 4 * pb->nn_P + int64_t(n) * n + 2 * int64_t(pb->nn_S) * n + 4 * B * h + 2 * B * n +
+                           6 * int64_t(n) + 2 * int64_t(h) + 4;
+    pb->o_nn = off;
+    off += align256(size_t(floats) * 4) + align256(size_t(n) * 8) + align256(64 * 8) + align256(1024 * 8) + 256;
+  }
   pb->total = off;
   *out = pb.release();
   return HHG_OK;
@@ -651,10 +678,18 @@ int prolong_add(hhg_problem* pb, int l, const T* xc, T* xf, bool velocity_interi
   return HHG_OK;
 }
 
+template <class T> int coarse_nn(hhg_problem* pb, const T* b, T* x);
+
 template <class T>
 int coarse_solve(hhg_problem* pb, const T* b, T* x) {
   Level& lv = pb->lv[0];
   HHG_CUDA(cudaMemsetAsync(x, 0, size_t(lv.nvec()) * sizeof(T), pb->stream));
+  if (pb->nn_recording) {
+    nn_gather<T>(b, pb->cidx, pb->nn_n, pb->nn_xin, pb->nn_scal, pb->stream);
+    nn_record(pb->nn_xin, pb->nn_X, pb->nn_n, pb->nn_S, pb->nn_counts + 2, pb->stream);
+  }
+  if (pb->nn_mode == 3) return HHG_OK;            // comparison mode: no coarse correction
+  if (pb->nn_mode != 0) return coarse_nn<T>(pb, b, x);
   launch_coarse<T>(pb->Z, pb->ncoarse, pb->cidx, b, x, pb->stream);
   HHG_CHECK_LAUNCH();
   return HHG_OK;
@@ -814,6 +849,122 @@ int build_coarse(hhg_problem* pb) {
   return HHG_OK;
 }
 
+// ------------------------------------------------ learned coarse correction
+// forward pass of the MLP on a batch X (B x n) into H1, H2 (B x h) and Y (B x n)
+void nn_forward(hhg_problem* pb, const float* X, int B, float* H1, float* H2, float* Y) {
+  const int n = pb->nn_n, h = pb->nn_h;
+  const float* W1 = pb->nn_params;
+  const float* b1 = W1 + int64_t(h) * n;
+  const float* W2 = b1 + h;
+  const float* b2 = W2 + int64_t(h) * h;
+  const float* W3 = b2 + h;
+  const float* b3 = W3 + int64_t(n) * h;
+  nn_gemm(false, true, B, h, n, 1.f, X, n, W1, n, 0.f, H1, h, pb->stream);
+  nn_bias_act(H1, b1, B, h, true, pb->stream);
+  nn_gemm(false, true, B, h, h, 1.f, H1, h, W2, h, 0.f, H2, h, pb->stream);
+  nn_bias_act(H2, b2, B, h, true, pb->stream);
+  nn_gemm(false, true, B, n, h, 1.f, H2, h, W3, h, 0.f, Y, n, pb->stream);
+  nn_bias_act(Y, b3, B, n, false, pb->stream);
+}
+
+// back-propagation of mean((Y - T)^2): gradients into nn_grads (same layout as the parameters)
+void nn_backward(hhg_problem* pb, const float* X, const float* T, int B) {
+  const int n = pb->nn_n, h = pb->nn_h;
+  const float* W2 = pb->nn_params + int64_t(h) * n + h;
+  const float* W3 = W2 + int64_t(h) * h + h;
+  float* gW1 = pb->nn_grads;
+  float* gb1 = gW1 + int64_t(h) * n;
+  float* gW2 = gb1 + h;
+  float* gb2 = gW2 + int64_t(h) * h;
+  float* gW3 = gb2 + h;
+  float* gb3 = gW3 + int64_t(n) * h;
+  nn_mse(pb->nn_Y, T, int64_t(B) * n, 1.f / float(int64_t(B) * n), pb->nn_dY, pb->nn_part, pb->stream);
+  nn_gemm(true, false, n, h, B, 1.f, pb->nn_dY, n, pb->nn_H2, h, 0.f, gW3, h, pb->stream);
+  nn_colsum(pb->nn_dY, B, n, gb3, pb->stream);
+  nn_gemm(false, false, B, h, n, 1.f, pb->nn_dY, n, W3, h, 0.f, pb->nn_dH2, h, pb->stream);
+  nn_relu_back(pb->nn_dH2, pb->nn_H2, int64_t(B) * h, pb->stream);
+  nn_gemm(true, false, h, h, B, 1.f, pb->nn_dH2, h, pb->nn_H1, h, 0.f, gW2, h, pb->stream);
+  nn_colsum(pb->nn_dH2, B, h, gb2, pb->stream);
+  nn_gemm(false, false, B, h, h, 1.f, pb->nn_dH2, h, W2, h, 0.f, pb->nn_dH1, h, pb->stream);
+  nn_relu_back(pb->nn_dH1, pb->nn_H1, int64_t(B) * h, pb->stream);
+  nn_gemm(true, false, h, n, B, 1.f, pb->nn_dH1, h, X, n, 0.f, gW1, n, pb->stream);
+  nn_colsum(pb->nn_dH1, B, h, gb1, pb->stream);
+}
+
+int nn_setup(hhg_problem* pb) {
+  const int n = pb->nn_n, h = pb->nn_h;
+  Level& c = pb->lv[0];
+  // FP32 copy of the coarse inverse and lumped masses of the pressure unknowns
+  nn_to_float(pb->Z, pb->nn_Z, int64_t(n) * n, pb->stream);
+  std::vector<int64_t> idx(n);
+  HHG_CUDA(cudaMemcpyAsync(idx.data(), pb->cidx, size_t(n) * 8, cudaMemcpyDeviceToHost, pb->stream));
+  std::vector<double> ml(size_t(c.g.arr));
+  HHG_CUDA(cudaMemcpyAsync(ml.data(), c.ml, ml.size() * 8, cudaMemcpyDeviceToHost, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  const int64_t po = p_offset(c);
+  int nu = 0;
+  while (nu < n && idx[nu] < po) ++nu;
+  std::vector<double> mlp(size_t(n - nu));
+  for (int i = nu; i < n; ++i) mlp[size_t(i - nu)] = ml[size_t(idx[i] - po)];
+  HHG_CUDA(cudaMemcpyAsync(pb->nn_mlp, mlp.data(), mlp.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  // coordinates of the unknowns: array a = field * G + group (velocity) or 3G (pressure)
+  std::vector<float> xyz(size_t(4) * n);
+  const Geo& gc = c.g;
+  for (int i = 0; i < n; ++i) {
+    const int64_t a = idx[i] / gc.arr, site = idx[i] % gc.arr;
+    const int64_t kk = site / gc.sy - 1, jj = (site % gc.sy) / gc.sx - 1, ii = site % gc.sx - 1;
+    int field, grp;
+    if (a < 3 * gc.G) { field = int(a / gc.G); grp = int(a % gc.G); }
+    else { field = 3; grp = 0; }
+    const int* o = kGroupOff[gc.G == 1 ? 0 : grp];
+    xyz[size_t(4) * i + 0] = float((2 * ii + o[0]) * 0.5 * gc.h);
+    xyz[size_t(4) * i + 1] = float((2 * jj + o[1]) * 0.5 * gc.h);
+    xyz[size_t(4) * i + 2] = float((2 * kk + o[2]) * 0.5 * gc.h);
+    xyz[size_t(4) * i + 3] = float(field);
+  }
+  HHG_CUDA(cudaMemcpyAsync(pb->nn_xyz, xyz.data(), xyz.size() * 4, cudaMemcpyHostToDevice, pb->stream));
+  // He-style initial weights (fixed seed); Adam moments zero
+  std::vector<float> P(size_t(pb->nn_P), 0.f);
+  uint64_t st = 0x5EEDull;
+  auto unif = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return (double((st >> 11) & ((1ull << 53) - 1)) + 0.5) / double(1ull << 53);
+  };
+  auto gauss = [&]() { return std::sqrt(-2.0 * std::log(unif())) * std::cos(6.283185307179586 * unif()); };
+  size_t o = 0;
+  for (int64_t i = 0; i < int64_t(h) * n; ++i) P[o++] = float(gauss() * std::sqrt(2.0 / n));
+  o += h;
+  for (int64_t i = 0; i < int64_t(h) * h; ++i) P[o++] = float(gauss() * std::sqrt(2.0 / h));
+  o += h;
+  for (int64_t i = 0; i < int64_t(n) * h; ++i) P[o++] = float(gauss() * std::sqrt(1.0 / h));
+  HHG_CUDA(cudaMemcpyAsync(pb->nn_params, P.data(), P.size() * 4, cudaMemcpyHostToDevice, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(pb->nn_m, 0, size_t(pb->nn_P) * 4, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(pb->nn_v, 0, size_t(pb->nn_P) * 4, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(pb->nn_counts, 0, 32, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  HHG_CHECK_LAUNCH();
+  pb->nn_step = 0;
+  return HHG_OK;
+}
+
+// learned coarse correction with the gate of hhg_coarse_nn_enable; x must be zero
+template <class T>
+int coarse_nn(hhg_problem* pb, const T* b, T* x) {
+  const int n = pb->nn_n;
+  nn_gather<T>(b, pb->cidx, n, pb->nn_xin, pb->nn_scal, pb->stream);
+  nn_forward(pb, pb->nn_xin, 1, pb->nn_h1, pb->nn_h2, pb->nn_y);
+  nn_scatter<T>(pb->nn_y, pb->cidx, n, pb->nn_scal, 1.0 / pb->nn_tscale, x, pb->stream);
+  if (pb->nn_mode == 1) {
+    Level& c = pb->lv[0];
+    T* r = vt<T>(c);
+    launch_apply<T>(c.g, c.op[OP_FULL], MODE_RES, x, b, r, 1.0, pb->stream);
+    launch_reduce<T>(RED_SQ, r, nullptr, nullptr, c.nvec(), pb->partials, pb->max_blocks, pb->nn_scal + 1, pb->stream);
+    nn_fallback<T>(pb->Z, n, pb->cidx, b, x, pb->nn_scal, pb->nn_theta, pb->nn_counts, pb->stream);
+  }
+  HHG_CHECK_LAUNCH();
+  return HHG_OK;
+}
+
 }  // namespace
 
 extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, void* stream) {
@@ -872,6 +1023,25 @@ extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, 
   pb->cidx = reinterpret_cast<int64_t*>(ws + pb->o_idx);
   pb->partials = reinterpret_cast<double*>(ws + pb->o_part);
   pb->scal = reinterpret_cast<double*>(ws + pb->o_scal);
+  if (pb->nn_h > 0) {
+    const int n = pb->nn_n, h = pb->nn_h;
+    const int64_t B = pb->nn_B;
+    float* f = reinterpret_cast<float*>(ws + pb->o_nn);
+    auto take = [&](int64_t cnt) { float* r = f; f += cnt; return r; };
+    pb->nn_params = take(pb->nn_P); pb->nn_grads = take(pb->nn_P); pb->nn_m = take(pb->nn_P); pb->nn_v = take(pb->nn_P);
+    pb->nn_Z = take(int64_t(n) * n);
+    pb->nn_X = take(int64_t(pb->nn_S) * n); pb->nn_T = take(int64_t(pb->nn_S) * n);
+    pb->nn_H1 = take(B * h); pb->nn_H2 = take(B * h); pb->nn_dH1 = take(B * h); pb->nn_dH2 = take(B * h);
+    pb->nn_Y = take(B * n); pb->nn_dY = take(B * n);
+    pb->nn_xin = take(n); pb->nn_y = take(n); pb->nn_h1 = take(h); pb->nn_h2 = take(h);
+    f = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(f) + 15) / 16 * 16);
+    pb->nn_xyz = take(4 * int64_t(n));
+    char* c = reinterpret_cast<char*>(ws + pb->o_nn) + align256(size_t(f - reinterpret_cast<float*>(ws + pb->o_nn)) * 4);
+    pb->nn_mlp = reinterpret_cast<double*>(c); c += align256(size_t(n) * 8);
+    pb->nn_scal = reinterpret_cast<double*>(c); c += align256(64 * 8);
+    pb->nn_part = reinterpret_cast<double*>(c); c += align256(1024 * 8);
+    pb->nn_counts = reinterpret_cast<unsigned long long*>(c);
+  }
   // zero all vectors (halo and padding stay zero for the lifetime of the problem)
   HHG_CUDA(cudaMemsetAsync(ws + pb->lv[0].o_rhs, 0, pb->o_Z - pb->lv[0].o_rhs, pb->stream));
   pb->bound = true;
@@ -894,6 +1064,7 @@ extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, 
     HHG_CUDA(cudaMemsetAsync(lv.bw64, 0, size_t(lv.nvec()) * 8, pb->stream));
   }
   HHG_TRY(build_coarse(pb));
+  if (pb->nn_h > 0) HHG_TRY(nn_setup(pb));
   Level& c = pb->lv[0];
   HHG_CUDA(cudaMemsetAsync(c.tmp64, 0, size_t(c.nvec()) * 8, pb->stream));
   HHG_CUDA(cudaMemsetAsync(c.bw64, 0, size_t(c.nvec()) * 8, pb->stream));
@@ -1145,6 +1316,192 @@ extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out
     stats->kernel_launches = kernels;
     if (!std::isfinite(nr[0]) || !std::isfinite(nr[1])) return fail(HHG_EDIVERGED, "FMG produced a non-finite residual");
   }
+  return HHG_OK;
+}
+
+// ================================================ learned coarse correction API
+namespace {
+int check_nn(const hhg_problem* pb) {
+  if (!pb) return fail(HHG_EINVAL, "null problem");
+  if (pb->nn_h <= 0) return fail(HHG_ESTATE, "problem created without nn_hidden");
+  if (!pb->bound) return fail(HHG_ESTATE, "problem has no workspace bound");
+  return HHG_OK;
+}
+}  // namespace
+
+extern "C" int hhg_coarse_nn_size(const hhg_problem* pb, int* n, int64_t* n_params) {
+  if (!pb || !n || !n_params) return fail(HHG_EINVAL, "null argument");
+  if (pb->nn_h <= 0) return fail(HHG_ESTATE, "problem created without nn_hidden");
+  *n = pb->nn_n;
+  *n_params = pb->nn_P;
+  return HHG_OK;
+}
+
+extern "C" int hhg_coarse_nn_set_params(hhg_problem* pb, const float* params) {
+  HHG_TRY(check_nn(pb));
+  if (!params) return fail(HHG_EINVAL, "null params");
+  HHG_CUDA(cudaMemcpyAsync(pb->nn_params, params, size_t(pb->nn_P) * 4, cudaMemcpyHostToDevice, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(pb->nn_m, 0, size_t(pb->nn_P) * 4, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(pb->nn_v, 0, size_t(pb->nn_P) * 4, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  pb->nn_step = 0;
+  return HHG_OK;
+}
+
+extern "C" int hhg_coarse_nn_get_params(hhg_problem* pb, float* params) {
+  HHG_TRY(check_nn(pb));
+  if (!params) return fail(HHG_EINVAL, "null params");
+  HHG_CUDA(cudaMemcpyAsync(params, pb->nn_params, size_t(pb->nn_P) * 4, cudaMemcpyDeviceToHost, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  return HHG_OK;
+}
+
+extern "C" int hhg_coarse_nn_grad(hhg_problem* pb, const float* X, const float* T, int B, double* loss, float* grads) {
+  HHG_TRY(check_nn(pb));
+  if (!X || !T || !loss || !grads || B < 1 || B > pb->nn_B || B > pb->nn_S)
+    return fail(HHG_EINVAL, "hhg_coarse_nn_grad: bad arguments (1 <= B <= nn_batch)");
+  const int n = pb->nn_n;
+  HHG_CUDA(cudaMemcpyAsync(pb->nn_X, X, size_t(B) * n * 4, cudaMemcpyHostToDevice, pb->stream));
+  HHG_CUDA(cudaMemcpyAsync(pb->nn_T, T, size_t(B) * n * 4, cudaMemcpyHostToDevice, pb->stream));
+  nn_forward(pb, pb->nn_X, B, pb->nn_H1, pb->nn_H2, pb->nn_Y);
+  nn_backward(pb, pb->nn_X, pb->nn_T, B);
+  const int nb = nn_mse(pb->nn_Y, pb->nn_T, int64_t(B) * n, 0.f, nullptr, pb->nn_part, pb->stream);
+  HHG_CHECK_LAUNCH();
+  std::vector<double> part(static_cast<size_t>(nb));
+  HHG_CUDA(cudaMemcpyAsync(part.data(), pb->nn_part, part.size() * 8, cudaMemcpyDeviceToHost, pb->stream));
+  HHG_CUDA(cudaMemcpyAsync(grads, pb->nn_grads, size_t(pb->nn_P) * 4, cudaMemcpyDeviceToHost, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  double sum = 0.0;
+  for (double v : part) sum += v;
+  *loss = sum / (double(B) * n);
+  return HHG_OK;
+}
+
+extern "C" int hhg_coarse_nn_train(hhg_problem* pb, const hhg_nn_cfg* cfg, hhg_nn_report* rep) {
+  HHG_TRY(check_nn(pb));
+  if (!cfg || cfg->epochs < 1 || cfg->batch < 1 || cfg->batch > pb->nn_B || cfg->n_train < 1 ||
+      cfg->n_train >= pb->nn_S || !(cfg->lr > 0) || cfg->smooth_frac < 0 || cfg->smooth_frac > 1)
+    return fail(HHG_EINVAL, "hhg_coarse_nn_train: bad configuration (batch <= nn_batch, n_train < nn_samples)");
+  const int n = pb->nn_n, S = pb->nn_S;
+  cudaEvent_t e0, e1;
+  HHG_CUDA(cudaEventCreate(&e0));
+  HHG_CUDA(cudaEventCreate(&e1));
+  HHG_CUDA(cudaEventRecord(e0, pb->stream));
+  // random unit defects and the plain coarse solve of each: T = X Z^T
+  const int nu = n - int((pb->lv[0].g.nx + 1) * int64_t(pb->lv[0].g.ny + 1) * (pb->lv[0].g.nz + 1));
+  int R = 0;                                       // recorded defects kept in samples [0, R)
+  if (cfg->recorded) {
+    unsigned long long cnt = 0;
+    HHG_CUDA(cudaMemcpyAsync(&cnt, pb->nn_counts + 2, 8, cudaMemcpyDeviceToHost, pb->stream));
+    HHG_CUDA(cudaStreamSynchronize(pb->stream));
+    R = int(std::min<unsigned long long>(cnt, unsigned(S)));
+  }
+  if (R < S)
+    nn_samples(pb->nn_X + int64_t(R) * n, S - R, n, nu, pb->nn_mlp, pb->lv[0].ml_sum, cfg->seed, pb->nn_xyz,
+               cfg->smooth_frac, pb->stream);
+  nn_gemm(false, true, S, n, n, 1.f, pb->nn_X, n, pb->nn_Z, n, 0.f, pb->nn_T, n, pb->stream);
+  {
+    // scale the targets to unit RMS; inference multiplies by the inverse
+    launch_reduce<float>(RED_SQ, pb->nn_T, nullptr, nullptr, int64_t(S) * n, pb->partials, pb->max_blocks,
+                         pb->nn_scal + 4, pb->stream);
+    double ms = 0.0;
+    HHG_CUDA(cudaMemcpyAsync(&ms, pb->nn_scal + 4, 8, cudaMemcpyDeviceToHost, pb->stream));
+    HHG_CUDA(cudaStreamSynchronize(pb->stream));
+    ms /= double(S) * n;
+    pb->nn_tscale = ms > 0 ? 1.0 / std::sqrt(ms) : 1.0;
+    nn_scale(pb->nn_T, int64_t(S) * n, float(pb->nn_tscale), pb->stream);
+  }
+  double first_loss = 0.0, last_loss = 0.0, val_rel = 0.0;
+  // mean squared error and mean relative error of the network on samples [first, first + count)
+  auto eval = [&](int first, int count, double& mse, double& rel) -> int {
+    double se = 0.0, rs = 0.0;
+    for (int s0 = first; s0 < first + count; s0 += pb->nn_B) {
+      const int bsz = std::min(pb->nn_B, first + count - s0);
+      nn_forward(pb, pb->nn_X + int64_t(s0) * n, bsz, pb->nn_H1, pb->nn_H2, pb->nn_Y);
+      std::vector<float> y(size_t(bsz) * n), t(size_t(bsz) * n);
+      HHG_CUDA(cudaMemcpyAsync(y.data(), pb->nn_Y, y.size() * 4, cudaMemcpyDeviceToHost, pb->stream));
+      HHG_CUDA(cudaMemcpyAsync(t.data(), pb->nn_T + int64_t(s0) * n, t.size() * 4, cudaMemcpyDeviceToHost, pb->stream));
+      HHG_CUDA(cudaStreamSynchronize(pb->stream));
+      for (int b = 0; b < bsz; ++b) {
+        double num = 0.0, den = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double d = double(y[size_t(b) * n + i]) - t[size_t(b) * n + i];
+          num += d * d;
+          den += double(t[size_t(b) * n + i]) * t[size_t(b) * n + i];
+        }
+        se += num;
+        rs += den > 0 ? std::sqrt(num / den) : 0.0;
+      }
+    }
+    mse = se / (double(count) * n);
+    rel = rs / count;
+    return HHG_OK;
+  };
+  double dummy;
+  HHG_TRY(eval(0, cfg->n_train, first_loss, dummy));
+  for (int ep = 0; ep < cfg->epochs; ++ep)
+    for (int s0 = 0; s0 < cfg->n_train; s0 += cfg->batch) {
+      const int bsz = std::min(cfg->batch, cfg->n_train - s0);
+      const float* X = pb->nn_X + int64_t(s0) * n;
+      nn_forward(pb, X, bsz, pb->nn_H1, pb->nn_H2, pb->nn_Y);
+      nn_backward(pb, X, pb->nn_T + int64_t(s0) * n, bsz);
+      nn_adam(pb->nn_params, pb->nn_grads, pb->nn_m, pb->nn_v, pb->nn_P, float(cfg->lr), ++pb->nn_step, pb->stream);
+    }
+  HHG_CHECK_LAUNCH();
+  HHG_CUDA(cudaEventRecord(e1, pb->stream));
+  HHG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HHG_TRY(eval(0, cfg->n_train, last_loss, dummy));
+  double val_mse;
+  HHG_TRY(eval(cfg->n_train, S - cfg->n_train, val_mse, val_rel));
+  if (rep) {
+    rep->n = n;
+    rep->n_params = pb->nn_P;
+    rep->loss_first = first_loss;
+    rep->loss_last = last_loss;
+    rep->val_rel_err = val_rel;
+    rep->train_ms = ms;
+  }
+  if (!std::isfinite(last_loss)) return fail(HHG_EDIVERGED, "training diverged");
+  return HHG_OK;
+}
+
+extern "C" int hhg_coarse_nn_record(hhg_problem* pb, int on, int64_t* recorded) {
+  HHG_TRY(check_nn(pb));
+  if (on && !pb->nn_recording) HHG_CUDA(cudaMemsetAsync(pb->nn_counts + 2, 0, 8, pb->stream));
+  pb->nn_recording = on != 0;
+  for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
+  pb->graphs.clear();
+  if (recorded) {
+    unsigned long long cnt = 0;
+    HHG_CUDA(cudaMemcpyAsync(&cnt, pb->nn_counts + 2, 8, cudaMemcpyDeviceToHost, pb->stream));
+    HHG_CUDA(cudaStreamSynchronize(pb->stream));
+    *recorded = int64_t(cnt);
+  }
+  return HHG_OK;
+}
+
+extern "C" int hhg_coarse_nn_enable(hhg_problem* pb, int mode, double theta) {
+  HHG_TRY(check_nn(pb));
+  if (mode < 0 || mode > 3 || !(theta > 0)) return fail(HHG_EINVAL, "mode in {0,1,2,3}, theta > 0");
+  pb->nn_mode = mode;
+  pb->nn_theta = theta;
+  for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
+  pb->graphs.clear();
+  return HHG_OK;
+}
+
+extern "C" int hhg_coarse_nn_counts(hhg_problem* pb, int64_t* accepted, int64_t* rejected) {
+  HHG_TRY(check_nn(pb));
+  unsigned long long c[2];
+  HHG_CUDA(cudaMemcpyAsync(c, pb->nn_counts, 16, cudaMemcpyDeviceToHost, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(pb->nn_counts, 0, 16, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  if (accepted) *accepted = int64_t(c[0]);
+  if (rejected) *rejected = int64_t(c[1]);
   return HHG_OK;
 }
 

@@ -28,7 +28,18 @@ AHAT = {"f": 0, "s": 1}
 
 class ProblemDesc(C.Structure):
     _fields_ = [("disc", C.c_int), ("L", C.c_int), ("coarse_level", C.c_int), ("solve", C.c_int),
-                ("nu_a", C.c_double), ("pspg_rhs", C.c_int), ("error_level", C.c_int)]
+                ("nu_a", C.c_double), ("pspg_rhs", C.c_int), ("error_level", C.c_int),
+                ("nn_hidden", C.c_int), ("nn_samples", C.c_int), ("nn_batch", C.c_int)]
+
+
+class NNCfg(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("n_train", C.c_int),
+                ("seed", C.c_uint64), ("recorded", C.c_int), ("smooth_frac", C.c_double)]
+
+
+class NNReport(C.Structure):
+    _fields_ = [("n", C.c_int), ("n_params", C.c_int64), ("loss_first", C.c_double), ("loss_last", C.c_double),
+                ("val_rel_err", C.c_double), ("train_ms", C.c_double)]
 
 
 class LayoutInfo(C.Structure):
@@ -94,6 +105,14 @@ def load():
         "hhg_block_norms_noalloc": [VP, I, C.c_int64, C.c_int64, VP, VP],
         "hhg_batch_create": [C.POINTER(P), I, C.POINTER(P)],
         "hhg_autotune": [P, I, C.POINTER(C.c_int)],
+        "hhg_coarse_nn_size": [P, C.POINTER(C.c_int), C.POINTER(C.c_int64)],
+        "hhg_coarse_nn_set_params": [P, C.POINTER(C.c_float)],
+        "hhg_coarse_nn_get_params": [P, C.POINTER(C.c_float)],
+        "hhg_coarse_nn_grad": [P, C.POINTER(C.c_float), C.POINTER(C.c_float), I, DP, C.POINTER(C.c_float)],
+        "hhg_coarse_nn_train": [P, C.POINTER(NNCfg), C.POINTER(NNReport)],
+        "hhg_coarse_nn_enable": [P, I, D],
+        "hhg_coarse_nn_record": [P, I, C.POINTER(C.c_int64)],
+        "hhg_coarse_nn_counts": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
         "hhg_batch_destroy": [P],
         "hhg_batch_fmg_solve": [P, C.POINTER(Params), VP, C.POINTER(C.c_int64)],
     }
@@ -163,13 +182,14 @@ class Problem:
     """A level hierarchy coarse_level..L of one Stokes problem on one GPU."""
 
     def __init__(self, mesh: Mesh, disc="P1P1", L=4, coarse_level=0, solve="fp64", nu_a=0.0, pspg_rhs=True,
-                 error_level=False, device="cuda", stream=None):
+                 error_level=False, device="cuda", stream=None, nn_hidden=0, nn_samples=0, nn_batch=0):
         lib = load()
         self.disc = disc
         self.L, self.lc = L, coarse_level
         self.solve = solve
         d = ProblemDesc(P1P1 if disc == "P1P1" else P2P1, L, coarse_level,
-                        SOLVE_MIXED if solve == "mixed" else SOLVE_FP64, float(nu_a), int(pspg_rhs), int(error_level))
+                        SOLVE_MIXED if solve == "mixed" else SOLVE_FP64, float(nu_a), int(pspg_rhs), int(error_level),
+                        int(nn_hidden), int(nn_samples), int(nn_batch))
         h = C.c_void_p()
         _check(lib.hhg_problem_create(mesh.h, C.byref(d), C.byref(h)), "hhg_problem_create")
         self.h = h
@@ -268,6 +288,54 @@ class Problem:
 
     def set_graph_mode(self, on):
         _check(load().hhg_set_graph_mode(self.h, int(on)), "hhg_set_graph_mode")
+
+    # ------------------------------------------- learned coarse correction
+    def nn_size(self):
+        n, p = C.c_int(), C.c_int64()
+        _check(load().hhg_coarse_nn_size(self.h, C.byref(n), C.byref(p)), "hhg_coarse_nn_size")
+        return n.value, p.value
+
+    def nn_set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(load().hhg_coarse_nn_set_params(self.h, a.ctypes.data_as(C.POINTER(C.c_float))),
+               "hhg_coarse_nn_set_params")
+
+    def nn_get_params(self):
+        _, p = self.nn_size()
+        a = np.zeros(p, dtype=np.float32)
+        _check(load().hhg_coarse_nn_get_params(self.h, a.ctypes.data_as(C.POINTER(C.c_float))),
+               "hhg_coarse_nn_get_params")
+        return a
+
+    def nn_grad(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        _, p = self.nn_size()
+        g = np.zeros(p, dtype=np.float32)
+        loss = C.c_double()
+        fp = C.POINTER(C.c_float)
+        _check(load().hhg_coarse_nn_grad(self.h, X.ctypes.data_as(fp), T.ctypes.data_as(fp), X.shape[0],
+                                         C.byref(loss), g.ctypes.data_as(fp)), "hhg_coarse_nn_grad")
+        return loss.value, g
+
+    def nn_train(self, epochs=30, batch=128, lr=1e-3, n_train=None, seed=2, smooth_frac=0.5, recorded=False):
+        cfg = NNCfg(epochs, batch, lr, n_train, seed, int(recorded), smooth_frac)
+        rep = NNReport()
+        _check(load().hhg_coarse_nn_train(self.h, C.byref(cfg), C.byref(rep)), "hhg_coarse_nn_train")
+        return rep
+
+    def nn_record(self, on):
+        c = C.c_int64()
+        _check(load().hhg_coarse_nn_record(self.h, int(on), C.byref(c)), "hhg_coarse_nn_record")
+        return c.value
+
+    def nn_enable(self, mode, theta=0.1):
+        _check(load().hhg_coarse_nn_enable(self.h, int(mode), float(theta)), "hhg_coarse_nn_enable")
+
+    def nn_counts(self):
+        a, r = C.c_int64(), C.c_int64()
+        _check(load().hhg_coarse_nn_counts(self.h, C.byref(a), C.byref(r)), "hhg_coarse_nn_counts")
+        return a.value, r.value
 
     def autotune(self, reps=5):
         """Per-level launch shapes; returns {level: (row_threads, row_kplanes, gs_threads)}."""

@@ -490,3 +490,28 @@ def test_sampled_rows_match_assembled(disc, nu_a):
     ys, ya = sample_rows((1, 2, 1), 0.5, 2, disc, xs, rows, nu_a, with_abs=True)
     ref = np.array([y[f * lev.nv + n] if f < 3 else y[3 * lev.nv + n] for f, n in rows])
     assert np.all(np.abs(ys - ref) <= 1e-14 * (ya + 1e-300) + 1e-300)
+
+
+def test_mlp_gradients_match_finite_differences():
+    """Back-propagation of the learned-coarse-correction MLP against central
+    differences of the loss (the definition of the derivative)."""
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    n, H, B = 7, 9, 5
+    params = mlp.init(n, H, seed=1)
+    params = [p + 0.05 * rng.standard_normal(p.shape) for p in params]
+    X = rng.standard_normal((B, n))
+    T = rng.standard_normal((B, n))
+    g = mlp.grads(params, X, T)
+    eps = 1e-6
+    for pi, p in enumerate(params):
+        flat = p.reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp = mlp.loss(params, X, T)
+            flat[idx] = old - eps
+            lm = mlp.loss(params, X, T)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - g[pi].reshape(-1)[idx]) <= 1e-6 * max(1.0, abs(fd)), (pi, idx)
