@@ -301,6 +301,147 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+def _gamma(pb, wl, prm, x, L, max_cycles=300):
+    """gamma_u, gamma_p of Eq. gamma for the FP64 solution x of level L."""
+    import torch
+    from paper_2010_13513_gb300 import hhg
+    info = pb.layout(L + 1)
+    ue = wl.exact_velocity(hhg.velocity_coords(info)).T.ravel()
+    pe = wl.exact_pressure(hhg.pressure_coords(info))
+    e_fmg = pb.error_norms(L, x, ue, pe)
+    xs = x.clone()
+    b = pb.level_vector(L, "rhs")
+    r = pb.new_vector(L)
+    for _ in range(max_cycles):
+        pb.vcycle(L, prm, xs, b)
+        if max(pb.residual(L, xs, b, r, norms=True)) < 1e-12:
+            break
+    e_disc = pb.error_norms(L, xs, ue, pe)
+    torch.cuda.synchronize()
+    return e_fmg[0] / e_disc[0], e_fmg[1] / e_disc[1]
+
+
+def _timed(fn, steps, warmup, stream):
+    import torch
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        fn()
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        e.synchronize()
+        ts.append(s.elapsed_time(e) * 1e-3)
+    return statistics.mean(ts)
+
+
+def run_p1_visc(args):
+    """P1-P1 PSPG, 48-tetrahedron cube (2x2x2 Kuhn box on [0,1]^3) on level 7,
+    viscosity nu = exp(a z) with a ~ U[0,4] from seed 0, FP32 V-cycles inside
+    FP64 iterative refinement; Table 3 tuple (2,3,2,1,A_s,1)."""
+    import torch
+    from hhg_inputs import Workload, draw_viscosity_exponent
+    from paper_2010_13513_gb300 import hhg
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    a = draw_viscosity_exponent(0)
+    L = 7
+    wl = Workload("curl", nu_a=a)
+    pb = hhg.Problem(hhg.Mesh.box(2, 2, 2, 0.5), disc="P1P1", L=L, coarse_level=0, solve="mixed", nu_a=a,
+                     error_level=True)
+    hhg.set_workload_rhs(pb, wl)
+    shapes = pb.autotune(reps=3)
+    info = pb.layout(L)
+    om = pb.estimate_omega(L, np.random.default_rng(0).uniform(-1, 1, info.n_pressure_nodes), 100)
+    prm = hhg.Params.make(2, 3, 2, 1, "s", 1, om)
+    x = pb.new_vector(L)
+    st = pb.fmg_solve(prm, x)
+    sampler = ClockSampler(0)
+    t = _timed(lambda: pb.fmg_solve(prm, x, stats=False), args.steps, args.warmup, stream)
+    clocks = sampler.stop()
+    gu, gp = _gamma(pb, wl, prm, x, L)
+    # operator apply roofline at this size (FP32)
+    xa = pb.new_vector(L, 1)
+    xa.uniform_(-1, 1)
+    ya = pb.new_vector(L, 1)
+    ta = _timed(lambda: pb.apply(L, "FULL", xa, ya), 10, 3, stream)
+    pk, src = peaks()
+    ach = info.n_dofs * 8 / ta / 1e9
+    print(json.dumps({
+        "metric": "FMG-solved Stokes DoF/s at disc.-error accuracy", "value": info.n_dofs / t, "unit": "DoF/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"P1-P1 PSPG, 48-tet cube, level 7, nu = exp({a:.4f} z), curl solution, FP32 V-cycles "
+                               "in FP64 refinement", "dofs": info.n_dofs, "omega_inv": om,
+                   "params": [2, 3, 2, 1, "s", 1], "gamma_u": gu, "gamma_p": gp, "wu_model": st.wu_model,
+                   "launch_shapes": {str(k): v for k, v in shapes.items()}},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": ach / pk["hbm_gbs"], "kernel": "FP32 FULL apply, level 7", "avg_launch_us": ta * 1e6,
+                     "peak_source": src},
+        "clocks": clocks}))
+
+
+def run_p2_l7(args):
+    """P2-P1 Taylor-Hood on the 6-tetrahedron cube, level 7 (50.9M velocity
+    DoFs), the paper's analytic solution, FP32 V-cycles in FP64 refinement,
+    coarse level 2: plain dense coarse solve against the learned coarse
+    correction (gated) trained on the GPU."""
+    import torch
+    from hhg_inputs import Workload
+    from paper_2010_13513_gb300 import hhg
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    L = 7
+    wl = Workload("paper")
+    pb = hhg.Problem(hhg.Mesh.box(1, 1, 1, 1.0), disc="P2P1", L=L, coarse_level=2, solve="mixed", error_level=True,
+                     nn_hidden=512, nn_samples=10000, nn_batch=256)
+    hhg.set_workload_rhs(pb, wl)
+    pb.autotune(reps=3)
+    info = pb.layout(L)
+    om = pb.estimate_omega(L, np.random.default_rng(0).uniform(-1, 1, info.n_pressure_nodes), 100)
+    prm = hhg.Params.make(**PARAMS, omega_inv=om)
+    x = pb.new_vector(L)
+    pb.fmg_solve(prm, x)
+    t_plain = _timed(lambda: pb.fmg_solve(prm, x, stats=False), args.steps, args.warmup, stream)
+    g_plain = _gamma(pb, wl, prm, x, L)
+    # training data: defects recorded from solves of random-forcing problems, plus random defects
+    pb.nn_record(True)
+    for seed in range(100):
+        hhg.set_workload_rhs(pb, Workload("modes", seed=7000 + seed), levels=range(2, 5))
+        xx = pb.new_vector(4)
+        pb.vcycle(4, prm, xx, pb.level_vector(4, "rhs"))
+        for _ in range(4):
+            pb.vcycle(4, prm, xx, pb.level_vector(4, "rhs"))
+    recorded = pb.nn_record(False)
+    hhg.set_workload_rhs(pb, wl)
+    rep = pb.nn_train(epochs=60, batch=256, lr=1e-3, n_train=9500, seed=2, recorded=True, smooth_frac=0.5)
+    out = {}
+    for mode, name in ((1, "gated"), (2, "network_only")):
+        pb.nn_enable(mode, theta=0.1)
+        pb.fmg_solve(prm, x, stats=False)
+        tt = _timed(lambda: pb.fmg_solve(prm, x, stats=False), args.steps, args.warmup, stream)
+        acc, rej = pb.nn_counts()
+        pb.fmg_solve(prm, x, stats=False)
+        gg = _gamma(pb, wl, prm, x, L)
+        out[name] = {"ms_per_step": tt * 1e3, "gamma_u": gg[0], "gamma_p": gg[1], "accepted": acc, "rejected": rej}
+        pb.nn_enable(0)
+    print(json.dumps({
+        "metric": "FMG-solved Stokes DoF/s at disc.-error accuracy", "value": info.n_dofs / t_plain, "unit": "DoF/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_plain * 1e3,
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "P2-P1 Taylor-Hood, 6-tet cube, level 7, analytic cube solution, coarse level 2, "
+                               "FP32 V-cycles in FP64 refinement", "dofs": info.n_dofs, "omega_inv": om,
+                   "params": PARAMS, "gamma_u": g_plain[0], "gamma_p": g_plain[1],
+                   "learned_coarse": {"n": rep.n, "params": rep.n_params, "recorded_defects": recorded,
+                                      "loss_first": rep.loss_first, "loss_last": rep.loss_last,
+                                      "val_rel_err": rep.val_rel_err, "train_ms": rep.train_ms, **out}}}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -337,7 +478,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hhg", choices=["hhg", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="p2-l6", choices=["p2-l6", "batched"])
+    ap.add_argument("--workload", default="p2-l6", choices=["p2-l6", "batched", "p1-visc", "p2-l7"])
     ap.add_argument("--profile-region", action="store_true",
                     help="only set-up, warm-up and the timed FMG steps, bracketed by cudaProfilerStart/Stop")
     args = ap.parse_args()
@@ -345,6 +486,10 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "p1-visc":
+        return run_p1_visc(args)
+    if args.workload == "p2-l7":
+        return run_p2_l7(args)
 
     import torch
     import torch.distributed as dist

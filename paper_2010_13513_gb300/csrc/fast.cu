@@ -136,8 +136,7 @@ __device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restric
     }
     T v = a0;
     if (VARNU) {
-      const T e = T(exp(g.nu_ah * k));
-      v += e * a1 + a2 / e;
+      v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
     } else {
       v += a1 + a2;
     }
@@ -189,7 +188,7 @@ __device__ __forceinline__ void gs_site(const Geo& g, T* __restrict__ u, const T
     a2 += wt * us[o + 2 * cs];
   }
   T einv = T(1);
-  if (VARNU) einv = T(exp(-g.nu_ah * k));
+  if (VARNU) einv = T(g.eisc[k]);
   const int64_t o0 = int64_t(GRP) * g.arr + idx;
   u[o0] = (rhs[o0] * einv - a0) * inv_diag;
   u[o0 + cs] = (rhs[o0 + cs] * einv - a1) * inv_diag;

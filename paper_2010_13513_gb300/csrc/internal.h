@@ -39,6 +39,8 @@ struct Geo {
   int G;                // velocity groups
   double h;             // mesh width
   double nu_ah;         // nu_a * h (row scaling exp(zs * nu_ah * k))
+  const double* esc;    // exp(+nu_ah k), k = 0..nz (device; set when nu_a != 0)
+  const double* eisc;   // exp(-nu_ah k)
 };
 
 inline Geo make_geo(int mx, int my, int mz, int level, int G, double H, double nu_a) {
@@ -52,6 +54,8 @@ inline Geo make_geo(int mx, int my, int mz, int level, int G, double H, double n
   g.G = G;
   g.h = H / n;
   g.nu_ah = nu_a * g.h;
+  g.esc = nullptr;
+  g.eisc = nullptr;
   return g;
 }
 

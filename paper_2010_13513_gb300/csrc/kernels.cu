@@ -86,8 +86,7 @@ __global__ void __launch_bounds__(128) k_apply(Geo g, OpDev op, const T* __restr
   }
   T v = acc[0];
   if (g.nu_ah != 0.0) {
-    const T e = T(exp(g.nu_ah * k));
-    v += e * acc[1] + acc[2] / e;
+    v += T(g.esc[k]) * acc[1] + T(g.eisc[k]) * acc[2];
   } else {
     v += acc[1] + acc[2];
   }
@@ -119,7 +118,7 @@ __global__ void __launch_bounds__(128) k_gs(Geo g, OpDev A, int grp, int colour,
     a2 += w * p[2 * cstride];
   }
   T einv = T(1);
-  if (g.nu_ah != 0.0) einv = T(exp(-g.nu_ah * k));
+  if (g.nu_ah != 0.0) einv = T(g.eisc[k]);
   const int64_t o0 = int64_t(grp) * g.arr + idx;
   u[o0] = (rhs[o0] * einv - a0) * inv_diag;
   u[o0 + cstride] = (rhs[o0 + cstride] * einv - a1) * inv_diag;

@@ -135,7 +135,7 @@ struct Level {
   bool small = false;
   Shape shape;                          // launch shapes of the specialised kernels
   // workspace offsets (bytes) of the level vectors
-  size_t o_rhs, o_W, o_x64, o_tmp64, o_bw64, o_x32, o_b32, o_tmp32, o_invml, o_ml;
+  size_t o_rhs, o_W, o_x64, o_tmp64, o_bw64, o_x32, o_b32, o_tmp32, o_invml, o_ml, o_esc;
   double *rhs = nullptr, *W = nullptr, *x64 = nullptr, *tmp64 = nullptr, *bw64 = nullptr;
   float *x32 = nullptr, *b32 = nullptr, *tmp32 = nullptr;
   double *inv_mlhat = nullptr, *ml = nullptr;
@@ -394,6 +394,7 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
     }
     lv.o_invml = off; off += a64;
     lv.o_ml = off; off += a64;
+    lv.o_esc = off; off += align256(size_t(2 * (lv.g.nz + 1)) * 8);
   }
   // coarse system: interior velocity DoFs of the coarse level + all pressure nodes
   {
@@ -1045,6 +1046,19 @@ extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, 
   // zero all vectors (halo and padding stay zero for the lifetime of the problem)
   HHG_CUDA(cudaMemsetAsync(ws + pb->lv[0].o_rhs, 0, pb->o_Z - pb->lv[0].o_rhs, pb->stream));
   pb->bound = true;
+  // viscosity row scales exp(+-nu_a h k) of every level (after the memset above)
+  for (Level& lv : pb->lv) {
+    double* esc = reinterpret_cast<double*>(ws + lv.o_esc);
+    std::vector<double> tab(size_t(2 * (lv.g.nz + 1)));
+    for (int k = 0; k <= lv.g.nz; ++k) {
+      tab[size_t(k)] = std::exp(lv.g.nu_ah * k);
+      tab[size_t(lv.g.nz + 1 + k)] = std::exp(-lv.g.nu_ah * k);
+    }
+    HHG_CUDA(cudaMemcpyAsync(esc, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+    HHG_CUDA(cudaStreamSynchronize(pb->stream));
+    lv.g.esc = esc;
+    lv.g.eisc = esc + lv.g.nz + 1;
+  }
   // lumped masses: M_L 1 (projection weights) and M_L(1/nu) (S_hat)
   for (Level& lv : pb->lv) {
     const int64_t po = p_offset(lv);

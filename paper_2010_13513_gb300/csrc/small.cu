@@ -90,8 +90,7 @@ __device__ __forceinline__ void sres_row(const Geo& g, int R, int i, int j, int 
   }
   T v = a0;
   if (VARNU) {
-    const T e = T(exp(g.nu_ah * k));
-    v += e * a1 + a2 / e;
+    v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
   } else {
     v += a1 + a2;
   }
@@ -119,7 +118,7 @@ __device__ __forceinline__ void sgs(const Geo& g, int i, int j, int k, T* u, con
     a2 += wt * ldc(us + o + 2 * cs);
   }
   T einv = T(1);
-  if (VARNU) einv = T(exp(-g.nu_ah * k));
+  if (VARNU) einv = T(g.eisc[k]);
   const int64_t o0 = int64_t(GRP) * g.arr + idx;
   u[o0] = (ldc(rhs + o0) * einv - a0) * inv_diag;
   u[o0 + cs] = (ldc(rhs + o0 + cs) * einv - a1) * inv_diag;
