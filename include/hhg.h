@@ -208,11 +208,13 @@ int hhg_vcycle(hhg_problem* pb, int level, const hhg_params* prm, int prec, void
 int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats* stats);
 /* Per-level autotuner of the launch shapes (threads per block and k planes
  * per thread of the stencil-row kernels, threads per block of the
- * Gauss-Seidel kernels): every candidate is timed `reps` times with CUDA
+ * Gauss-Seidel kernels, and the smoother's resident CTA count of
+ * hhg_set_level_smoother): every candidate is timed `reps` times with CUDA
  * events on the problem's stream in the precision of the V-cycles, the
- * fastest is kept.  Uses only the library's scratch vectors (tmp, b); cached
- * graphs are dropped.  shapes_out (optional) receives 3 ints per level
- * (coarse .. L).  Synchronises. */
+ * fastest is kept.  Uses only the library's scratch vectors; cached graphs
+ * are dropped.  shapes_out (optional) receives 4 ints per level (coarse ..
+ * L): row threads, row k planes, Gauss-Seidel threads, resident CTAs.
+ * Synchronises. */
 int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
 
 /* ------------------------------------------- learned coarse-grid correction */
@@ -286,10 +288,21 @@ int hhg_batch_fmg_solve(hhg_batch* batch, const hhg_params* params, void* stream
  * as a CUDA graph and replays it (default on).  Graphs are used only when the
  * bound stream is a created stream (not the legacy default stream). */
 int hhg_set_graph_mode(hhg_problem* pb, int on);
-/* Whether the smoother runs all phases of a small level (at most 5^3
- * lattice sites) in one thread-block-cluster launch (default on) or one
- * launch per phase.  Both give the same iterates. */
+/* Whether the smoother of the levels that have a resident CTA count (see
+ * hhg_set_level_smoother) runs all phases in one launch (default on) or one
+ * launch per phase everywhere.  Both give the same iterates. */
 int hhg_set_small_level_mode(hhg_problem* pb, int on);
+/* Not in the paper (a GPU execution choice, Sec. 3.2's smoother unchanged):
+ * the number of CTAs `ctas` (1..16, one thread-block cluster) that run all
+ * phases of the Uzawa smoother of `level` in precision `prec` in one launch
+ * with the level's block vector held in their shared memory (a slab of k
+ * planes per CTA), or 0 for one launch per phase.  HHG_EINVAL if the level
+ * does not fit (at most 227 KB of slab per CTA, at least one plane per CTA,
+ * the cluster must be schedulable).  Default at bind: the fewest CTAs (<= 8)
+ * with at most 8192 lattice sites each, else 0; hhg_autotune times all
+ * choices.  Drops cached graphs.  The iterates do not depend on the choice. */
+int hhg_set_level_smoother(hhg_problem* pb, int level, int prec, int ctas);
+int hhg_get_level_smoother(hhg_problem* pb, int level, int prec, int* ctas);
 /* omega^{-1}: `iters` power iterations on M_L^{-1}(C + B A_s^{-1} B^T)
  * (Eq. omega-eigenvalue-problem) from the host start vector v0 (canonical
  * pressure order). */

@@ -130,9 +130,11 @@ struct Level {
   // parameter blocks of the specialised kernels (FastTab<T, N> images)
   std::vector<char> ftab64[OP_COUNT], ftab32[OP_COUNT];
   bool has_fast[OP_COUNT] = {};
-  // parameter block of the cluster-resident smoother (small levels only)
+  // parameter blocks of the shared-memory-resident smoother: global-stride
+  // images, and per CTA count the images localised to the slab stride
   std::vector<char> stab64, stab32;
-  bool small = false;
+  std::map<int, std::vector<char>> rtab64, rtab32;
+  int rctas[2] = {0, 0};                // CTAs of the resident smoother per precision (0: per-phase kernels)
   Shape shape;                          // launch shapes of the specialised kernels
   // workspace offsets (bytes) of the level vectors
   size_t o_rhs, o_W, o_x64, o_tmp64, o_bw64, o_x32, o_b32, o_tmp32, o_invml, o_ml, o_esc;
@@ -357,10 +359,8 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
   };
   put_x(pb->tv, pb->xoff_v);
   put_x(pb->tp, pb->xoff_p);
-  // small levels: tables of the cluster-resident smoother
+  // tables of the shared-memory-resident smoother
   for (Level& lv : pb->lv) {
-    const int64_t sites = int64_t(lv.g.nx + 1) * (lv.g.ny + 1) * (lv.g.nz + 1);
-    if (sites > kSmallLevelSites) continue;
     auto pack = [&](int prec, const std::vector<char>* src, std::vector<char>& out) {
       out.assign(small_tabs_bytes(desc->disc, varnu, prec), 0);
       const int ops[3] = {OP_A, OP_BT, OP_BC};
@@ -371,7 +371,6 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
     };
     pack(HHG_FP64, lv.ftab64, lv.stab64);
     pack(HHG_FP32, lv.ftab32, lv.stab32);
-    lv.small = true;
   }
 
   // ---- workspace layout
@@ -608,25 +607,72 @@ double level_weight(hhg_problem* pb, const Level& lv) {
   return double(lv.n_dofs()) / double(pb->L(pb->desc.L).n_dofs());
 }
 
-template <class T> const void* stab(Level& lv);
-template <> const void* stab<double>(Level& lv) { return lv.stab64.data(); }
-template <> const void* stab<float>(Level& lv) { return lv.stab32.data(); }
+template <class T> constexpr int prec_index() { return sizeof(T) == 8 ? HHG_FP64 : HHG_FP32; }
+template <class T> const void* rtab(Level& lv, int C);
+template <> const void* rtab<double>(Level& lv, int C) { return lv.rtab64.at(C).data(); }
+template <> const void* rtab<float>(Level& lv, int C) { return lv.rtab32.at(C).data(); }
+
+// selects `ctas` CTAs (0: per-phase kernels) for the resident smoother of a
+// level in precision `prec`; HHG_EINVAL if the level does not fit
+int set_resident(hhg_problem* pb, Level& lv, int prec, int ctas) {
+  if (ctas < 0 || ctas > kResidentMaxCtas) return fail(HHG_EINVAL, "ctas must be in 0..16");
+  if (ctas > 0) {
+    const int varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
+    if (!resident_feasible(pb->desc.disc, varnu, prec, lv.g, ctas))
+      return fail(HHG_EINVAL, "level does not fit the shared memory of that many CTAs");
+    // the per-cube boundary terms of (B, -C) must stay within the adjacent
+    // sites, as the slab holds one halo plane on each side
+    const OpOffsets& of = lv.opoff[OP_BC];
+    const DRow* rows = reinterpret_cast<const DRow*>(pb->tables.bytes.data() + of.rows);
+    const DTermB* bt = reinterpret_cast<const DTermB*>(pb->tables.bytes.data() + of.bterms);
+    for (int r = 0; r < of.nrows; ++r)
+      for (int t = rows[r].b0; t < rows[r].b0 + rows[r].m0 + rows[r].m1 + rows[r].m2; ++t) {
+        const int64_t dk = std::llround(double(bt[t].off) / double(lv.g.sy));
+        const int64_t dj = std::llround(double(bt[t].off - dk * lv.g.sy) / double(lv.g.sx));
+        const int64_t di = bt[t].off - dk * lv.g.sy - dj * lv.g.sx;
+        if (bt[t].arr < 0 || bt[t].arr > 3 * lv.g.G || dk < -1 || dk > 1 || dj < -1 || dj > 1 || di < -1 || di > 1)
+          return fail(HHG_EINVAL, "internal: boundary stencil offsets beyond adjacent sites");
+      }
+    auto& cache = prec == HHG_FP64 ? lv.rtab64 : lv.rtab32;
+    if (!cache.count(ctas)) {
+      std::vector<char> img;
+      if (!small_tabs_localise(pb->desc.disc, varnu, prec, prec == HHG_FP64 ? lv.stab64 : lv.stab32, lv.g,
+                               resident_arr(lv.g, ctas), img))
+        return fail(HHG_EINVAL, "internal: stencil offsets beyond adjacent sites");
+      cache[ctas] = std::move(img);
+    }
+  }
+  lv.rctas[prec] = ctas;
+  return HHG_OK;
+}
+
+// default CTA count: the fewest CTAs (at most 8) that hold the level with at
+// most 8192 lattice sites each, else none (per-phase kernels)
+int default_resident(hhg_problem* pb, Level& lv, int prec) {
+  const int varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
+  const int64_t plane = int64_t(lv.g.nx + 1) * (lv.g.ny + 1), nzp = lv.g.nz + 1;
+  for (int C : {1, 2, 4, 8})
+    if (plane * ((nzp + C - 1) / C) <= 8192 && resident_feasible(pb->desc.disc, varnu, prec, lv.g, C))
+      return set_resident(pb, lv, prec, C);
+  return set_resident(pb, lv, prec, 0);
+}
 
 template <class T>
 int uzawa(hhg_problem* pb, Level& lv, const hhg_params& prm, int sweeps, T* x, const T* b, T* tmp) {
   const int G = lv.g.G;
   if (sweeps <= 0) return HHG_OK;
-  if (lv.small && pb->use_cluster) {
-    // all phases of all sweeps in one cluster launch
+  const int C = lv.rctas[prec_index<T>()];
+  if (C > 0 && pb->use_cluster) {
+    // all phases of all sweeps in one cluster launch, the level in shared memory
     SmallArgs a{};
     a.iterations = sweeps;
     a.xi = prm.xi;
     a.ahat = prm.ahat;
     a.inv_omega_inv = 1.0 / prm.omega_inv;
     for (int gg = 0; gg < G; ++gg) a.inv_diag[gg] = lv.inv_diag[gg];
-    if (uzawa_cluster<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, lv.g, x, b, tmp, lv.inv_mlhat, a,
-                         lv.op[OP_BC], stab<T>(lv), pb->stream) != 0)
-      return fail(HHG_ECUDA, std::string("cluster smoother launch: ") + cudaGetErrorString(cudaGetLastError()));
+    if (uzawa_resident<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, lv.g, C, x, b, tmp, lv.inv_mlhat, a,
+                          lv.op[OP_BC], rtab<T>(lv, C), pb->stream) != 0)
+      return fail(HHG_ECUDA, std::string("resident smoother launch: ") + cudaGetErrorString(cudaGetLastError()));
     const Costs cs = block_costs(pb->ov);
     pb->wu_counted += sweeps * level_weight(pb, lv) * (prm.xi * (prm.ahat == HHG_AHAT_S ? 2 : 1) * cs.A + 2 * cs.B + cs.C);
     return HHG_OK;
@@ -1079,6 +1125,10 @@ extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, 
   }
   HHG_TRY(build_coarse(pb));
   if (pb->nn_h > 0) HHG_TRY(nn_setup(pb));
+  for (Level& lv : pb->lv) {
+    HHG_TRY(default_resident(pb, lv, HHG_FP64));
+    HHG_TRY(default_resident(pb, lv, HHG_FP32));
+  }
   Level& c = pb->lv[0];
   HHG_CUDA(cudaMemsetAsync(c.tmp64, 0, size_t(c.nvec()) * 8, pb->stream));
   HHG_CUDA(cudaMemsetAsync(c.bw64, 0, size_t(c.nvec()) * 8, pb->stream));
@@ -1275,6 +1325,23 @@ bool capturable(cudaStream_t s) {
 extern "C" int hhg_set_graph_mode(hhg_problem* pb, int on) {
   if (!pb) return fail(HHG_EINVAL, "null problem");
   pb->use_graphs = on != 0;
+  return HHG_OK;
+}
+
+extern "C" int hhg_set_level_smoother(hhg_problem* pb, int level, int prec, int ctas) {
+  HHG_TRY(check_level(pb, level));
+  if (prec != HHG_FP64 && prec != HHG_FP32) return fail(HHG_EINVAL, "prec must be HHG_FP64 or HHG_FP32");
+  HHG_TRY(set_resident(pb, pb->L(level), prec, ctas));
+  for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
+  pb->graphs.clear();
+  return HHG_OK;
+}
+
+extern "C" int hhg_get_level_smoother(hhg_problem* pb, int level, int prec, int* ctas) {
+  HHG_TRY(check_level(pb, level));
+  if (prec != HHG_FP64 && prec != HHG_FP32) return fail(HHG_EINVAL, "prec must be HHG_FP64 or HHG_FP32");
+  if (!ctas) return fail(HHG_EINVAL, "null argument");
+  *ctas = pb->L(level).rctas[prec];
   return HHG_OK;
 }
 
@@ -1538,7 +1605,7 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
   };
   const int disc = pb->desc.disc, varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
   // row kernels: FULL residual
-  const int threads[3] = {64, 128, 256}, planes[3] = {1, 2, 4};
+  const int threads[3] = {64, 128, 256}, planes[5] = {1, 2, 4, 8, 16};
   float best = 1e30f;
   Shape bestS = lv.shape;
   for (int t : threads)
@@ -1571,21 +1638,64 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
   HHG_CUDA(cudaStreamSynchronize(pb->stream));
   return HHG_OK;
 }
+// the smoother of a level: per-phase kernels against the resident smoother
+// on every CTA count that holds the level (two Uzawa iterations, xi = 2)
+template <class T>
+int tune_smoother(hhg_problem* pb, Level& lv, int reps, T* x, const T* b, T* tmp) {
+  const int prec = prec_index<T>();
+  const int varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
+  const size_t bytes = size_t(lv.nvec()) * sizeof(T);
+  hhg_params prm{1, 1, 0, 1, HHG_AHAT_F, 2, 0.5};
+  cudaEvent_t e0, e1;
+  HHG_CUDA(cudaEventCreate(&e0));
+  HHG_CUDA(cudaEventCreate(&e1));
+  int best_c = 0;
+  float best = 1e30f;
+  for (int C : {0, 1, 2, 4, 8, 16}) {
+    if (C > 0 && !resident_feasible(pb->desc.disc, varnu, prec, lv.g, C)) continue;
+    HHG_TRY(set_resident(pb, lv, prec, C));
+    HHG_CUDA(cudaMemsetAsync(x, 0, bytes, pb->stream));
+    HHG_CUDA(cudaMemsetAsync(tmp, 0, bytes, pb->stream));
+    HHG_TRY(uzawa<T>(pb, lv, prm, 2, x, b, tmp));
+    cudaEventRecord(e0, pb->stream);
+    for (int r = 0; r < reps; ++r) HHG_TRY(uzawa<T>(pb, lv, prm, 2, x, b, tmp));
+    cudaEventRecord(e1, pb->stream);
+    HHG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_c = C; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HHG_TRY(set_resident(pb, lv, prec, best_c));
+  HHG_CUDA(cudaMemsetAsync(x, 0, bytes, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(tmp, 0, bytes, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  return HHG_OK;
+}
 }  // namespace
 
 extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
   HHG_TRY(check_level(pb, pb ? pb->desc.L : 0));
   if (reps < 1) return fail(HHG_EINVAL, "reps must be positive");
   const bool mixed = pb->desc.solve == HHG_SOLVE_MIXED;
+  const double wu = pb->wu_counted;
   for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l) {
     Level& lv = pb->L(l);
-    if (mixed) HHG_TRY(tune_level<float>(pb, lv, reps, lv.tmp32, lv.b32));
-    else HHG_TRY(tune_level<double>(pb, lv, reps, lv.tmp64, lv.bw64));
+    if (mixed) {
+      HHG_TRY(tune_level<float>(pb, lv, reps, lv.tmp32, lv.b32));
+      HHG_TRY(tune_smoother<float>(pb, lv, reps, lv.x32, lv.b32, lv.tmp32));
+    } else {
+      HHG_TRY(tune_level<double>(pb, lv, reps, lv.tmp64, lv.bw64));
+      HHG_TRY(tune_smoother<double>(pb, lv, reps, lv.bw64, lv.rhs, lv.tmp64));
+    }
     if (shapes_out) {
-      int* o = shapes_out + 3 * (l - pb->desc.coarse_level);
+      int* o = shapes_out + 4 * (l - pb->desc.coarse_level);
       o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
+      o[3] = lv.rctas[mixed ? HHG_FP32 : HHG_FP64];
     }
   }
+  pb->wu_counted = wu;
   for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
   pb->graphs.clear();
   return HHG_OK;

@@ -1,7 +1,9 @@
-// Cluster-resident inexact Uzawa smoother for small levels (small.cu).
+// Shared-memory-resident inexact Uzawa smoother for small levels (small.cu).
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <vector>
 
 #include "fast.h"
 #include "internal.h"
@@ -29,13 +31,32 @@ struct SmallTabs {
 size_t small_tabs_bytes(int disc, int varnu, int prec);
 size_t small_tabs_offset(int disc, int varnu, int prec, int which);   // 0 = A, 1 = BT, 2 = BC
 
-// `iterations` inexact Uzawa iterations of a level in one cluster launch;
-// returns 0 or -1 (launch failure).  Levels with more than 5^3 sites use the
-// per-phase kernels instead.
-template <class T>
-int uzawa_cluster(int disc, int varnu, const Geo& g, T* x, const T* b, T* tmp, const double* inv_ml,
-                  const SmallArgs& a, const OpDev& bc_op, const void* tabs, cudaStream_t s);
+constexpr int kResidentThreads = 1024;            // threads per CTA
+constexpr int kResidentMaxCtas = 16;              // largest (non-portable) cluster
+constexpr size_t kResidentSmemMax = 227 * 1024;   // dynamic shared memory per CTA
 
-constexpr int64_t kSmallLevelSites = 5 * 5 * 5;
+// Slab decomposition: CTA c of a cluster of C owns the k planes
+// [c (nz+1) / C, (c+1) (nz+1) / C) of every array of the block vector and
+// keeps them, with one halo plane below and above, in shared memory.  Local
+// array stride (elements) and shared memory per CTA (bytes):
+int64_t resident_arr(const Geo& g, int ctas);
+size_t resident_smem(const Geo& g, int ctas, int prec);
+// true if `ctas` CTAs can hold the level (every CTA owns a plane, the slab
+// fits the shared memory, the cluster can be scheduled).  Sets the kernel's
+// shared-memory and cluster-size attributes; call before any launch with
+// this CTA count and outside stream capture.
+bool resident_feasible(int disc, int varnu, int prec, const Geo& g, int ctas);
+// rewrites the linear offsets (array * arr_g + rel) of a SmallTabs image to
+// the local array stride arr_l; false if a term reaches beyond the adjacent
+// sites (then the slab layout would not hold it)
+bool small_tabs_localise(int disc, int varnu, int prec, const std::vector<char>& in, const Geo& g, int64_t arr_l,
+                         std::vector<char>& out);
+
+// `iterations` inexact Uzawa iterations of a level in one launch of a
+// cluster of `ctas` CTAs; `tabs` is a SmallTabs image localised to
+// resident_arr(g, ctas).  Returns 0 or -1 (launch failure).
+template <class T>
+int uzawa_resident(int disc, int varnu, const Geo& g, int ctas, T* x, const T* b, T* tmp, const double* inv_ml,
+                   const SmallArgs& a, const OpDev& bc_op, const void* tabs, cudaStream_t s);
 
 }  // namespace hhg

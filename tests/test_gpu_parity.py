@@ -89,6 +89,60 @@ def test_uzawa_parity(disc, ahat, xi, nu_a):
     assert rel(pb.to_host(L, xd), ref) < 1e-12
 
 
+@pytest.mark.parametrize("disc,L,nu_a,ahat,xi", [("P2P1", 2, 0.0, "s", 2), ("P2P1", 2, 1.3, "f", 1),
+                                                  ("P1P1", 3, 0.0, "s", 1), ("P1P1", 3, 0.8, "f", 2)])
+def test_resident_smoother_every_cta_count(disc, L, nu_a, ahat, xi):
+    """The shared-memory-resident smoother on 1, 2, 4, 8 (and 16) CTAs, each
+    owning a slab of k planes, gives the oracle's Uzawa iterates (FP64), and
+    in FP32 the iterates of the per-phase launches."""
+    from oracle.stokes import Params
+    from paper_2010_13513_gb300 import hhg
+    box = (1, 1, 2)
+    pb = lib_problem(box, L, disc, lc=1, nu_a=nu_a, solve="mixed")
+    hy = oracle_hierarchy(box, L, disc, lc=1, nu_a=nu_a)
+    lev = hy.lv[L]
+    x, b = random_vector(lev, 14), random_vector(lev, 15)
+    om = OMEGA_INV[disc]
+    lprm = hhg.Params.make(ahat=ahat, xi=xi, omega_inv=om)
+    prm = Params(ahat=ahat, xi=xi, omega_inv=om)
+    ref = lev.uzawa(lev.uzawa(x, b, prm), b, prm)
+    tried = []
+    out32 = {}
+    for ctas in (0, 1, 2, 4, 8, 16):
+        try:
+            pb.set_level_smoother(L, ctas, prec=hhg.FP64)
+        except hhg.HHGError:
+            continue
+        assert pb.level_smoother(L, prec=hhg.FP64) == ctas
+        xd = pb.to_device(L, x)
+        pb.smooth(L, lprm, 2, xd, pb.to_device(L, b))
+        assert rel(pb.to_host(L, xd), ref) < 1e-12, ctas
+        tried.append(ctas)
+        pb.set_level_smoother(L, ctas, prec=hhg.FP32)
+        x32 = pb.to_device(L, x, prec=hhg.FP32)
+        pb.smooth(L, lprm, 2, x32, pb.to_device(L, b, prec=hhg.FP32))
+        out32[ctas] = pb.to_host(L, x32)
+    assert {0, 1, 2, 4, 8} <= set(tried)
+    if disc == "P1P1":
+        assert 16 in tried                  # 17 k planes: the non-portable 16-CTA cluster
+    for ctas, v in out32.items():
+        assert rel(v, out32[0]) < 1e-6, ctas
+        assert rel(v, ref) < 1e-4
+
+
+def test_resident_smoother_rejects_what_does_not_fit():
+    from paper_2010_13513_gb300 import hhg
+    pb = lib_problem((1, 1, 1), 3, "P2P1", lc=1)
+    with pytest.raises(hhg.HHGError):
+        pb.set_level_smoother(2, 8)          # 5 k planes on level 2
+    with pytest.raises(hhg.HHGError):
+        pb.set_level_smoother(3, -1)
+    with pytest.raises(hhg.HHGError):
+        pb.set_level_smoother(3, 17)
+    pb.set_level_smoother(3, 0)
+    assert pb.level_smoother(3) == 0
+
+
 @pytest.mark.parametrize("disc,box", [("P1P1", (2, 1, 1)), ("P2P1", (1, 1, 2)), ("P2P1", (1, 1, 1))])
 def test_transfer_parity(disc, box):
     L = 2
@@ -305,8 +359,9 @@ def test_autotune_keeps_results():
     pb.fmg_solve(prm, x1, stats=False)
     shapes = pb.autotune(reps=2)
     assert set(shapes) == {1, 2, 3, 4}
-    for t, kp, gs in shapes.values():
-        assert t in (64, 128, 256) and kp in (1, 2, 4) and gs in (64, 128, 256)
+    for t, kp, gs, rc in shapes.values():
+        assert t in (64, 128, 256) and kp in (1, 2, 4, 8, 16) and gs in (64, 128, 256)
+        assert rc in (0, 1, 2, 4, 8, 16)
     x2 = pb.new_vector(4)
     pb.fmg_solve(prm, x2, stats=False)
     torch.cuda.synchronize()
