@@ -212,9 +212,9 @@ int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats
  * hhg_set_level_smoother): every candidate is timed `reps` times with CUDA
  * events on the problem's stream in the precision of the V-cycles, the
  * fastest is kept.  Uses only the library's scratch vectors; cached graphs
- * are dropped.  shapes_out (optional) receives 4 ints per level (coarse ..
- * L): row threads, row k planes, Gauss-Seidel threads, resident CTAs.
- * Synchronises. */
+ * are dropped.  shapes_out (optional) receives 5 ints per level (coarse ..
+ * L): row threads, row k planes, Gauss-Seidel threads, resident CTAs and
+ * resident threads per CTA.  Synchronises. */
 int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
 
 /* ------------------------------------------- learned coarse-grid correction */
@@ -293,16 +293,19 @@ int hhg_set_graph_mode(hhg_problem* pb, int on);
  * launch per phase everywhere.  Both give the same iterates. */
 int hhg_set_small_level_mode(hhg_problem* pb, int on);
 /* Not in the paper (a GPU execution choice, Sec. 3.2's smoother unchanged):
- * the number of CTAs `ctas` (1..16, one thread-block cluster) that run all
- * phases of the Uzawa smoother of `level` in precision `prec` in one launch
- * with the level's block vector held in their shared memory (a slab of k
- * planes per CTA), or 0 for one launch per phase.  HHG_EINVAL if the level
- * does not fit (at most 227 KB of slab per CTA, at least one plane per CTA,
- * the cluster must be schedulable).  Default at bind: the fewest CTAs (<= 8)
- * with at most 8192 lattice sites each, else 0; hhg_autotune times all
- * choices.  Drops cached graphs.  The iterates do not depend on the choice. */
-int hhg_set_level_smoother(hhg_problem* pb, int level, int prec, int ctas);
-int hhg_get_level_smoother(hhg_problem* pb, int level, int prec, int* ctas);
+ * the number of CTAs `ctas` (1..16, one thread-block cluster) of `threads`
+ * threads (a multiple of 32 in 128..1024; 0 = 1024) that run all phases of
+ * the Uzawa smoother of `level` in precision `prec` in one launch with the
+ * level's block vector held in their shared memory (a slab of k planes per
+ * CTA), or ctas = 0 for one launch per phase.  HHG_EINVAL if the level does
+ * not fit (at most 227 KB of slab, residuals and tables per CTA, at least one
+ * plane per CTA, the cluster must be schedulable).  Default at bind: the
+ * fewest CTAs (<= 8) with at most 8192 lattice sites each, 1024 threads,
+ * else 0; hhg_autotune times the choices.  Drops cached graphs.  The iterates
+ * agree up to the rounding of the precision (the resident kernel adds the
+ * terms of a row in another order). */
+int hhg_set_level_smoother(hhg_problem* pb, int level, int prec, int ctas, int threads);
+int hhg_get_level_smoother(hhg_problem* pb, int level, int prec, int* ctas, int* threads);
 /* omega^{-1}: `iters` power iterations on M_L^{-1}(C + B A_s^{-1} B^T)
  * (Eq. omega-eigenvalue-problem) from the host start vector v0 (canonical
  * pressure order). */

@@ -130,11 +130,11 @@ struct Level {
   // parameter blocks of the specialised kernels (FastTab<T, N> images)
   std::vector<char> ftab64[OP_COUNT], ftab32[OP_COUNT];
   bool has_fast[OP_COUNT] = {};
-  // parameter blocks of the shared-memory-resident smoother: global-stride
-  // images, and per CTA count the images localised to the slab stride
-  std::vector<char> stab64, stab32;
+  // parameter blocks (ResTabs images) of the shared-memory-resident
+  // smoother, per CTA count (the offsets depend on the slab stride)
   std::map<int, std::vector<char>> rtab64, rtab32;
   int rctas[2] = {0, 0};                // CTAs of the resident smoother per precision (0: per-phase kernels)
+  int rthreads[2] = {kResidentThreads, kResidentThreads};   // and threads per CTA
   Shape shape;                          // launch shapes of the specialised kernels
   // workspace offsets (bytes) of the level vectors
   size_t o_rhs, o_W, o_x64, o_tmp64, o_bw64, o_x32, o_b32, o_tmp32, o_invml, o_ml, o_esc;
@@ -359,19 +359,6 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
   };
   put_x(pb->tv, pb->xoff_v);
   put_x(pb->tp, pb->xoff_p);
-  // tables of the shared-memory-resident smoother
-  for (Level& lv : pb->lv) {
-    auto pack = [&](int prec, const std::vector<char>* src, std::vector<char>& out) {
-      out.assign(small_tabs_bytes(desc->disc, varnu, prec), 0);
-      const int ops[3] = {OP_A, OP_BT, OP_BC};
-      for (int w = 0; w < 3; ++w) {
-        const size_t off = small_tabs_offset(desc->disc, varnu, prec, w);
-        std::memcpy(out.data() + off, src[ops[w]].data(), src[ops[w]].size());
-      }
-    };
-    pack(HHG_FP64, lv.ftab64, lv.stab64);
-    pack(HHG_FP32, lv.ftab32, lv.stab32);
-  }
 
   // ---- workspace layout
   size_t off = 0;
@@ -608,17 +595,72 @@ double level_weight(hhg_problem* pb, const Level& lv) {
 }
 
 template <class T> constexpr int prec_index() { return sizeof(T) == 8 ? HHG_FP64 : HHG_FP32; }
-template <class T> const void* rtab(Level& lv, int C);
-template <> const void* rtab<double>(Level& lv, int C) { return lv.rtab64.at(C).data(); }
-template <> const void* rtab<float>(Level& lv, int C) { return lv.rtab32.at(C).data(); }
+template <class T> const ResTabs<T>& rtab(Level& lv, int C);
+template <> const ResTabs<double>& rtab<double>(Level& lv, int C) {
+  return *reinterpret_cast<const ResTabs<double>*>(lv.rtab64.at(C).data());
+}
+template <> const ResTabs<float>& rtab<float>(Level& lv, int C) {
+  return *reinterpret_cast<const ResTabs<float>*>(lv.rtab32.at(C).data());
+}
+
+// true if a linear offset di + dj sx + dk sy reaches only adjacent sites
+bool adjacent(const Geo& g, int64_t off) {
+  const int64_t dk = std::llround(double(off) / double(g.sy));
+  const int64_t dj = std::llround(double(off - dk * g.sy) / double(g.sx));
+  const int64_t di = off - dk * g.sy - dj * g.sx;
+  return dk >= -1 && dk <= 1 && dj >= -1 && dj <= 1 && di >= -1 && di <= 1;
+}
+
+// the resident smoother's parameter block for slab stride arr_l: rows and
+// terms of A (component 0 of each group), B^T and (B, -C) from the level's
+// stencil tables, offsets rewritten to the slab stride
+template <class T>
+int build_res_tabs(hhg_problem* pb, Level& lv, int64_t arr_l, std::vector<char>& out) {
+  out.assign(sizeof(ResTabs<T>), 0);
+  ResTabs<T>& rt = *reinterpret_cast<ResTabs<T>*>(out.data());
+  const int G = lv.g.G;
+  rt.G = G;
+  rt.nbt = 3 * G;
+  rt.varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
+  const char* blob = pb->tables.bytes.data();
+  int nw = 0;
+  auto add = [&](int op, int r, ResRow& dst) {
+    const OpOffsets& of = lv.opoff[op];
+    if (r >= of.nrows) return false;
+    const DRow& d = reinterpret_cast<const DRow*>(blob + of.rows)[r];
+    const DTerm* terms = reinterpret_cast<const DTerm*>(blob + of.terms);
+    const double* w = reinterpret_cast<const double*>(blob + of.w64);
+    const int n = d.n0 + d.n1 + d.n2;
+    if (nw + n > kResMaxTerms) return false;
+    dst = ResRow{d.out_arr, d.og, d.all_rows, nw, d.n0, d.n1, d.n2, d.b0 + d.m0 + d.m1, d.m2};
+    for (int t = d.t0; t < d.t0 + n; ++t) {
+      if (terms[t].arr < 0 || terms[t].arr > 3 * G || !adjacent(lv.g, terms[t].off)) return false;
+      rt.w[nw] = T(w[t]);
+      rt.off[nw] = int(terms[t].arr * arr_l + terms[t].off);
+      ++nw;
+    }
+    return true;
+  };
+  bool ok = G <= 8 && 3 * G <= kResMaxRows;
+  for (int gg = 0; ok && gg < G; ++gg) {
+    ok = add(OP_A, gg, rt.A[gg]);
+    ok = ok && rt.A[gg].n0 == 0 && rt.A[gg].n2 == 0 && rt.A[gg].n1 > 0;   // diagonal first, all in segment 1
+  }
+  for (int r = 0; ok && r < 3 * G; ++r) ok = add(OP_BT, r, rt.BT[r]);
+  ok = ok && add(OP_BC, 0, rt.BC);
+  if (!ok) return fail(HHG_EINVAL, "internal: stencil tables do not fit the resident smoother");
+  rt.nw = nw;
+  return HHG_OK;
+}
 
 // selects `ctas` CTAs (0: per-phase kernels) for the resident smoother of a
 // level in precision `prec`; HHG_EINVAL if the level does not fit
-int set_resident(hhg_problem* pb, Level& lv, int prec, int ctas) {
+int set_resident(hhg_problem* pb, Level& lv, int prec, int ctas, int threads = kResidentThreads) {
   if (ctas < 0 || ctas > kResidentMaxCtas) return fail(HHG_EINVAL, "ctas must be in 0..16");
+  if (threads < 128 || threads > kResidentThreads || threads % 32)
+    return fail(HHG_EINVAL, "threads must be a multiple of 32 in 128..1024");
   if (ctas > 0) {
-    const int varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
-    if (!resident_feasible(pb->desc.disc, varnu, prec, lv.g, ctas))
+    if (!resident_feasible(prec, lv.g, ctas))
       return fail(HHG_EINVAL, "level does not fit the shared memory of that many CTAs");
     // the per-cube boundary terms of (B, -C) must stay within the adjacent
     // sites, as the slab holds one halo plane on each side
@@ -636,23 +678,22 @@ int set_resident(hhg_problem* pb, Level& lv, int prec, int ctas) {
     auto& cache = prec == HHG_FP64 ? lv.rtab64 : lv.rtab32;
     if (!cache.count(ctas)) {
       std::vector<char> img;
-      if (!small_tabs_localise(pb->desc.disc, varnu, prec, prec == HHG_FP64 ? lv.stab64 : lv.stab32, lv.g,
-                               resident_arr(lv.g, ctas), img))
-        return fail(HHG_EINVAL, "internal: stencil offsets beyond adjacent sites");
+      if (prec == HHG_FP64) HHG_TRY(build_res_tabs<double>(pb, lv, resident_arr(lv.g, ctas), img));
+      else HHG_TRY(build_res_tabs<float>(pb, lv, resident_arr(lv.g, ctas), img));
       cache[ctas] = std::move(img);
     }
   }
   lv.rctas[prec] = ctas;
+  lv.rthreads[prec] = threads;
   return HHG_OK;
 }
 
 // default CTA count: the fewest CTAs (at most 8) that hold the level with at
 // most 8192 lattice sites each, else none (per-phase kernels)
 int default_resident(hhg_problem* pb, Level& lv, int prec) {
-  const int varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
   const int64_t plane = int64_t(lv.g.nx + 1) * (lv.g.ny + 1), nzp = lv.g.nz + 1;
   for (int C : {1, 2, 4, 8})
-    if (plane * ((nzp + C - 1) / C) <= 8192 && resident_feasible(pb->desc.disc, varnu, prec, lv.g, C))
+    if (plane * ((nzp + C - 1) / C) <= 8192 && resident_feasible(prec, lv.g, C))
       return set_resident(pb, lv, prec, C);
   return set_resident(pb, lv, prec, 0);
 }
@@ -670,8 +711,8 @@ int uzawa(hhg_problem* pb, Level& lv, const hhg_params& prm, int sweeps, T* x, c
     a.ahat = prm.ahat;
     a.inv_omega_inv = 1.0 / prm.omega_inv;
     for (int gg = 0; gg < G; ++gg) a.inv_diag[gg] = lv.inv_diag[gg];
-    if (uzawa_resident<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, lv.g, C, x, b, tmp, lv.inv_mlhat, a,
-                          lv.op[OP_BC], rtab<T>(lv, C), pb->stream) != 0)
+    if (uzawa_resident<T>(lv.g, C, lv.rthreads[prec_index<T>()], x, b, lv.inv_mlhat, a, lv.op[OP_BC], rtab<T>(lv, C),
+                          pb->stream) != 0)
       return fail(HHG_ECUDA, std::string("resident smoother launch: ") + cudaGetErrorString(cudaGetLastError()));
     const Costs cs = block_costs(pb->ov);
     pb->wu_counted += sweeps * level_weight(pb, lv) * (prm.xi * (prm.ahat == HHG_AHAT_S ? 2 : 1) * cs.A + 2 * cs.B + cs.C);
@@ -1328,20 +1369,21 @@ extern "C" int hhg_set_graph_mode(hhg_problem* pb, int on) {
   return HHG_OK;
 }
 
-extern "C" int hhg_set_level_smoother(hhg_problem* pb, int level, int prec, int ctas) {
+extern "C" int hhg_set_level_smoother(hhg_problem* pb, int level, int prec, int ctas, int threads) {
   HHG_TRY(check_level(pb, level));
   if (prec != HHG_FP64 && prec != HHG_FP32) return fail(HHG_EINVAL, "prec must be HHG_FP64 or HHG_FP32");
-  HHG_TRY(set_resident(pb, pb->L(level), prec, ctas));
+  HHG_TRY(set_resident(pb, pb->L(level), prec, ctas, threads == 0 ? kResidentThreads : threads));
   for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
   pb->graphs.clear();
   return HHG_OK;
 }
 
-extern "C" int hhg_get_level_smoother(hhg_problem* pb, int level, int prec, int* ctas) {
+extern "C" int hhg_get_level_smoother(hhg_problem* pb, int level, int prec, int* ctas, int* threads) {
   HHG_TRY(check_level(pb, level));
   if (prec != HHG_FP64 && prec != HHG_FP32) return fail(HHG_EINVAL, "prec must be HHG_FP64 or HHG_FP32");
-  if (!ctas) return fail(HHG_EINVAL, "null argument");
+  if (!ctas || !threads) return fail(HHG_EINVAL, "null argument");
   *ctas = pb->L(level).rctas[prec];
+  *threads = pb->L(level).rthreads[prec];
   return HHG_OK;
 }
 
@@ -1643,17 +1685,17 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
 template <class T>
 int tune_smoother(hhg_problem* pb, Level& lv, int reps, T* x, const T* b, T* tmp) {
   const int prec = prec_index<T>();
-  const int varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
   const size_t bytes = size_t(lv.nvec()) * sizeof(T);
   hhg_params prm{1, 1, 0, 1, HHG_AHAT_F, 2, 0.5};
   cudaEvent_t e0, e1;
   HHG_CUDA(cudaEventCreate(&e0));
   HHG_CUDA(cudaEventCreate(&e1));
-  int best_c = 0;
+  int best_c = 0, best_t = kResidentThreads;
   float best = 1e30f;
-  for (int C : {0, 1, 2, 4, 8, 16}) {
-    if (C > 0 && !resident_feasible(pb->desc.disc, varnu, prec, lv.g, C)) continue;
-    HHG_TRY(set_resident(pb, lv, prec, C));
+  for (int cand = 0; cand < 16; ++cand) {
+    const int C = cand == 0 ? 0 : 1 << ((cand - 1) / 3), th = cand == 0 ? kResidentThreads : 256 << ((cand - 1) % 3);
+    if (C > kResidentMaxCtas || (C > 0 && !resident_feasible(prec, lv.g, C))) continue;
+    HHG_TRY(set_resident(pb, lv, prec, C, th));
     HHG_CUDA(cudaMemsetAsync(x, 0, bytes, pb->stream));
     HHG_CUDA(cudaMemsetAsync(tmp, 0, bytes, pb->stream));
     HHG_TRY(uzawa<T>(pb, lv, prm, 2, x, b, tmp));
@@ -1663,11 +1705,11 @@ int tune_smoother(hhg_problem* pb, Level& lv, int reps, T* x, const T* b, T* tmp
     HHG_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; best_c = C; }
+    if (ms < best) { best = ms; best_c = C; best_t = th; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  HHG_TRY(set_resident(pb, lv, prec, best_c));
+  HHG_TRY(set_resident(pb, lv, prec, best_c, best_t));
   HHG_CUDA(cudaMemsetAsync(x, 0, bytes, pb->stream));
   HHG_CUDA(cudaMemsetAsync(tmp, 0, bytes, pb->stream));
   HHG_CUDA(cudaStreamSynchronize(pb->stream));
@@ -1690,9 +1732,10 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       HHG_TRY(tune_smoother<double>(pb, lv, reps, lv.bw64, lv.rhs, lv.tmp64));
     }
     if (shapes_out) {
-      int* o = shapes_out + 4 * (l - pb->desc.coarse_level);
+      int* o = shapes_out + 5 * (l - pb->desc.coarse_level);
       o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
       o[3] = lv.rctas[mixed ? HHG_FP32 : HHG_FP64];
+      o[4] = lv.rthreads[mixed ? HHG_FP32 : HHG_FP64];
     }
   }
   pb->wu_counted = wu;

@@ -12,259 +12,340 @@
 //  * CTA c owns the k planes [c (nz+1) / C, (c+1) (nz+1) / C) of every array
 //    (velocity groups and pressure) and stores them, plus one halo plane
 //    below and above, in the global array layout with a local array stride,
-//    so the stencil offsets keep their in-array part (di + dj sx + dk sy);
-//  * a phase updates the CTA's own sites from shared memory; after a cluster
-//    barrier every CTA copies the sites the phase changed in its neighbours'
-//    boundary planes into its own halo planes (distributed shared memory);
-//  * the right-hand side is read through the read-only path; the residuals
-//    tmp = b - B^T p and g - (B u - C p) go to global memory and are read back
-//    only by the CTA that wrote them (visible after __syncthreads).
+//    so a stencil offset is array * arr_l + di + dj sx + dk sy;
+//  * a phase updates the CTA's own sites from shared memory; a value written
+//    to a boundary plane is also stored into the neighbour's halo plane
+//    (distributed shared memory), and a cluster barrier ends the phase;
+//  * a phase has few sites, so each row is shared by P lanes (P = 1..32,
+//    chosen per phase from the number of rows): lane p takes the terms
+//    p, p+P, ... and the partial sums are added by a butterfly of shuffles;
+//  * the residuals tmp = b - B^T p and g - (B u - C p) and the scaled inverse
+//    lumped pressure mass omega M_L^{-1} of the owned planes stay in shared
+//    memory too; the right-hand side is read through the read-only path,
+//    issued before the row sums so that its latency overlaps them.
 //
-// A phase only ever updates sites that no site of the same phase reads (a
-// vertex colour, or one edge group), so the copy after phase p never races
-// with the writes of phase p+1.  The one exception, the same phase twice in a
-// row at the turn of a symmetric sweep, is skipped: with no coupling inside a
-// phase its second application reproduces the same values.  Phase order,
-// arithmetic and the row/term order are those of fast.cu, so the iterates
-// equal those of the per-phase launches.
+// A Gauss-Seidel phase only ever updates sites that no site of the same phase
+// reads (a vertex colour, or one edge group), so the halo stores of a phase
+// never touch values read in that phase.  The same phase twice in a row, at
+// the turn of a symmetric sweep, is skipped: with no coupling inside a phase
+// its second application reproduces the same values.  The pressure update,
+// whose halo stores would reach values the (B, -C) residual reads, follows
+// that residual after a cluster barrier.  Phase order and arithmetic are
+// those of the per-phase kernels; only the order in which the terms of one
+// row are added differs (partial sums per lane).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
-#include <cmath>
-#include <cstring>
-#include <type_traits>
-
-#include "fast.h"
 #include "kernels.h"
 #include "small.h"
-#include "structure.inc"
 
 namespace cg = cooperative_groups;
 
 namespace hhg {
 namespace {
 
-template <class S, int R, class F>
-__device__ __forceinline__ void sdispatch(int r, F&& f) {
-  if constexpr (R < S::R) {
-    if (r == R) f(std::integral_constant<int, R>{});
-    else sdispatch<S, R + 1>(r, f);
-  }
+template <class T> __device__ __forceinline__ T bw(const OpDev& op, int t);
+template <> __device__ __forceinline__ double bw<double>(const OpDev& op, int t) { return __ldg(op.bw64 + t); }
+template <> __device__ __forceinline__ float bw<float>(const OpDev& op, int t) { return __ldg(op.bw32 + t); }
+
+// offset bits of an output group: x for groups 1,4,5,7, y for 2,4,6,7, z for 3,5,6,7
+__device__ __forceinline__ int gox(int og) { return (0xB2 >> og) & 1; }
+__device__ __forceinline__ int goy(int og) { return (0xD4 >> og) & 1; }
+__device__ __forceinline__ int goz(int og) { return (0xE8 >> og) & 1; }
+
+template <class T>
+__device__ __forceinline__ T group_sum(T v, int P) {
+  for (int m = P >> 1; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
 }
 
-template <int T0, int N, class T, class Tab>
-__device__ __forceinline__ T sseg(const Tab& tab, const T* xl) {
-  T a = T(0);
-#pragma unroll
-  for (int t = 0; t < N; ++t) a += tab.w[T0 + t] * xl[tab.off[T0 + t]];
-  return a;
+// floor(n / d) for 0 <= n < 2^22, d >= 1 and rd = 1/d rounded: the float
+// quotient is off by at most one, fixed by one comparison
+__device__ __forceinline__ int qdiv(int n, int d, float rd) {
+  int q = __float2int_rz(__int2float_rn(n) * rd);
+  if (q * d > n) --q;
+  else if ((q + 1) * d <= n) ++q;
+  return q;
 }
 
-template <class T> __device__ __forceinline__ T sbw(const OpDev& op, int t);
-template <> __device__ __forceinline__ double sbw<double>(const OpDev& op, int t) { return __ldg(op.bw64 + t); }
-template <> __device__ __forceinline__ float sbw<float>(const OpDev& op, int t) { return __ldg(op.bw32 + t); }
+// one phase of the smoother in one CTA: its rows (instances), lanes per row
+// (2^lp), lanes in whole warps, and the mixed-radix decomposition of an
+// instance index (up to three divisors with their reciprocals) into the row
+// kind and the site relative to (i0, j0, kf)
+struct PhaseDesc {
+  int ninst, lp, total;
+  int d0, d1, d2;
+  float r0, r1, r2;
+  int kf, i0, j0;
+};
 
-// y = b - (row of S at site (i,j,k)); x from the shared slab (local index il,
-// local array stride arr_l), b and y in global memory (index ig); boundary
-// rules as in fast.cu
-template <int VARNU, int OUT, int OG, int ALL, int T0, int N0, int N1, int N2, class T, class Tab>
-__device__ __forceinline__ void rres_row(const Geo& g, int arr_l, int R, int i, int j, int k, int64_t ig, int il,
-                                         const T* xs, const T* __restrict__ b, T* y, const OpDev& op,
-                                         const Tab& tab) {
-  constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
-  constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
-  constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
-  if (i > g.nx - ox || j > g.ny - oy || k > g.nz - oz) return;
-  const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
-  const bool bnd = Px == 0 || Py == 0 || Pz == 0 || Px == 2 * g.nx || Py == 2 * g.ny || Pz == 2 * g.nz;
-  T* yo = y + int64_t(OUT) * g.arr + ig;
-  if (bnd && !ALL) {
-    *yo = T(0);
-    return;
-  }
-  const T* xl = xs + il;
-  const T a0 = sseg<T0, N0, T>(tab, xl);
-  const T a1 = sseg<T0 + N0, N1, T>(tab, xl);
-  T a2;
-  if (!bnd) {
-    a2 = sseg<T0 + N0 + N1, N2, T>(tab, xl);
-  } else {
-    a2 = T(0);
-    if (N2 > 0) {
-      const DRow row = op.rows[R];
-      for (int t = row.b0 + row.m0 + row.m1; t < row.b0 + row.m0 + row.m1 + row.m2; ++t) {
-        const DTermB tm = op.bterms[t];
-        const int qx = i + tm.cx, qy = j + tm.cy, qz = k + tm.cz;
-        if (qx < 0 || qy < 0 || qz < 0 || qx >= g.nx || qy >= g.ny || qz >= g.nz) continue;
-        a2 += sbw<T>(op, t) * xs[tm.arr * arr_l + il + tm.off];
-      }
-    }
-  }
-  T v = a0;
-  if (VARNU) {
-    v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
-  } else {
-    v += a1 + a2;
-  }
-  *yo = __ldg(b + int64_t(OUT) * g.arr + ig) - v;
+// lanes per row: enough to hide the latency of a row sum, few enough that
+// the shuffles and the index arithmetic do not outweigh the terms (about
+// four terms per lane, at most `cap` lanes in the phase)
+__device__ __forceinline__ int lanes_log2(int n, int terms, int cap) {
+  int lp = 0;
+  while (lp < 5 && (1 << lp) * 4 < terms && n * (2 << lp) <= cap) ++lp;
+  return lp;
 }
 
-// one Gauss-Seidel update of the three velocity components of group GRP at
-// site (i,j,k) (Dirichlet sites are left alone)
-template <int VARNU, int GRP, int T0, int N1, class T, class Tab>
-__device__ __forceinline__ void rgs(const Geo& g, int arr_l, int i, int j, int k, int64_t ig, int il, T* xs,
-                                    const T* tmp, T inv_diag, const Tab& tab) {
-  constexpr int ox = GRP == 1 || GRP == 4 || GRP == 5 || GRP == 7;
-  constexpr int oy = GRP == 2 || GRP == 4 || GRP == 6 || GRP == 7;
-  constexpr int oz = GRP == 3 || GRP == 5 || GRP == 6 || GRP == 7;
-  const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
-  if (Px <= 0 || Py <= 0 || Pz <= 0 || Px >= 2 * g.nx || Py >= 2 * g.ny || Pz >= 2 * g.nz) return;
-  const int csl = g.G * arr_l;
-  const T* us = xs + il;
-  T a0 = T(0), a1 = T(0), a2 = T(0);
-#pragma unroll
-  for (int t = 1; t < N1; ++t) {               // the diagonal is the first term
-    const T wt = tab.w[T0 + t];
-    const int o = tab.off[T0 + t];
-    a0 += wt * us[o];
-    a1 += wt * us[o + csl];
-    a2 += wt * us[o + 2 * csl];
-  }
-  T einv = T(1);
-  if (VARNU) einv = T(g.eisc[k]);
-  const int ol = GRP * arr_l + il;
-  const int64_t og = int64_t(GRP) * g.arr + ig, csg = int64_t(g.G) * g.arr;
-  xs[ol] = (tmp[og] * einv - a0) * inv_diag;
-  xs[ol + csl] = (tmp[og + csg] * einv - a1) * inv_diag;
-  xs[ol + 2 * csl] = (tmp[og + 2 * csg] * einv - a2) * inv_diag;
+__device__ __forceinline__ void set_desc(PhaseDesc& d, int ninst, int terms, int cap, int d0, int d1, int d2, int kf,
+                                         int i0, int j0) {
+  d.ninst = ninst;
+  d.lp = lanes_log2(ninst, terms, cap);
+  d.total = ((ninst << d.lp) + 31) & ~31;
+  d.d0 = max(d0, 1);
+  d.d1 = max(d1, 1);
+  d.d2 = max(d2, 1);
+  d.r0 = 1.0f / float(d.d0);
+  d.r1 = 1.0f / float(d.d1);
+  d.r2 = 1.0f / float(d.d2);
+  d.kf = kf;
+  d.i0 = i0;
+  d.j0 = j0;
 }
 
-template <int DISC, int VARNU, class T>
+// lanes that may share the rows of a Gauss-Seidel or B^T phase
+constexpr int kPhaseLanes = 256;
+
+template <class T>
 __global__ void __launch_bounds__(kResidentThreads)
-    k_uzawa_resident(Geo g, int arr_l, T* xg, const T* __restrict__ b, T* tmp, const double* __restrict__ inv_ml,
-                     SmallArgs a, OpDev bc_op, const __grid_constant__ SmallTabs<DISC, VARNU, T> tabs) {
-  using SA = gen::S<DISC, VARNU, OP_A>;
-  using SBT = gen::S<DISC, VARNU, OP_BT>;
-  using SBC = gen::S<DISC, VARNU, OP_BC>;
-  constexpr int G = DISC == 1 ? 1 : 8;
-  constexpr int NA = 3 * G + 1;                 // arrays of the block vector
+    k_uzawa_resident(Geo g, int arr_l, int arr_t, T* xg, const T* __restrict__ b, const double* __restrict__ inv_ml,
+                     SmallArgs a, OpDev bc_op, const __grid_constant__ ResTabs<T> tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ PhaseDesc sd[13];                     // GS phases 0..nph-1, then B^T, then (B, -C)
+  __shared__ T sdiag[8];
+  const int G = tb.G, NA = 3 * G + 1;
+  // shared memory: the slab (NA arrays of stride arr_l, owned planes plus
+  // halos), the residuals of the owned planes (NA arrays of stride arr_t,
+  // local plane kl at kl sy), omega M_L^{-1} (one array of stride arr_t), tables
   T* xs = reinterpret_cast<T*>(smem_raw);
+  T* ts = xs + NA * arr_l;
+  T* mls = ts + NA * arr_t;
+  T* sw = mls + arr_t;
+  int* soff = reinterpret_cast<int*>(sw + tb.nw);
   cg::cluster_group cluster = cg::this_cluster();
   const int C = int(cluster.num_blocks()), c = int(cluster.block_rank());
   const int nxp = g.nx + 1, nyp = g.ny + 1, nzp = g.nz + 1;
   const int kb = c * nzp / C, ke = (c + 1) * nzp / C, nk = ke - kb;
   const int sx = g.sx, sy = int(g.sy);
-  const int tid = int(threadIdx.x), nthr = int(blockDim.x);
+  const int tid = int(threadIdx.x), nthr = int(blockDim.x), wbase = tid & ~31;
+  const bool varnu = tb.varnu != 0;
+  const int nph = 4 + (G - 1);
+  // neighbours' slabs: my plane kb is the lower neighbour's upper halo plane
+  // (local plane nk_lo + 1), my plane ke-1 the upper neighbour's plane 0
+  T* lo = (C > 1 && c > 0) ? cluster.map_shared_rank(xs, c - 1) : nullptr;
+  T* hi = (C > 1 && c < C - 1) ? cluster.map_shared_rank(xs, c + 1) : nullptr;
+  const int nk_lo = c > 0 ? kb - (c - 1) * nzp / C : 0;
   auto bar = [&] {
     if (C > 1) cluster.sync();
     else __syncthreads();
   };
+  auto store = [&](int li, int kl, T v) {          // slab value and its halo copies
+    xs[li] = v;
+    if (kl == 0 && lo) lo[li + nk_lo * sy] = v;
+    if (kl == nk - 1 && hi) hi[li - nk * sy] = v;
+  };
+
+  for (int t = tid; t < tb.nw; t += nthr) {
+    sw[t] = tb.w[t];
+    soff[t] = tb.off[t];
+  }
+  if (tid < G) sdiag[tid] = T(a.inv_diag[tid]);
+  if (tid < nph) {
+    // Gauss-Seidel phase: interior sites of the group, i in [1-ox, nx-1],
+    // j in [1-oy, ny-1], k in [1-oz, nz-1] within the slab; a vertex colour
+    // takes every fourth i of a row
+    const int ph = tid, grp = ph < 4 ? 0 : ph - 3, colour = ph < 4 ? ph : -1;
+    const int i0 = 1 - gox(grp), j0 = 1 - goy(grp), kf = max(kb, 1 - goz(grp));
+    const int nkk = max(0, min(ke, g.nz) - kf), nj = g.ny - j0, nis = colour >= 0 ? (g.nx + 2) / 4 : g.nx - i0;
+    set_desc(sd[ph], nis * nj * nkk, tb.A[grp].n1 - 1, kPhaseLanes, nis * nj, nis, 1, kf, i0, j0);
+  } else if (tid == nph) {
+    // B^T rows of every (component, group) at i < nx, j < ny, k < nz
+    const int kf = max(kb, 0), nkk = max(0, min(ke, g.nz) - kf), Vb = g.nx * g.ny * nkk;
+    int terms = 0;
+    for (int r = 0; r < tb.nbt; ++r) terms = max(terms, tb.BT[r].n0 + tb.BT[r].n1 + tb.BT[r].n2);
+    set_desc(sd[nph], tb.nbt * Vb, terms, kPhaseLanes, Vb, g.nx * g.ny, g.nx, kf, 0, 0);
+  } else if (tid == nph + 1) {
+    // the pressure row at every pressure site of the owned planes
+    set_desc(sd[nph + 1], nxp * nyp * nk, tb.BC.n0 + tb.BC.n1 + tb.BC.n2, nthr, nxp * nyp, nxp, 1, kb, 0, 0);
+  }
   // owned planes kb .. ke-1 and the halo planes kb-1, ke (global plane k
-  // starts at (k+1) sy, local plane k-kb+1 at (k-kb+1) sy)
+  // starts at (k+1) sy, local plane k-kb+1 at (k-kb+1) sy); residuals start
+  // at 0 so that the lattice's zero ring stays 0 in the pressure update
   {
     const int span = (nk + 2) * sy;
     for (int q = tid; q < NA * span; q += nthr) {
       const int ar = q / span, r = q - ar * span;
       xs[ar * arr_l + r] = xg[int64_t(ar) * g.arr + int64_t(kb) * sy + r];
     }
+    for (int r = tid; r < nk * sy; r += nthr) mls[r] = T(a.inv_omega_inv * inv_ml[int64_t(kb + 1) * sy + r]);
+    for (int r = tid; r < NA * arr_t; r += nthr) ts[r] = T(0);
   }
-  bar();                                         // every CTA of the cluster runs before any remote access
+  bar();                                           // every CTA runs before any remote store
 
-  // copy the sites of arrays a0, a0+astep, ... (na arrays) that the last
-  // phase changed from the neighbours' boundary planes into the halo planes
-  auto pull = [&](int a0, int na, int astep, int colour) {
-    if (C == 1) return;
-    for (int side = 0; side < 2; ++side) {
-      if ((side == 0 && c == 0) || (side == 1 && c == C - 1)) continue;
-      const int nb = side == 0 ? c - 1 : c + 1;
-      const int kh = side == 0 ? kb - 1 : ke;          // global plane of the halo
-      const int src = kh - nb * nzp / C + 1;           // its local plane in the neighbour
-      const int dst = side == 0 ? 0 : nk + 1;
-      const T* rem = cluster.map_shared_rank(xs, nb);
-      for (int q = tid; q < na * sy; q += nthr) {
-        const int aa = q / sy, e = q - aa * sy;
-        if (colour >= 0) {
-          const int jj = e / sx - 1, ii = e - (jj + 1) * sx - 1;
-          if (ii < 0 || jj < 0 || ii > g.nx || jj > g.ny || ((ii + jj + kh) & 3) != colour) continue;
+  const int pol = 3 * G * arr_l, pot = 3 * G * arr_t;
+  const int csl = G * arr_l, cst = G * arr_t;
+  const float rsy = 1.0f / float(sy);
+  for (int it = 0; it < a.iterations; ++it) {
+    // ---- velocity step: tmp_u = b_u - B^T p at the interior sites of every
+    // group (Dirichlet rows are never read)
+    if (wbase < sd[nph].total) {
+      const PhaseDesc d = sd[nph];
+      const int P = 1 << d.lp;
+      for (int q = tid; q < d.total; q += nthr) {  // whole warps: the shuffles see all lanes
+        const int inst = q >> d.lp, p = q & (P - 1);
+        const bool valid = inst < d.ninst;
+        int r = 0, i = 0, j = 0, k = d.kf;
+        if (valid) {
+          r = qdiv(inst, d.d0, d.r0);
+          const int s = inst - r * d.d0, kk = qdiv(s, d.d1, d.r1), rem = s - kk * d.d1;
+          j = qdiv(rem, d.d2, d.r2);
+          i = rem - j * d.d2;
+          k += kk;
         }
-        const int ar = a0 + aa * astep;
-        xs[ar * arr_l + dst * sy + e] = rem[ar * arr_l + src * sy + e];
+        const ResRow rw = tb.BT[r];
+        const bool ok = valid && (i > 0 || gox(rw.og)) && (j > 0 || goy(rw.og)) && (k > 0 || goz(rw.og));
+        const int kl = k - kb;
+        const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
+        const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(k + 1) * sy;
+        const T bv = (ok && p == 0) ? __ldg(b + int64_t(rw.out) * g.arr + ig) : T(0);
+        T a0 = T(0), a1 = T(0), a2 = T(0);
+        if (ok) {
+          const T* xl = xs + il;
+          const int e0 = rw.t0 + rw.n0, e1 = e0 + rw.n1, e2 = e1 + rw.n2;
+          for (int t = rw.t0 + p; t < e0; t += P) a0 += sw[t] * xl[soff[t]];
+          for (int t = e0 + p; t < e1; t += P) a1 += sw[t] * xl[soff[t]];
+          for (int t = e1 + p; t < e2; t += P) a2 += sw[t] * xl[soff[t]];
+        }
+        if (P > 1) {
+          a0 = group_sum(a0, P);
+          a1 = group_sum(a1, P);
+          a2 = group_sum(a2, P);
+        }
+        if (ok && p == 0) {
+          T v = a0;
+          if (varnu) v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
+          else v += a1 + a2;
+          ts[rw.out * arr_t + il - sy] = bv - v;
+        }
       }
     }
     __syncthreads();
-  };
-
-  const int plane = nxp * nyp, Vl = plane * nk;
-  const int64_t pog = 3 * int64_t(G) * g.arr;
-  const int pol = 3 * G * arr_l;
-  for (int it = 0; it < a.iterations; ++it) {
-    // velocity step: tmp_u = b_u - B^T p
-    for (int q = tid; q < SBT::R * Vl; q += nthr) {
-      const int r = q / Vl, s = q - r * Vl;
-      const int kl = s / plane, rem = s - kl * plane, j = rem / nxp, i = rem - j * nxp;
-      const int k = kb + kl;
-      const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
-      const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(k + 1) * sy;
-      sdispatch<SBT, 0>(r, [&](auto rc) {
-        constexpr int R = decltype(rc)::value;
-        constexpr gen::RowS rw = SBT::rows[R];
-        rres_row<VARNU, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, arr_l, R, i, j, k, ig, il, xs, b, tmp,
-                                                                           bc_op, tabs.BT);
-      });
-    }
-    __syncthreads();
-    // xi Gauss-Seidel sweeps on A u = tmp_u (forward, and backward for A_s)
-    constexpr int nph = 4 + (G - 1);
+    // ---- xi Gauss-Seidel sweeps on A u = tmp_u (forward, and backward for A_s)
     int prev = -1;
-    for (int sw = 0; sw < a.xi; ++sw) {
+    for (int sw_ = 0; sw_ < a.xi; ++sw_) {
       for (int pass = 0; pass < (a.ahat == HHG_AHAT_S ? 2 : 1); ++pass) {
         for (int pi = 0; pi < nph; ++pi) {
           const int ph = pass == 0 ? pi : nph - 1 - pi;
           if (ph == prev) continue;
           prev = ph;
-          const int grp = ph < 4 ? 0 : ph - 3;
-          const int colour = ph < 4 ? ph : -1;
-          const int w = colour >= 0 ? (nxp + 3) / 4 : nxp;
-          for (int q = tid; q < w * nyp * nk; q += nthr) {
-            const int kl = q / (w * nyp), rem = q - kl * w * nyp, j = rem / w;
-            const int k = kb + kl;
-            int i = rem - j * w;
-            if (colour >= 0) i = 4 * i + (((colour - j - k) % 4) + 4) % 4;
-            const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
-            const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(k + 1) * sy;
-            sdispatch<SA, 0>(grp, [&](auto rc) {
-              constexpr int GR = decltype(rc)::value;
-              if constexpr (GR < G) {
-                constexpr gen::RowS rw = SA::rows[GR];
-                rgs<VARNU, GR, rw.t0, rw.n1>(g, arr_l, i, j, k, ig, il, xs, tmp, T(a.inv_diag[GR]), tabs.A);
+          if (wbase < sd[ph].total) {
+            const PhaseDesc d = sd[ph];
+            const int grp = ph < 4 ? 0 : ph - 3, colour = ph < 4 ? ph : -1;
+            const int P = 1 << d.lp;
+            const ResRow rw = tb.A[grp];
+            const T inv_diag = sdiag[grp];
+            for (int q = tid; q < d.total; q += nthr) {
+              const int inst = q >> d.lp, p = q & (P - 1);
+              int i = 0, j = 0, k = d.kf;
+              bool ok = false;
+              if (inst < d.ninst) {
+                const int kk = qdiv(inst, d.d0, d.r0), rem = inst - kk * d.d0, jj = qdiv(rem, d.d1, d.r1);
+                const int ii = rem - jj * d.d1;
+                j = d.j0 + jj;
+                k += kk;
+                i = colour >= 0 ? 1 + (((colour - j - k - 1) % 4) + 4) % 4 + 4 * ii : d.i0 + ii;
+                ok = i <= g.nx - 1;
               }
-            });
+              const int kl = k - kb;
+              const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
+              T a0 = T(0), a1 = T(0), a2 = T(0);
+              if (ok) {
+                const T* us = xs + il;
+                for (int t = rw.t0 + 1 + p; t < rw.t0 + rw.n1; t += P) {   // the diagonal is the first term
+                  const T wt = sw[t];
+                  const int o = soff[t];
+                  a0 += wt * us[o];
+                  a1 += wt * us[o + csl];
+                  a2 += wt * us[o + 2 * csl];
+                }
+              }
+              if (P > 1) {
+                a0 = group_sum(a0, P);
+                a1 = group_sum(a1, P);
+                a2 = group_sum(a2, P);
+              }
+              if (ok && p == 0) {
+                const T einv = varnu ? T(g.eisc[k]) : T(1);
+                const int ol = grp * arr_l + il, ot = grp * arr_t + il - sy;
+                store(ol, kl, (ts[ot] * einv - a0) * inv_diag);
+                store(ol + csl, kl, (ts[ot + cst] * einv - a1) * inv_diag);
+                store(ol + 2 * csl, kl, (ts[ot + 2 * cst] * einv - a2) * inv_diag);
+              }
+            }
           }
           bar();
-          pull(grp, 3, G, colour);
         }
       }
     }
-    // pressure step: tmp_p = g - (B u - C p), then p -= tmp_p / (omega^{-1} M_L)
-    for (int q = tid; q < Vl; q += nthr) {
-      const int kl = q / plane, rem = q - kl * plane, j = rem / nxp, i = rem - j * nxp;
-      const int k = kb + kl;
-      const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
-      const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(k + 1) * sy;
-      constexpr gen::RowS rw = SBC::rows[0];
-      rres_row<VARNU, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, arr_l, 0, i, j, k, ig, il, xs, b, tmp,
-                                                                         bc_op, tabs.BC);
+    // ---- pressure step: tmp_p = g - (B u - C p) at every pressure site,
+    // then p -= omega M_L^{-1} tmp_p
+    if (wbase < sd[nph + 1].total) {
+      const PhaseDesc d = sd[nph + 1];
+      const int P = 1 << d.lp;
+      const ResRow& rw = tb.BC;
+      for (int q = tid; q < d.total; q += nthr) {
+        const int inst = q >> d.lp, p = q & (P - 1);
+        const bool valid = inst < d.ninst;
+        int i = 0, j = 0, kl = 0;
+        if (valid) {
+          kl = qdiv(inst, d.d0, d.r0);
+          const int rem = inst - kl * d.d0;
+          j = qdiv(rem, d.d1, d.r1);
+          i = rem - j * d.d1;
+        }
+        const int k = kb + kl;
+        const bool bnd = i == 0 || j == 0 || k == 0 || i == g.nx || j == g.ny || k == g.nz;
+        const bool comp = valid && (!bnd || rw.all);
+        const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
+        const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(k + 1) * sy;
+        const T bv = (comp && p == 0) ? __ldg(b + int64_t(rw.out) * g.arr + ig) : T(0);
+        T a0 = T(0), a1 = T(0), a2 = T(0);
+        if (comp) {
+          const T* xl = xs + il;
+          const int e0 = rw.t0 + rw.n0, e1 = e0 + rw.n1, e2 = e1 + rw.n2;
+          for (int t = rw.t0 + p; t < e0; t += P) a0 += sw[t] * xl[soff[t]];
+          for (int t = e0 + p; t < e1; t += P) a1 += sw[t] * xl[soff[t]];
+          if (!bnd) {
+            for (int t = e1 + p; t < e2; t += P) a2 += sw[t] * xl[soff[t]];
+          } else {
+            for (int t = rw.bs + p; t < rw.bs + rw.bn; t += P) {
+              const DTermB tm = bc_op.bterms[t];
+              const int qx = i + tm.cx, qy = j + tm.cy, qz = k + tm.cz;
+              if (qx < 0 || qy < 0 || qz < 0 || qx >= g.nx || qy >= g.ny || qz >= g.nz) continue;
+              a2 += bw<T>(bc_op, t) * xs[tm.arr * arr_l + il + tm.off];
+            }
+          }
+        }
+        if (P > 1) {
+          a0 = group_sum(a0, P);
+          a1 = group_sum(a1, P);
+          a2 = group_sum(a2, P);
+        }
+        if (valid && p == 0) {
+          T v = a0;
+          if (varnu) v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
+          else v += a1 + a2;
+          ts[rw.out * arr_t + il - sy] = comp ? bv - v : T(0);
+        }
+      }
     }
-    __syncthreads();
-    for (int q = tid; q < Vl; q += nthr) {
-      const int kl = q / plane, rem = q - kl * plane, j = rem / nxp, i = rem - j * nxp;
-      const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
-      const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(kb + kl + 1) * sy;
-      xs[pol + il] -= T(a.inv_omega_inv * inv_ml[ig]) * tmp[pog + ig];
+    bar();                                         // the neighbours have read the old halo pressures
+    for (int r = tid; r < nk * sy; r += nthr) {    // owned planes, zero ring included (stays 0)
+      const int kl = qdiv(r, sy, rsy);
+      store(pol + sy + r, kl, xs[pol + sy + r] - mls[r] * ts[pot + r]);
     }
     bar();
-    pull(3 * G, 1, 1, -1);
   }
   // owned planes back to global memory
   {
@@ -274,15 +355,15 @@ __global__ void __launch_bounds__(kResidentThreads)
       xg[int64_t(ar) * g.arr + int64_t(kb + 1) * sy + r] = xs[ar * arr_l + sy + r];
     }
   }
-  if (C > 1) cluster.sync();                     // no CTA leaves while a neighbour may read its shared memory
 }
 
 template <class T> constexpr int prec_of() { return sizeof(T) == 8 ? HHG_FP64 : HHG_FP32; }
 
-void fill_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int C, size_t smem, cudaStream_t s) {
+void fill_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int C, int threads, size_t smem,
+                 cudaStream_t s) {
   cfg = {};
   cfg.gridDim = dim3(C, 1, 1);
-  cfg.blockDim = dim3(kResidentThreads, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -293,12 +374,12 @@ void fill_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int C, size
   cfg.numAttrs = 1;
 }
 
-template <int DISC, int VARNU, class T>
+template <class T>
 bool feasible_impl(const Geo& g, int C) {
   if (C < 1 || C > kResidentMaxCtas || C > g.nz + 1) return false;
   const size_t smem = resident_smem(g, C, prec_of<T>());
   if (smem > kResidentSmemMax) return false;
-  auto fn = k_uzawa_resident<DISC, VARNU, T>;
+  auto fn = k_uzawa_resident<T>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kResidentSmemMax)) != cudaSuccess ||
       cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
@@ -306,52 +387,13 @@ bool feasible_impl(const Geo& g, int C) {
   }
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  fill_config(cfg, attr, C, smem, nullptr);
+  fill_config(cfg, attr, C, kResidentThreads, smem, nullptr);
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   return n > 0;
-}
-
-template <int DISC, int VARNU, class T>
-int launch_resident(const Geo& g, int C, T* x, const T* b, T* tmp, const double* inv_ml, const SmallArgs& a,
-                    const OpDev& bc_op, const void* tabs, cudaStream_t s) {
-  using Tabs = SmallTabs<DISC, VARNU, T>;
-  cudaLaunchConfig_t cfg;
-  cudaLaunchAttribute attr[1];
-  fill_config(cfg, attr, C, resident_smem(g, C, prec_of<T>()), s);
-  ++g_launches;
-  const Tabs& tb = *static_cast<const Tabs*>(tabs);
-  const int arr_l = int(resident_arr(g, C));
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_uzawa_resident<DISC, VARNU, T>, g, arr_l, x, b, tmp, inv_ml, a, bc_op, tb);
-  return e == cudaSuccess ? 0 : -1;
-}
-
-template <class T, int N>
-bool localise_tab(FastTab<T, N>& tab, const Geo& g, int64_t arr_l) {
-  const int64_t na = 3 * int64_t(g.G) + 1;
-  for (int t = 0; t < N; ++t) {
-    const int64_t off = tab.off[t];
-    const int64_t ar = std::llround(double(off) / double(g.arr));
-    const int64_t rel = off - ar * g.arr;
-    const int64_t dk = std::llround(double(rel) / double(g.sy));
-    const int64_t dj = std::llround(double(rel - dk * g.sy) / double(g.sx));
-    const int64_t di = rel - dk * g.sy - dj * g.sx;
-    if (ar < 0 || ar >= na || dk < -1 || dk > 1 || dj < -1 || dj > 1 || di < -1 || di > 1) return false;
-    tab.off[t] = int(ar * arr_l + rel);
-  }
-  return true;
-}
-
-template <int D, int V, class T>
-bool localise_impl(const std::vector<char>& in, const Geo& g, int64_t arr_l, std::vector<char>& out) {
-  using ST = SmallTabs<D, V, T>;
-  if (in.size() != sizeof(ST)) return false;
-  out = in;
-  ST* st = reinterpret_cast<ST*>(out.data());
-  return localise_tab(st->A, g, arr_l) && localise_tab(st->BT, g, arr_l) && localise_tab(st->BC, g, arr_l);
 }
 
 }  // namespace
@@ -362,68 +404,38 @@ int64_t resident_arr(const Geo& g, int ctas) {
   return (planes * g.sy + 3) / 4 * 4;
 }
 
+int64_t resident_arr_t(const Geo& g, int ctas) {
+  const int64_t nzp = g.nz + 1;
+  return (((nzp + ctas - 1) / ctas) * g.sy + 3) / 4 * 4;
+}
+
 size_t resident_smem(const Geo& g, int ctas, int prec) {
   const size_t es = prec == HHG_FP64 ? 8 : 4;
-  return size_t(3 * g.G + 1) * size_t(resident_arr(g, ctas)) * es;
+  const size_t na = size_t(3 * g.G + 1);
+  return (na * size_t(resident_arr(g, ctas)) + (na + 1) * size_t(resident_arr_t(g, ctas))) * es +
+         size_t(kResMaxTerms) * (es + 4);
 }
 
-bool resident_feasible(int disc, int varnu, int prec, const Geo& g, int ctas) {
-  if (prec == HHG_FP64) {
-    if (disc == 1) return varnu ? feasible_impl<1, 1, double>(g, ctas) : feasible_impl<1, 0, double>(g, ctas);
-    return varnu ? feasible_impl<2, 1, double>(g, ctas) : feasible_impl<2, 0, double>(g, ctas);
-  }
-  if (disc == 1) return varnu ? feasible_impl<1, 1, float>(g, ctas) : feasible_impl<1, 0, float>(g, ctas);
-  return varnu ? feasible_impl<2, 1, float>(g, ctas) : feasible_impl<2, 0, float>(g, ctas);
-}
-
-bool small_tabs_localise(int disc, int varnu, int prec, const std::vector<char>& in, const Geo& g, int64_t arr_l,
-                         std::vector<char>& out) {
-  if (prec == HHG_FP64) {
-    if (disc == 1)
-      return varnu ? localise_impl<1, 1, double>(in, g, arr_l, out) : localise_impl<1, 0, double>(in, g, arr_l, out);
-    return varnu ? localise_impl<2, 1, double>(in, g, arr_l, out) : localise_impl<2, 0, double>(in, g, arr_l, out);
-  }
-  if (disc == 1)
-    return varnu ? localise_impl<1, 1, float>(in, g, arr_l, out) : localise_impl<1, 0, float>(in, g, arr_l, out);
-  return varnu ? localise_impl<2, 1, float>(in, g, arr_l, out) : localise_impl<2, 0, float>(in, g, arr_l, out);
+bool resident_feasible(int prec, const Geo& g, int ctas) {
+  return prec == HHG_FP64 ? feasible_impl<double>(g, ctas) : feasible_impl<float>(g, ctas);
 }
 
 template <class T>
-int uzawa_resident(int disc, int varnu, const Geo& g, int ctas, T* x, const T* b, T* tmp, const double* inv_ml,
-                   const SmallArgs& a, const OpDev& bc_op, const void* tabs, cudaStream_t s) {
-  if (disc == 1 && !varnu) return launch_resident<1, 0, T>(g, ctas, x, b, tmp, inv_ml, a, bc_op, tabs, s);
-  if (disc == 1) return launch_resident<1, 1, T>(g, ctas, x, b, tmp, inv_ml, a, bc_op, tabs, s);
-  if (!varnu) return launch_resident<2, 0, T>(g, ctas, x, b, tmp, inv_ml, a, bc_op, tabs, s);
-  return launch_resident<2, 1, T>(g, ctas, x, b, tmp, inv_ml, a, bc_op, tabs, s);
+int uzawa_resident(const Geo& g, int ctas, int threads, T* x, const T* b, const double* inv_ml, const SmallArgs& a,
+                   const OpDev& bc_op, const ResTabs<T>& tabs, cudaStream_t s) {
+  if (threads < 128 || threads > kResidentThreads || threads % 32) return -1;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fill_config(cfg, attr, ctas, threads, resident_smem(g, ctas, prec_of<T>()), s);
+  ++g_launches;
+  const int arr_l = int(resident_arr(g, ctas)), arr_t = int(resident_arr_t(g, ctas));
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_uzawa_resident<T>, g, arr_l, arr_t, x, b, inv_ml, a, bc_op, tabs);
+  return e == cudaSuccess ? 0 : -1;
 }
 
-size_t small_tabs_bytes(int disc, int varnu, int prec) {
-  if (prec == HHG_FP64) {
-    if (disc == 1) return varnu ? sizeof(SmallTabs<1, 1, double>) : sizeof(SmallTabs<1, 0, double>);
-    return varnu ? sizeof(SmallTabs<2, 1, double>) : sizeof(SmallTabs<2, 0, double>);
-  }
-  if (disc == 1) return varnu ? sizeof(SmallTabs<1, 1, float>) : sizeof(SmallTabs<1, 0, float>);
-  return varnu ? sizeof(SmallTabs<2, 1, float>) : sizeof(SmallTabs<2, 0, float>);
-}
-
-size_t small_tabs_offset(int disc, int varnu, int prec, int which) {
-#define HHG_OFFS(D, V, T)                                                  \
-  if (disc == D && varnu == V) {                                           \
-    using ST = SmallTabs<D, V, T>;                                         \
-    return which == 0 ? offsetof(ST, A) : which == 1 ? offsetof(ST, BT) : offsetof(ST, BC); \
-  }
-  if (prec == HHG_FP64) {
-    HHG_OFFS(1, 0, double) HHG_OFFS(1, 1, double) HHG_OFFS(2, 0, double) HHG_OFFS(2, 1, double)
-  } else {
-    HHG_OFFS(1, 0, float) HHG_OFFS(1, 1, float) HHG_OFFS(2, 0, float) HHG_OFFS(2, 1, float)
-  }
-#undef HHG_OFFS
-  return 0;
-}
-
-template int uzawa_resident<double>(int, int, const Geo&, int, double*, const double*, double*, const double*,
-                                    const SmallArgs&, const OpDev&, const void*, cudaStream_t);
-template int uzawa_resident<float>(int, int, const Geo&, int, float*, const float*, float*, const double*,
-                                   const SmallArgs&, const OpDev&, const void*, cudaStream_t);
+template int uzawa_resident<double>(const Geo&, int, int, double*, const double*, const double*, const SmallArgs&,
+                                    const OpDev&, const ResTabs<double>&, cudaStream_t);
+template int uzawa_resident<float>(const Geo&, int, int, float*, const float*, const double*, const SmallArgs&,
+                                   const OpDev&, const ResTabs<float>&, cudaStream_t);
 
 }  // namespace hhg

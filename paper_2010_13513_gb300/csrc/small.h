@@ -3,11 +3,7 @@
 
 #include <cuda_runtime.h>
 
-#include <vector>
-
-#include "fast.h"
 #include "internal.h"
-#include "structure.inc"
 
 namespace hhg {
 
@@ -20,43 +16,55 @@ struct SmallArgs {
   double inv_diag[8];      // 1 / diag(A) per group
 };
 
-// the parameter tables of the three operators used by the smoother
-template <int DISC, int VARNU, class T>
-struct SmallTabs {
-  FastTab<T, gen::S<DISC, VARNU, OP_A>::N> A;
-  FastTab<T, gen::S<DISC, VARNU, OP_BT>::N> BT;
-  FastTab<T, gen::S<DISC, VARNU, OP_BC>::N> BC;
+// one stencil row of the smoother's operators: output array, output group,
+// whether boundary sites are computed (else set to 0), its interior terms
+// [t0, t0 + n0 + n1 + n2) in three segments (unscaled, x e^{+}, x e^{-}), and
+// its per-cube boundary terms [bs, bs + bn) of segment 2 in the op's bterms
+struct ResRow {
+  int out, og, all, t0, n0, n1, n2, bs, bn;
 };
 
-size_t small_tabs_bytes(int disc, int varnu, int prec);
-size_t small_tabs_offset(int disc, int varnu, int prec, int which);   // 0 = A, 1 = BT, 2 = BC
+constexpr int kResMaxTerms = 640;
+constexpr int kResMaxRows = 24;
 
-constexpr int kResidentThreads = 1024;            // threads per CTA
+// parameter block of one launch: the component-0 rows of A per velocity
+// group (all terms in segment 1, the diagonal first), the 3G rows of B^T,
+// the pressure row of (B, -C), and their terms with offsets in the slab's
+// local array stride (array * arr_l + di + dj sx + dk sy)
+template <class T>
+struct ResTabs {
+  int G, nbt, nw, varnu;
+  ResRow A[8];
+  ResRow BT[kResMaxRows];
+  ResRow BC;
+  T w[kResMaxTerms];
+  int off[kResMaxTerms];
+};
+
+constexpr int kResidentThreads = 1024;            // most threads per CTA (128..1024, a multiple of 32)
 constexpr int kResidentMaxCtas = 16;              // largest (non-portable) cluster
-constexpr size_t kResidentSmemMax = 227 * 1024;   // dynamic shared memory per CTA
+constexpr size_t kResidentSmemMax = 226 * 1024;   // dynamic shared memory per CTA (static use below 1 KB)
 
 // Slab decomposition: CTA c of a cluster of C owns the k planes
 // [c (nz+1) / C, (c+1) (nz+1) / C) of every array of the block vector and
-// keeps them, with one halo plane below and above, in shared memory.  Local
-// array stride (elements) and shared memory per CTA (bytes):
+// keeps them, with one halo plane below and above, in shared memory, next to
+// the residuals and omega M_L^{-1} of its owned planes.  Local array strides
+// (elements) of the slab and of the owned-plane arrays, and shared memory per
+// CTA (bytes, including the tables):
 int64_t resident_arr(const Geo& g, int ctas);
+int64_t resident_arr_t(const Geo& g, int ctas);
 size_t resident_smem(const Geo& g, int ctas, int prec);
 // true if `ctas` CTAs can hold the level (every CTA owns a plane, the slab
 // fits the shared memory, the cluster can be scheduled).  Sets the kernel's
 // shared-memory and cluster-size attributes; call before any launch with
 // this CTA count and outside stream capture.
-bool resident_feasible(int disc, int varnu, int prec, const Geo& g, int ctas);
-// rewrites the linear offsets (array * arr_g + rel) of a SmallTabs image to
-// the local array stride arr_l; false if a term reaches beyond the adjacent
-// sites (then the slab layout would not hold it)
-bool small_tabs_localise(int disc, int varnu, int prec, const std::vector<char>& in, const Geo& g, int64_t arr_l,
-                         std::vector<char>& out);
+bool resident_feasible(int prec, const Geo& g, int ctas);
 
 // `iterations` inexact Uzawa iterations of a level in one launch of a
-// cluster of `ctas` CTAs; `tabs` is a SmallTabs image localised to
+// cluster of `ctas` CTAs of `threads` threads; `tabs` built for
 // resident_arr(g, ctas).  Returns 0 or -1 (launch failure).
 template <class T>
-int uzawa_resident(int disc, int varnu, const Geo& g, int ctas, T* x, const T* b, T* tmp, const double* inv_ml,
-                   const SmallArgs& a, const OpDev& bc_op, const void* tabs, cudaStream_t s);
+int uzawa_resident(const Geo& g, int ctas, int threads, T* x, const T* b, const double* inv_ml, const SmallArgs& a,
+                   const OpDev& bc_op, const ResTabs<T>& tabs, cudaStream_t s);
 
 }  // namespace hhg

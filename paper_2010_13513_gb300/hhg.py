@@ -101,8 +101,8 @@ def load():
         "hhg_estimate_omega": [P, I, I, DP, DP],
         "hhg_set_graph_mode": [P, I],
         "hhg_set_small_level_mode": [P, I],
-        "hhg_set_level_smoother": [P, I, I, I],
-        "hhg_get_level_smoother": [P, I, I, C.POINTER(C.c_int)],
+        "hhg_set_level_smoother": [P, I, I, I, I],
+        "hhg_get_level_smoother": [P, I, I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "hhg_error_norms": [P, I, VP, DP, DP, DP, DP],
         "hhg_block_norms_noalloc": [VP, I, C.c_int64, C.c_int64, VP, VP],
         "hhg_batch_create": [C.POINTER(P), I, C.POINTER(P)],
@@ -340,12 +340,12 @@ class Problem:
         return a.value, r.value
 
     def autotune(self, reps=5):
-        """Per-level launch choices; returns
-        {level: (row_threads, row_kplanes, gs_threads, resident_ctas)}."""
+        """Per-level launch choices; returns {level: (row_threads,
+        row_kplanes, gs_threads, resident_ctas, resident_threads)}."""
         n = self.L - self.lc + 1
-        out = (C.c_int * (4 * n))()
+        out = (C.c_int * (5 * n))()
         _check(load().hhg_autotune(self.h, reps, out), "hhg_autotune")
-        return {self.lc + i: tuple(out[4 * i:4 * i + 4]) for i in range(n)}
+        return {self.lc + i: tuple(out[5 * i:5 * i + 5]) for i in range(n)}
 
     def set_small_level_mode(self, on):
         _check(load().hhg_set_small_level_mode(self.h, int(on)), "hhg_set_small_level_mode")
@@ -353,17 +353,19 @@ class Problem:
     def _vprec(self):
         return FP32 if self.solve == "mixed" else FP64
 
-    def set_level_smoother(self, level, ctas, prec=None):
-        """CTAs (0..16) of the shared-memory-resident smoother of a level; 0 =
-        one launch per phase.  prec defaults to the V-cycle precision."""
+    def set_level_smoother(self, level, ctas, threads=0, prec=None):
+        """CTAs (0..16) and threads per CTA (0 = 1024) of the
+        shared-memory-resident smoother of a level; ctas = 0: one launch per
+        phase.  prec defaults to the V-cycle precision."""
         p = self._vprec() if prec is None else prec
-        _check(load().hhg_set_level_smoother(self.h, level, p, ctas), "hhg_set_level_smoother")
+        _check(load().hhg_set_level_smoother(self.h, level, p, ctas, threads), "hhg_set_level_smoother")
 
     def level_smoother(self, level, prec=None):
+        """(ctas, threads) of the level's smoother."""
         p = self._vprec() if prec is None else prec
-        out = C.c_int()
-        _check(load().hhg_get_level_smoother(self.h, level, p, C.byref(out)), "hhg_get_level_smoother")
-        return out.value
+        c, t = C.c_int(), C.c_int()
+        _check(load().hhg_get_level_smoother(self.h, level, p, C.byref(c), C.byref(t)), "hhg_get_level_smoother")
+        return c.value, t.value
 
     def estimate_omega(self, level, v0, iters=100):
         v = np.ascontiguousarray(v0, dtype=np.float64)

@@ -94,7 +94,7 @@ def test_uzawa_parity(disc, ahat, xi, nu_a):
 def test_resident_smoother_every_cta_count(disc, L, nu_a, ahat, xi):
     """The shared-memory-resident smoother on 1, 2, 4, 8 (and 16) CTAs, each
     owning a slab of k planes, gives the oracle's Uzawa iterates (FP64), and
-    in FP32 the iterates of the per-phase launches."""
+    in FP32 the iterates of the per-phase launches up to rounding."""
     from oracle.stokes import Params
     from paper_2010_13513_gb300 import hhg
     box = (1, 1, 2)
@@ -113,7 +113,7 @@ def test_resident_smoother_every_cta_count(disc, L, nu_a, ahat, xi):
             pb.set_level_smoother(L, ctas, prec=hhg.FP64)
         except hhg.HHGError:
             continue
-        assert pb.level_smoother(L, prec=hhg.FP64) == ctas
+        assert pb.level_smoother(L, prec=hhg.FP64) == (ctas, 1024)
         xd = pb.to_device(L, x)
         pb.smooth(L, lprm, 2, xd, pb.to_device(L, b))
         assert rel(pb.to_host(L, xd), ref) < 1e-12, ctas
@@ -125,8 +125,13 @@ def test_resident_smoother_every_cta_count(disc, L, nu_a, ahat, xi):
     assert {0, 1, 2, 4, 8} <= set(tried)
     if disc == "P1P1":
         assert 16 in tried                  # 17 k planes: the non-portable 16-CTA cluster
-    for ctas, v in out32.items():
-        assert rel(v, out32[0]) < 1e-6, ctas
+    for threads in (128, 256, 512):         # fewer threads per CTA: same iterates up to rounding
+        pb.set_level_smoother(L, 2, threads, prec=hhg.FP64)
+        xd = pb.to_device(L, x)
+        pb.smooth(L, lprm, 2, xd, pb.to_device(L, b))
+        assert rel(pb.to_host(L, xd), ref) < 1e-12, threads
+    for ctas, v in out32.items():               # terms of a row summed in another order
+        assert rel(v, out32[0]) < 1e-5, ctas
         assert rel(v, ref) < 1e-4
 
 
@@ -139,8 +144,10 @@ def test_resident_smoother_rejects_what_does_not_fit():
         pb.set_level_smoother(3, -1)
     with pytest.raises(hhg.HHGError):
         pb.set_level_smoother(3, 17)
+    with pytest.raises(hhg.HHGError):
+        pb.set_level_smoother(3, 1, 100)     # not a multiple of 32
     pb.set_level_smoother(3, 0)
-    assert pb.level_smoother(3) == 0
+    assert pb.level_smoother(3)[0] == 0
 
 
 @pytest.mark.parametrize("disc,box", [("P1P1", (2, 1, 1)), ("P2P1", (1, 1, 2)), ("P2P1", (1, 1, 1))])
@@ -308,17 +315,20 @@ def test_fmg_graph_replay_matches_direct_launches():
                                                   ("P1P1", 3, 1, "mixed", "s")])
 def test_cluster_smoother_matches_per_phase_launches(disc, L, lc, solve, ahat):
     """Small levels run all smoother phases in one thread-block-cluster launch;
-    the iterates equal those of one launch per phase."""
+    the FMG result equals that of one launch per phase up to the rounding of
+    the V-cycle precision (the resident kernel adds the terms of a row in
+    another order)."""
     from paper_2010_13513_gb300 import hhg
     pb = lib_problem((1, 1, 1), L, disc, lc=lc, solve=solve, workload=curl_workload())
     prm = hhg.Params.make(1, 3, 2, 1, ahat, 2, OMEGA_INV[disc])
+    assert any(pb.level_smoother(l)[0] > 0 for l in range(lc, L + 1))
     x1 = pb.new_vector(L)
     pb.fmg_solve(prm, x1, stats=False)
     pb.set_small_level_mode(False)
     x2 = pb.new_vector(L)
     pb.fmg_solve(prm, x2, stats=False)
     torch.cuda.synchronize()
-    assert rel(x1.cpu().numpy(), x2.cpu().numpy()) < 1e-13
+    assert rel(x1.cpu().numpy(), x2.cpu().numpy()) < (1e-13 if solve == "fp64" else 1e-5)
 
 
 def test_batch_graph_matches_individual_solves():
@@ -359,10 +369,12 @@ def test_autotune_keeps_results():
     pb.fmg_solve(prm, x1, stats=False)
     shapes = pb.autotune(reps=2)
     assert set(shapes) == {1, 2, 3, 4}
-    for t, kp, gs, rc in shapes.values():
+    for t, kp, gs, rc, rt in shapes.values():
         assert t in (64, 128, 256) and kp in (1, 2, 4, 8, 16) and gs in (64, 128, 256)
-        assert rc in (0, 1, 2, 4, 8, 16)
+        assert rc in (0, 1, 2, 4, 8, 16) and rt in (256, 512, 1024)
     x2 = pb.new_vector(4)
     pb.fmg_solve(prm, x2, stats=False)
     torch.cuda.synchronize()
-    assert torch.equal(x1, x2)
+    # launch shapes do not change the arithmetic; the resident smoother's CTA
+    # count changes the order of the FP32 partial sums of a row
+    assert rel(x1.cpu().numpy(), x2.cpu().numpy()) < 1e-5
