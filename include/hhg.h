@@ -298,7 +298,7 @@ int hhg_set_small_level_mode(hhg_problem* pb, int on);
  * the Uzawa smoother of `level` in precision `prec` in one launch with the
  * level's block vector held in their shared memory (a slab of k planes per
  * CTA), or ctas = 0 for one launch per phase.  HHG_EINVAL if the level does
- * not fit (at most 227 KB of slab, residuals and tables per CTA, at least one
+ * not fit (at most 225 KB of slab, residuals and tables per CTA, at least one
  * plane per CTA, the cluster must be schedulable).  Default at bind: the
  * fewest CTAs (<= 8) with at most 8192 lattice sites each, 1024 threads,
  * else 0; hhg_autotune times the choices.  Drops cached graphs.  The iterates

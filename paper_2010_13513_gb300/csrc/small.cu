@@ -36,6 +36,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 #include "small.h"
 
@@ -53,38 +55,52 @@ __device__ __forceinline__ int gox(int og) { return (0xB2 >> og) & 1; }
 __device__ __forceinline__ int goy(int og) { return (0xD4 >> og) & 1; }
 __device__ __forceinline__ int goz(int og) { return (0xE8 >> og) & 1; }
 
-template <class T>
-__device__ __forceinline__ T group_sum(T v, int P) {
+// sum over aligned groups of P lanes (every lane of the warp takes part)
+template <int P, class T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
   for (int m = P >> 1; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
   return v;
 }
 
-// floor(n / d) for 0 <= n < 2^22, d >= 1 and rd = 1/d rounded: the float
-// quotient is off by at most one, fixed by one comparison
-__device__ __forceinline__ int qdiv(int n, int d, float rd) {
-  int q = __float2int_rz(__int2float_rn(n) * rd);
-  if (q * d > n) --q;
-  else if ((q + 1) * d <= n) ++q;
-  return q;
+// calls f with the lanes-per-row exponent as a compile-time constant
+template <class F>
+__device__ __forceinline__ void with_lanes(int lp, F&& f) {
+  switch (lp) {
+    case 0: f(std::integral_constant<int, 0>{}); break;
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    default: f(std::integral_constant<int, 5>{}); break;
+  }
 }
+
+// floor(n / d) for 0 <= n, d < 2^16 from m = floor(2^32 / d) + 1: the
+// product n m / 2^32 exceeds n / d by less than n / 2^32 < 1 / d, which never
+// reaches the next integer (one wide multiply instead of a division)
+__device__ __forceinline__ int qdiv(int n, unsigned long long m) {
+  return int((unsigned long long)(unsigned)n * m >> 32);
+}
+__device__ __forceinline__ unsigned long long qmagic(int d) { return (1ull << 32) / unsigned(d) + 1; }
 
 // one phase of the smoother in one CTA: its rows (instances), lanes per row
 // (2^lp), lanes in whole warps, and the mixed-radix decomposition of an
-// instance index (up to three divisors with their reciprocals) into the row
+// instance index (up to three divisors with their multipliers) into the row
 // kind and the site relative to (i0, j0, kf)
 struct PhaseDesc {
   int ninst, lp, total;
   int d0, d1, d2;
-  float r0, r1, r2;
+  unsigned long long m0, m1, m2;
   int kf, i0, j0;
 };
 
 // lanes per row: enough to hide the latency of a row sum, few enough that
-// the shuffles and the index arithmetic do not outweigh the terms (about
-// four terms per lane, at most `cap` lanes in the phase)
+// the shuffles (about 30 cycles a level) do not outweigh the terms (about
+// eight terms per lane, at most `cap` lanes in the phase)
 __device__ __forceinline__ int lanes_log2(int n, int terms, int cap) {
   int lp = 0;
-  while (lp < 5 && (1 << lp) * 4 < terms && n * (2 << lp) <= cap) ++lp;
+  while (lp < 5 && (1 << lp) * 8 < terms && n * (2 << lp) <= cap) ++lp;
   return lp;
 }
 
@@ -96,15 +112,15 @@ __device__ __forceinline__ void set_desc(PhaseDesc& d, int ninst, int terms, int
   d.d0 = max(d0, 1);
   d.d1 = max(d1, 1);
   d.d2 = max(d2, 1);
-  d.r0 = 1.0f / float(d.d0);
-  d.r1 = 1.0f / float(d.d1);
-  d.r2 = 1.0f / float(d.d2);
+  d.m0 = qmagic(d.d0);
+  d.m1 = qmagic(d.d1);
+  d.m2 = qmagic(d.d2);
   d.kf = kf;
   d.i0 = i0;
   d.j0 = j0;
 }
 
-// lanes that may share the rows of a Gauss-Seidel or B^T phase
+// lanes that may share the rows of a Gauss-Seidel phase
 constexpr int kPhaseLanes = 256;
 
 template <class T>
@@ -114,6 +130,7 @@ __global__ void __launch_bounds__(kResidentThreads)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PhaseDesc sd[13];                     // GS phases 0..nph-1, then B^T, then (B, -C)
   __shared__ T sdiag[8];
+  __shared__ ResRow srowA[8];
   const int G = tb.G, NA = 3 * G + 1;
   // shared memory: the slab (NA arrays of stride arr_l, owned planes plus
   // halos), the residuals of the owned planes (NA arrays of stride arr_t,
@@ -150,7 +167,10 @@ __global__ void __launch_bounds__(kResidentThreads)
     sw[t] = tb.w[t];
     soff[t] = tb.off[t];
   }
-  if (tid < G) sdiag[tid] = T(a.inv_diag[tid]);
+  if (tid < G) {
+    sdiag[tid] = T(a.inv_diag[tid]);
+    srowA[tid] = tb.A[tid];
+  }
   if (tid < nph) {
     // Gauss-Seidel phase: interior sites of the group, i in [1-ox, nx-1],
     // j in [1-oy, ny-1], k in [1-oz, nz-1] within the slab; a vertex colour
@@ -164,7 +184,7 @@ __global__ void __launch_bounds__(kResidentThreads)
     const int kf = max(kb, 0), nkk = max(0, min(ke, g.nz) - kf), Vb = g.nx * g.ny * nkk;
     int terms = 0;
     for (int r = 0; r < tb.nbt; ++r) terms = max(terms, tb.BT[r].n0 + tb.BT[r].n1 + tb.BT[r].n2);
-    set_desc(sd[nph], tb.nbt * Vb, terms, kPhaseLanes, Vb, g.nx * g.ny, g.nx, kf, 0, 0);
+    set_desc(sd[nph], tb.nbt * Vb, terms, nthr, Vb, g.nx * g.ny, g.nx, kf, 0, 0);
   } else if (tid == nph + 1) {
     // the pressure row at every pressure site of the owned planes
     set_desc(sd[nph + 1], nxp * nyp * nk, tb.BC.n0 + tb.BC.n1 + tb.BC.n2, nthr, nxp * nyp, nxp, 1, kb, 0, 0);
@@ -185,50 +205,53 @@ __global__ void __launch_bounds__(kResidentThreads)
 
   const int pol = 3 * G * arr_l, pot = 3 * G * arr_t;
   const int csl = G * arr_l, cst = G * arr_t;
-  const float rsy = 1.0f / float(sy);
+  const unsigned long long msy = qmagic(sy);
   for (int it = 0; it < a.iterations; ++it) {
     // ---- velocity step: tmp_u = b_u - B^T p at the interior sites of every
     // group (Dirichlet rows are never read)
     if (wbase < sd[nph].total) {
       const PhaseDesc d = sd[nph];
-      const int P = 1 << d.lp;
-      for (int q = tid; q < d.total; q += nthr) {  // whole warps: the shuffles see all lanes
-        const int inst = q >> d.lp, p = q & (P - 1);
-        const bool valid = inst < d.ninst;
-        int r = 0, i = 0, j = 0, k = d.kf;
-        if (valid) {
-          r = qdiv(inst, d.d0, d.r0);
-          const int s = inst - r * d.d0, kk = qdiv(s, d.d1, d.r1), rem = s - kk * d.d1;
-          j = qdiv(rem, d.d2, d.r2);
-          i = rem - j * d.d2;
-          k += kk;
+      with_lanes(d.lp, [&](auto lpc) {
+        constexpr int LP = decltype(lpc)::value, P = 1 << LP;
+        for (int q = tid; q < d.total; q += nthr) {  // whole warps: the shuffles see all lanes
+          const int inst = q >> LP, p = q & (P - 1);
+          const bool valid = inst < d.ninst;
+          int r = 0, i = 0, j = 0, k = d.kf;
+          if (valid) {
+            r = qdiv(inst, d.m0);
+            const int s = inst - r * d.d0, kk = qdiv(s, d.m1), rem = s - kk * d.d1;
+            j = qdiv(rem, d.m2);
+            i = rem - j * d.d2;
+            k += kk;
+          }
+          const ResRow rw = tb.BT[r];
+          const bool ok = valid && (i > 0 || gox(rw.og)) && (j > 0 || goy(rw.og)) && (k > 0 || goz(rw.og));
+          const int kl = k - kb;
+          const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
+          const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(k + 1) * sy;
+          const T bv = (ok && p == 0) ? __ldg(b + int64_t(rw.out) * g.arr + ig) : T(0);
+          T a0 = T(0), a1 = T(0), a2 = T(0);
+          if (ok) {
+            const T* xl = xs + il;
+            const int e0 = rw.t0 + rw.n0, e1 = e0 + rw.n1, e2 = e1 + rw.n2;
+#pragma unroll 4
+            for (int t = rw.t0 + p; t < e0; t += P) a0 += sw[t] * xl[soff[t]];
+#pragma unroll 4
+            for (int t = e0 + p; t < e1; t += P) a1 += sw[t] * xl[soff[t]];
+#pragma unroll 4
+            for (int t = e1 + p; t < e2; t += P) a2 += sw[t] * xl[soff[t]];
+          }
+          a0 = group_sum<P>(a0);
+          a1 = group_sum<P>(a1);
+          a2 = group_sum<P>(a2);
+          if (ok && p == 0) {
+            T v = a0;
+            if (varnu) v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
+            else v += a1 + a2;
+            ts[rw.out * arr_t + il - sy] = bv - v;
+          }
         }
-        const ResRow rw = tb.BT[r];
-        const bool ok = valid && (i > 0 || gox(rw.og)) && (j > 0 || goy(rw.og)) && (k > 0 || goz(rw.og));
-        const int kl = k - kb;
-        const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
-        const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(k + 1) * sy;
-        const T bv = (ok && p == 0) ? __ldg(b + int64_t(rw.out) * g.arr + ig) : T(0);
-        T a0 = T(0), a1 = T(0), a2 = T(0);
-        if (ok) {
-          const T* xl = xs + il;
-          const int e0 = rw.t0 + rw.n0, e1 = e0 + rw.n1, e2 = e1 + rw.n2;
-          for (int t = rw.t0 + p; t < e0; t += P) a0 += sw[t] * xl[soff[t]];
-          for (int t = e0 + p; t < e1; t += P) a1 += sw[t] * xl[soff[t]];
-          for (int t = e1 + p; t < e2; t += P) a2 += sw[t] * xl[soff[t]];
-        }
-        if (P > 1) {
-          a0 = group_sum(a0, P);
-          a1 = group_sum(a1, P);
-          a2 = group_sum(a2, P);
-        }
-        if (ok && p == 0) {
-          T v = a0;
-          if (varnu) v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
-          else v += a1 + a2;
-          ts[rw.out * arr_t + il - sy] = bv - v;
-        }
-      }
+      });
     }
     __syncthreads();
     // ---- xi Gauss-Seidel sweeps on A u = tmp_u (forward, and backward for A_s)
@@ -242,47 +265,48 @@ __global__ void __launch_bounds__(kResidentThreads)
           if (wbase < sd[ph].total) {
             const PhaseDesc d = sd[ph];
             const int grp = ph < 4 ? 0 : ph - 3, colour = ph < 4 ? ph : -1;
-            const int P = 1 << d.lp;
-            const ResRow rw = tb.A[grp];
+            const int t0 = srowA[grp].t0, t1 = t0 + srowA[grp].n1;
             const T inv_diag = sdiag[grp];
-            for (int q = tid; q < d.total; q += nthr) {
-              const int inst = q >> d.lp, p = q & (P - 1);
-              int i = 0, j = 0, k = d.kf;
-              bool ok = false;
-              if (inst < d.ninst) {
-                const int kk = qdiv(inst, d.d0, d.r0), rem = inst - kk * d.d0, jj = qdiv(rem, d.d1, d.r1);
-                const int ii = rem - jj * d.d1;
-                j = d.j0 + jj;
-                k += kk;
-                i = colour >= 0 ? 1 + (((colour - j - k - 1) % 4) + 4) % 4 + 4 * ii : d.i0 + ii;
-                ok = i <= g.nx - 1;
-              }
-              const int kl = k - kb;
-              const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
-              T a0 = T(0), a1 = T(0), a2 = T(0);
-              if (ok) {
-                const T* us = xs + il;
-                for (int t = rw.t0 + 1 + p; t < rw.t0 + rw.n1; t += P) {   // the diagonal is the first term
-                  const T wt = sw[t];
-                  const int o = soff[t];
-                  a0 += wt * us[o];
-                  a1 += wt * us[o + csl];
-                  a2 += wt * us[o + 2 * csl];
+            with_lanes(d.lp, [&](auto lpc) {
+              constexpr int LP = decltype(lpc)::value, P = 1 << LP;
+              for (int q = tid; q < d.total; q += nthr) {
+                const int inst = q >> LP, p = q & (P - 1);
+                int i = 0, j = 0, k = d.kf;
+                bool ok = false;
+                if (inst < d.ninst) {
+                  const int kk = qdiv(inst, d.m0), rem = inst - kk * d.d0, jj = qdiv(rem, d.m1);
+                  const int ii = rem - jj * d.d1;
+                  j = d.j0 + jj;
+                  k += kk;
+                  i = colour >= 0 ? 1 + ((colour - j - k - 1) & 3) + 4 * ii : d.i0 + ii;
+                  ok = i <= g.nx - 1;
+                }
+                const int kl = k - kb;
+                const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
+                T a0 = T(0), a1 = T(0), a2 = T(0);
+                if (ok) {
+                  const T* us = xs + il;
+#pragma unroll 4
+                  for (int t = t0 + 1 + p; t < t1; t += P) {   // the diagonal is the first term
+                    const T wt = sw[t];
+                    const int o = soff[t];
+                    a0 += wt * us[o];
+                    a1 += wt * us[o + csl];
+                    a2 += wt * us[o + 2 * csl];
+                  }
+                }
+                a0 = group_sum<P>(a0);
+                a1 = group_sum<P>(a1);
+                a2 = group_sum<P>(a2);
+                if (ok && p == 0) {
+                  const T einv = varnu ? T(g.eisc[k]) : T(1);
+                  const int ol = grp * arr_l + il, ot = grp * arr_t + il - sy;
+                  store(ol, kl, (ts[ot] * einv - a0) * inv_diag);
+                  store(ol + csl, kl, (ts[ot + cst] * einv - a1) * inv_diag);
+                  store(ol + 2 * csl, kl, (ts[ot + 2 * cst] * einv - a2) * inv_diag);
                 }
               }
-              if (P > 1) {
-                a0 = group_sum(a0, P);
-                a1 = group_sum(a1, P);
-                a2 = group_sum(a2, P);
-              }
-              if (ok && p == 0) {
-                const T einv = varnu ? T(g.eisc[k]) : T(1);
-                const int ol = grp * arr_l + il, ot = grp * arr_t + il - sy;
-                store(ol, kl, (ts[ot] * einv - a0) * inv_diag);
-                store(ol + csl, kl, (ts[ot + cst] * einv - a1) * inv_diag);
-                store(ol + 2 * csl, kl, (ts[ot + 2 * cst] * einv - a2) * inv_diag);
-              }
-            }
+            });
           }
           bar();
         }
@@ -292,57 +316,60 @@ __global__ void __launch_bounds__(kResidentThreads)
     // then p -= omega M_L^{-1} tmp_p
     if (wbase < sd[nph + 1].total) {
       const PhaseDesc d = sd[nph + 1];
-      const int P = 1 << d.lp;
       const ResRow& rw = tb.BC;
-      for (int q = tid; q < d.total; q += nthr) {
-        const int inst = q >> d.lp, p = q & (P - 1);
-        const bool valid = inst < d.ninst;
-        int i = 0, j = 0, kl = 0;
-        if (valid) {
-          kl = qdiv(inst, d.d0, d.r0);
-          const int rem = inst - kl * d.d0;
-          j = qdiv(rem, d.d1, d.r1);
-          i = rem - j * d.d1;
-        }
-        const int k = kb + kl;
-        const bool bnd = i == 0 || j == 0 || k == 0 || i == g.nx || j == g.ny || k == g.nz;
-        const bool comp = valid && (!bnd || rw.all);
-        const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
-        const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(k + 1) * sy;
-        const T bv = (comp && p == 0) ? __ldg(b + int64_t(rw.out) * g.arr + ig) : T(0);
-        T a0 = T(0), a1 = T(0), a2 = T(0);
-        if (comp) {
-          const T* xl = xs + il;
-          const int e0 = rw.t0 + rw.n0, e1 = e0 + rw.n1, e2 = e1 + rw.n2;
-          for (int t = rw.t0 + p; t < e0; t += P) a0 += sw[t] * xl[soff[t]];
-          for (int t = e0 + p; t < e1; t += P) a1 += sw[t] * xl[soff[t]];
-          if (!bnd) {
-            for (int t = e1 + p; t < e2; t += P) a2 += sw[t] * xl[soff[t]];
-          } else {
-            for (int t = rw.bs + p; t < rw.bs + rw.bn; t += P) {
-              const DTermB tm = bc_op.bterms[t];
-              const int qx = i + tm.cx, qy = j + tm.cy, qz = k + tm.cz;
-              if (qx < 0 || qy < 0 || qz < 0 || qx >= g.nx || qy >= g.ny || qz >= g.nz) continue;
-              a2 += bw<T>(bc_op, t) * xs[tm.arr * arr_l + il + tm.off];
+      with_lanes(d.lp, [&](auto lpc) {
+        constexpr int LP = decltype(lpc)::value, P = 1 << LP;
+        for (int q = tid; q < d.total; q += nthr) {
+          const int inst = q >> LP, p = q & (P - 1);
+          const bool valid = inst < d.ninst;
+          int i = 0, j = 0, kl = 0;
+          if (valid) {
+            kl = qdiv(inst, d.m0);
+            const int rem = inst - kl * d.d0;
+            j = qdiv(rem, d.m1);
+            i = rem - j * d.d1;
+          }
+          const int k = kb + kl;
+          const bool bnd = i == 0 || j == 0 || k == 0 || i == g.nx || j == g.ny || k == g.nz;
+          const bool comp = valid && (!bnd || rw.all);
+          const int il = (i + 1) + (j + 1) * sx + (kl + 1) * sy;
+          const int64_t ig = int64_t(i + 1) + int64_t(j + 1) * sx + int64_t(k + 1) * sy;
+          const T bv = (comp && p == 0) ? __ldg(b + int64_t(rw.out) * g.arr + ig) : T(0);
+          T a0 = T(0), a1 = T(0), a2 = T(0);
+          if (comp) {
+            const T* xl = xs + il;
+            const int e0 = rw.t0 + rw.n0, e1 = e0 + rw.n1, e2 = e1 + rw.n2;
+#pragma unroll 4
+            for (int t = rw.t0 + p; t < e0; t += P) a0 += sw[t] * xl[soff[t]];
+#pragma unroll 4
+            for (int t = e0 + p; t < e1; t += P) a1 += sw[t] * xl[soff[t]];
+            if (!bnd) {
+#pragma unroll 4
+              for (int t = e1 + p; t < e2; t += P) a2 += sw[t] * xl[soff[t]];
+            } else {
+              for (int t = rw.bs + p; t < rw.bs + rw.bn; t += P) {
+                const DTermB tm = bc_op.bterms[t];
+                const int qx = i + tm.cx, qy = j + tm.cy, qz = k + tm.cz;
+                if (qx < 0 || qy < 0 || qz < 0 || qx >= g.nx || qy >= g.ny || qz >= g.nz) continue;
+                a2 += bw<T>(bc_op, t) * xs[tm.arr * arr_l + il + tm.off];
+              }
             }
           }
+          a0 = group_sum<P>(a0);
+          a1 = group_sum<P>(a1);
+          a2 = group_sum<P>(a2);
+          if (valid && p == 0) {
+            T v = a0;
+            if (varnu) v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
+            else v += a1 + a2;
+            ts[rw.out * arr_t + il - sy] = comp ? bv - v : T(0);
+          }
         }
-        if (P > 1) {
-          a0 = group_sum(a0, P);
-          a1 = group_sum(a1, P);
-          a2 = group_sum(a2, P);
-        }
-        if (valid && p == 0) {
-          T v = a0;
-          if (varnu) v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
-          else v += a1 + a2;
-          ts[rw.out * arr_t + il - sy] = comp ? bv - v : T(0);
-        }
-      }
+      });
     }
     bar();                                         // the neighbours have read the old halo pressures
     for (int r = tid; r < nk * sy; r += nthr) {    // owned planes, zero ring included (stays 0)
-      const int kl = qdiv(r, sy, rsy);
+      const int kl = qdiv(r, msy);
       store(pol + sy + r, kl, xs[pol + sy + r] - mls[r] * ts[pot + r]);
     }
     bar();
@@ -377,6 +404,9 @@ void fill_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int C, int 
 template <class T>
 bool feasible_impl(const Geo& g, int C) {
   if (C < 1 || C > kResidentMaxCtas || C > g.nz + 1) return false;
+  // instance counts and divisors of a phase stay below 2^16 (qdiv)
+  const int64_t planes = (g.nz + 1 + C - 1) / C;
+  if (3 * int64_t(g.G) * (g.nx + 1) * (g.ny + 1) * planes >= 65536 || planes * g.sy >= 65536) return false;
   const size_t smem = resident_smem(g, C, prec_of<T>());
   if (smem > kResidentSmemMax) return false;
   auto fn = k_uzawa_resident<T>;

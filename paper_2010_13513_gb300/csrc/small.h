@@ -43,7 +43,7 @@ struct ResTabs {
 
 constexpr int kResidentThreads = 1024;            // most threads per CTA (128..1024, a multiple of 32)
 constexpr int kResidentMaxCtas = 16;              // largest (non-portable) cluster
-constexpr size_t kResidentSmemMax = 226 * 1024;   // dynamic shared memory per CTA (static use below 1 KB)
+constexpr size_t kResidentSmemMax = 225 * 1024;   // dynamic shared memory per CTA (static use below 2 KB)
 
 // Slab decomposition: CTA c of a cluster of C owns the k planes
 // [c (nz+1) / C, (c+1) (nz+1) / C) of every array of the block vector and
