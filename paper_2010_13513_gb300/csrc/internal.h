@@ -135,6 +135,7 @@ struct DXTerm {
 };
 struct XferDev {
   int order, nclass, ngroups;
+  int rmax;                   // most restriction terms of a group
   const int* pcls_start;      // nclass + 1
   const DXTerm* pterms;
   const double* pw64;

@@ -182,33 +182,53 @@ __global__ void __launch_bounds__(128) k_prolong(Geo gf, Geo gc, XferDev X, int 
   }
 }
 
-template <class T>
+// r_c = I^T r_f per coarse DoF: its restriction terms (up to 125 for the P2
+// vertex group) are shared by P lanes, lane p taking terms p, p+P, ..., and
+// the partial sums are added by shuffles.  Block: 128 threads = 128/P coarse
+// sites along i; grid: (i blocks, j, (k, group)).
+template <class T, int P>
 __global__ void __launch_bounds__(128) k_restrict(Geo gf, Geo gc, XferDev X, int base_f, int base_c, int ncomp, int G,
                                                   int interior_only, const T* __restrict__ rf, T* __restrict__ rc) {
   const int nzp = gc.nz + 1;
   const int gci = blockIdx.z / nzp;
   const int k = blockIdx.z - gci * nzp;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = blockIdx.x * (128 / P) + int(threadIdx.x) / P, p = int(threadIdx.x) % P;
+  const int j = blockIdx.y;
   const int ox = G == 1 ? 0 : c_goff[gci][0], oy = G == 1 ? 0 : c_goff[gci][1], oz = G == 1 ? 0 : c_goff[gci][2];
-  if (!dof_valid(gc, i, j, k, ox, oy, oz)) return;
-  const int64_t cidx = site_index(gc, i, j, k);
-  const int64_t cstride_c = int64_t(G) * gc.arr, cstride_f = int64_t(G) * gf.arr;
-  if (interior_only && dof_boundary(gc, i, j, k, ox, oy, oz)) {
-    for (int c = 0; c < ncomp; ++c) rc[int64_t(base_c + gci) * gc.arr + c * cstride_c + cidx] = T(0);
-    return;
+  const bool valid = dof_valid(gc, i, j, k, ox, oy, oz);
+  const bool zero = valid && interior_only && dof_boundary(gc, i, j, k, ox, oy, oz);
+  const int64_t cstride_f = int64_t(G) * gf.arr;
+  T a0 = T(0), a1 = T(0), a2 = T(0);
+  if (valid && !zero) {
+    const int t0 = X.rg_start[gci], t1 = X.rg_start[gci + 1];
+#pragma unroll 4
+    for (int t = t0 + p; t < t1; t += P) {
+      const DXTerm tm = X.rterms[t];
+      const int fi = 2 * i + tm.di, fj = 2 * j + tm.dj, fk = 2 * k + tm.dk;
+      if (fi < -1 || fj < -1 || fk < -1 || fi > gf.nx + 1 || fj > gf.ny + 1 || fk > gf.nz + 1) continue;
+      const T w = wsel<T>(X.rw64, X.rw32, t);
+      const T* f = rf + int64_t(base_f + tm.arr) * gf.arr + site_index(gf, fi, fj, fk);
+      a0 += w * f[0];
+      if (ncomp > 1) {
+        a1 += w * f[cstride_f];
+        a2 += w * f[2 * cstride_f];
+      }
+    }
   }
-  const int t0 = X.rg_start[gci], t1 = X.rg_start[gci + 1];
-  T a[3] = {T(0), T(0), T(0)};
-  for (int t = t0; t < t1; ++t) {
-    const DXTerm tm = X.rterms[t];
-    const int fi = 2 * i + tm.di, fj = 2 * j + tm.dj, fk = 2 * k + tm.dk;
-    if (fi < -1 || fj < -1 || fk < -1 || fi > gf.nx + 1 || fj > gf.ny + 1 || fk > gf.nz + 1) continue;
-    const T w = wsel<T>(X.rw64, X.rw32, t);
-    const int64_t f = int64_t(base_f + tm.arr) * gf.arr + site_index(gf, fi, fj, fk);
-    for (int c = 0; c < ncomp; ++c) a[c] += w * rf[f + c * cstride_f];
+#pragma unroll
+  for (int m = P >> 1; m > 0; m >>= 1) {          // all lanes of the warp take part
+    a0 += __shfl_xor_sync(0xffffffffu, a0, m);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, m);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, m);
   }
-  for (int c = 0; c < ncomp; ++c) rc[int64_t(base_c + gci) * gc.arr + c * cstride_c + cidx] = a[c];
+  if (!valid || p != 0) return;
+  const int64_t cidx = site_index(gc, i, j, k), cstride_c = int64_t(G) * gc.arr;
+  T* o = rc + int64_t(base_c + gci) * gc.arr + cidx;
+  o[0] = zero ? T(0) : a0;
+  if (ncomp > 1) {
+    o[cstride_c] = zero ? T(0) : a1;
+    o[2 * cstride_c] = zero ? T(0) : a2;
+  }
 }
 
 // ---------------------------------------------------------------- reductions
@@ -343,10 +363,18 @@ void launch_prolong(const Geo& gf, const Geo& gc, const XferDev& X, int base_f, 
 template <class T>
 void launch_restrict(const Geo& gf, const Geo& gc, const XferDev& X, int base_f, int base_c, int ncomp, int G,
                      bool interior_only, const T* rf, T* rc, cudaStream_t s) {
-  dim3 blk(32, 4, 1);
-  dim3 grd((gc.nx + 1 + 31) / 32, (gc.ny + 1 + 3) / 4, (gc.nz + 1) * G);
+  // lanes per coarse DoF: about eight terms each
+  const int P = X.rmax > 32 ? 8 : X.rmax > 16 ? 4 : X.rmax > 8 ? 2 : 1;
+  dim3 blk(128, 1, 1);
+  dim3 grd((gc.nx + 1 + 128 / P - 1) / (128 / P), gc.ny + 1, (gc.nz + 1) * G);
   ++g_launches;
-  k_restrict<T><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, interior_only ? 1 : 0, rf, rc);
+  const int io = interior_only ? 1 : 0;
+  switch (P) {
+    case 8: k_restrict<T, 8><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, io, rf, rc); break;
+    case 4: k_restrict<T, 4><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, io, rf, rc); break;
+    case 2: k_restrict<T, 2><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, io, rf, rc); break;
+    default: k_restrict<T, 1><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, io, rf, rc); break;
+  }
 }
 
 template <class T>

@@ -117,7 +117,7 @@ struct OpOffsets {
 
 struct XferOffsets {
   size_t pstart, pterms, pw64, pw32, rstart, rterms, rw64, rw32;
-  int order, nclass, ngroups;
+  int order, nclass, ngroups, rmax;
 };
 
 struct Level {
@@ -298,7 +298,7 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
     Level lv;
     lv.l = l;
     lv.g = make_geo(mesh->mx, mesh->my, mesh->mz, l, pb->G, mesh->H, desc->nu_a);
-    if (int64_t(lv.g.nz + 1) * 25 > 65535 || lv.g.ny + 1 > 65535 * 4)
+    if (int64_t(lv.g.nz + 1) * 25 > 65535 || lv.g.ny + 1 > 65535)
       return fail(HHG_EINVAL, "level too large for the launch geometry");
     lv.st = build_stencils(desc->disc, lv.g.h, desc->nu_a, desc->pspg_rhs != 0);
     for (int gg = 0; gg < pb->G; ++gg) lv.inv_diag.push_back(1.0 / lv.st.diagA[gg]);
@@ -354,6 +354,8 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
     }
     std::vector<float> pw32(pw.begin(), pw.end()), rw32(rw.begin(), rw.end());
     xo.order = X.order; xo.nclass = X.nclass; xo.ngroups = int(X.restr.size());
+    xo.rmax = 0;
+    for (auto& c : X.restr) xo.rmax = std::max(xo.rmax, int(c.size()));
     xo.pstart = B.put(ps); xo.pterms = B.put(pt); xo.pw64 = B.put(pw); xo.pw32 = B.put(pw32);
     xo.rstart = B.put(rs); xo.rterms = B.put(rt); xo.rw64 = B.put(rw); xo.rw32 = B.put(rw32);
   };
@@ -1103,6 +1105,7 @@ extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, 
     X.rterms = reinterpret_cast<const DXTerm*>(tb + xo.rterms);
     X.rw64 = reinterpret_cast<const double*>(tb + xo.rw64);
     X.rw32 = reinterpret_cast<const float*>(tb + xo.rw32);
+    X.rmax = xo.rmax;
     return X;
   };
   pb->xv = xdev(pb->xoff_v);
