@@ -168,6 +168,53 @@ def apply_roofline(pb, steps=20):
     return alg_bytes, t
 
 
+def kernel_source_hash():
+    """sha256 of the sources of the specialised stencil kernels (the apply
+    kernel of the roofline line)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fast.cu", "fast.h", "gen_structure.cpp", "stencils.cpp"):
+        with open(os.path.join(ROOT, "paper_2010_13513_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the level-6 FP32 apply from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "apply_p2_l6_dram.md")
+    try:
+        fields = dict(l.strip("- \n").split(": ", 1) for l in open(path) if l.startswith("- ") and ": " in l)
+        if fields.get("kernel_source_sha256") == kernel_source_hash():
+            return int(fields["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def profile_apply():
+    """Only the roofline apply: set-up, three warm-up launches, then three
+    launches (each after an L2 flush) between cudaProfilerStart/Stop."""
+    import torch
+    torch.cuda.set_stream(torch.cuda.Stream())
+    pb, _ = make_problem("mixed")
+    pb.autotune(reps=3)
+    L = WORKLOAD["L"]
+    x = pb.new_vector(L, prec=1)
+    x.uniform_(-1, 1)
+    y = pb.new_vector(L, prec=1)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        pb.apply(L, "FULL", x, y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(3):
+        flush.fill_(1.0)
+        pb.apply(L, "FULL", x, y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+
+
 def e2e_steps(pb, wl, prm, steps):
     """Through the public API with host data: nodal forcing/Dirichlet data from
     host memory (hhg_set_rhs on every level, assembled on the GPU), the FMG
@@ -481,7 +528,11 @@ def main():
     ap.add_argument("--workload", default="p2-l6", choices=["p2-l6", "batched", "p1-visc", "p2-l7"])
     ap.add_argument("--profile-region", action="store_true",
                     help="only set-up, warm-up and the timed FMG steps, bracketed by cudaProfilerStart/Stop")
+    ap.add_argument("--profile-apply", action="store_true",
+                    help="only the level-6 FP32 apply of the roofline line, bracketed by cudaProfilerStart/Stop")
     args = ap.parse_args()
+    if args.profile_apply:
+        return profile_apply()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
@@ -579,8 +630,8 @@ def main():
                    "fp64_gpu_ms_per_step": t64 * 1e3, "mixed_speedup_vs_fp64_gpu": t64 / t_step,
                    "mixed_vs_fp64_rel_diff": mixed_vs_fp64},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                     "kernel": "FP32 operator apply y = calA x, level 6 (k_apply)",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": measured_traffic(),
+                     "kernel": "FP32 operator apply y = calA x, level 6 (k_rows_fast, FULL)",
                      "alg_bytes": alg_bytes, "avg_launch_us": t_apply * 1e6, "peak_source": src},
         "e2e": {"value": e2e_v, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
