@@ -224,15 +224,16 @@ def e2e_steps(pb, wl, prm, steps):
     L = WORKLOAD["L"]
     host = {}
     h2d = 0
-    for l in range(WORKLOAD["lc"], L + 1):
+    for l in range(WORKLOAD["lc"], L + 1):       # the step's inputs, in pinned host memory
         info = pb.layout(l)
         X = hhg.velocity_coords(info)
-        f = np.ascontiguousarray(wl.forcing(X).T.ravel())
-        w = np.ascontiguousarray(wl.dirichlet(X).T.ravel())
+        f = torch.from_numpy(np.ascontiguousarray(wl.forcing(X).T.ravel())).pin_memory()
+        w = torch.from_numpy(np.ascontiguousarray(wl.dirichlet(X).T.ravel())).pin_memory()
         host[l] = (f, w)
-        h2d += f.nbytes + w.nbytes
+        h2d += 8 * (f.numel() + w.numel())
     x = pb.new_vector(L)
     d2h = pb.layout(L).n_dofs * 8
+    out = torch.empty(pb.layout(L).n_dofs, dtype=torch.float64).pin_memory()
     ts = []
     for _ in range(steps):
         torch.cuda.synchronize()
@@ -240,9 +241,9 @@ def e2e_steps(pb, wl, prm, steps):
         for l, (f, w) in host.items():
             pb.set_rhs(l, f, w)
         pb.fmg_solve(prm, x, stats=False)
-        out = pb.to_host(L, x)
+        pb.to_host(L, x, out=out)
         ts.append(time.perf_counter() - t0)
-    assert np.isfinite(out).all()
+    assert torch.isfinite(out).all()
     return ts, h2d, d2h
 
 

@@ -168,7 +168,10 @@ int hhg_layout(const hhg_problem* pb, int level, hhg_layout_info* info);
 
 /* Canonical host vector -> device layout (and back); halo and padding
  * entries are written as zeros.  Velocity Dirichlet entries are copied as
- * given.  Synchronous. */
+ * given.  The canonical data cross the bus in one copy (fast from pinned host
+ * memory) and are scattered/gathered on the device, staged in the level's
+ * scratch vector.  Synchronous (the host buffer may be reused on return).
+ * FP32 device vectors need a problem created with HHG_SOLVE_MIXED. */
 int hhg_vector_from_host(hhg_problem* pb, int level, int prec, const double* host, void* dev);
 int hhg_vector_to_host(hhg_problem* pb, int level, int prec, const void* dev, double* host);
 
@@ -176,7 +179,8 @@ int hhg_vector_to_host(hhg_problem* pb, int level, int prec, const void* dev, do
  *   f = M f_h - A w_h (interior velocity rows), g = -B w_h (+ PSPG load),
  * g projected to sum zero.  f_nodal: forcing at the canonical velocity nodes
  * (3 x n_velocity_nodes, component-major); w_nodal: Dirichlet data at the same
- * nodes (only boundary entries are read).  Kept inside the workspace. */
+ * nodes (only boundary entries are read).  Kept inside the workspace.  Both
+ * arrays are copied as they are and placed by a device kernel; synchronous. */
 int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal);
 /* Device pointer of a library-owned FP64 level vector: 0 = rhs, 1 = boundary
  * lifting w_h, 2 = FMG solution x. */

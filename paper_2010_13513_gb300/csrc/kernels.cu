@@ -231,6 +231,56 @@ __global__ void __launch_bounds__(128) k_restrict(Geo gf, Geo gc, XferDev X, int
   }
 }
 
+// ------------------------------------------ canonical order <-> padded layout
+// Canonical host order: 3 velocity components (component-major) over the
+// velocity nodes in lexicographic order (P1: the lattice sites; P2: the
+// doubled lattice, node (I,J,K) in group of parity (I&1, J&1, K&1) at site
+// (I>>1, J>>1, K>>1)), then the pressure nodes (the lattice sites).
+__constant__ int c_parity_group[8] = {0, 1, 2, 4, 3, 5, 6, 7};   // index ox | oy << 1 | oz << 2
+
+struct CanonMap {
+  int64_t off;      // element of the node in the layout vector
+  bool bnd;         // on the domain boundary
+};
+
+// blockIdx.y: component 0..2 (velocity) or 3 (pressure); x: node index
+__device__ __forceinline__ CanonMap canon_map(const Geo& g, int comp, int64_t ci) {
+  CanonMap m;
+  if (comp < 3 && g.G > 1) {
+    const int64_t nI = 2 * int64_t(g.nx) + 1, nJ = 2 * int64_t(g.ny) + 1;
+    const int64_t K = ci / (nI * nJ), rem = ci - K * nI * nJ, J = rem / nI, I = rem - J * nI;
+    const int gg = c_parity_group[int(I & 1) | int(J & 1) << 1 | int(K & 1) << 2];
+    m.off = int64_t(comp * g.G + gg) * g.arr + ((I >> 1) + 1) + ((J >> 1) + 1) * g.sx + ((K >> 1) + 1) * g.sy;
+    m.bnd = I == 0 || J == 0 || K == 0 || I == 2 * g.nx || J == 2 * g.ny || K == 2 * g.nz;
+  } else {
+    const int64_t nI = g.nx + 1, nJ = g.ny + 1;
+    const int64_t k = ci / (nI * nJ), rem = ci - k * nI * nJ, j = rem / nI, i = rem - j * nI;
+    const int arr = comp < 3 ? comp * g.G : 3 * g.G;
+    m.off = int64_t(arr) * g.arr + (i + 1) + (j + 1) * g.sx + (k + 1) * g.sy;
+    m.bnd = i == 0 || j == 0 || k == 0 || i == g.nx || j == g.ny || k == g.nz;
+  }
+  return m;
+}
+
+template <class T>
+__global__ void k_canon_scatter(Geo g, const double* __restrict__ src, T* __restrict__ dst, int64_t nvn, int64_t npn,
+                                int boundary_only) {
+  const int comp = blockIdx.y;
+  const int64_t n = comp < 3 ? nvn : npn;
+  for (int64_t ci = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; ci < n; ci += int64_t(gridDim.x) * blockDim.x) {
+    const CanonMap m = canon_map(g, comp, ci);
+    if (!boundary_only || m.bnd) dst[m.off] = T(src[comp * nvn + ci]);
+  }
+}
+
+template <class T>
+__global__ void k_canon_gather(Geo g, const T* __restrict__ src, double* __restrict__ dst, int64_t nvn, int64_t npn) {
+  const int comp = blockIdx.y;
+  const int64_t n = comp < 3 ? nvn : npn;
+  for (int64_t ci = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; ci < n; ci += int64_t(gridDim.x) * blockDim.x)
+    dst[comp * nvn + ci] = double(src[canon_map(g, comp, ci).off]);
+}
+
 // ---------------------------------------------------------------- reductions
 template <class T, int MODE>
 __global__ void __launch_bounds__(256) k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b,
@@ -393,6 +443,21 @@ void launch_reduce(int mode, const T* a, const T* b, const double* w, int64_t n,
 }
 
 template <class T>
+void launch_canon_scatter(const Geo& g, const double* src, T* dst, int64_t nvn, int64_t npn, bool with_pressure,
+                          bool boundary_only, cudaStream_t s) {
+  ++g_launches;
+  dim3 grd(unsigned(std::min<int64_t>((nvn + 255) / 256, 152 * 8)), with_pressure ? 4 : 3);
+  k_canon_scatter<T><<<grd, 256, 0, s>>>(g, src, dst, nvn, npn, boundary_only ? 1 : 0);
+}
+
+template <class T>
+void launch_canon_gather(const Geo& g, const T* src, double* dst, int64_t nvn, int64_t npn, cudaStream_t s) {
+  ++g_launches;
+  dim3 grd(unsigned(std::min<int64_t>((nvn + 255) / 256, 152 * 8)), 4);
+  k_canon_gather<T><<<grd, 256, 0, s>>>(g, src, dst, nvn, npn);
+}
+
+template <class T>
 void launch_coarse(const double* Z, int n, const int64_t* idx, const T* b, T* x, cudaStream_t s) {
   ++g_launches;
   k_coarse<T><<<n, 128, 0, s>>>(Z, n, idx, b, x);
@@ -420,6 +485,11 @@ void launch_inv(const double* a, double* b, int64_t n, cudaStream_t s) {
   ++g_launches;
   k_inv<<<lin_blocks(n), 256, 0, s>>>(a, b, n);
 }
+
+template void launch_canon_scatter<double>(const Geo&, const double*, double*, int64_t, int64_t, bool, bool, cudaStream_t);
+template void launch_canon_scatter<float>(const Geo&, const double*, float*, int64_t, int64_t, bool, bool, cudaStream_t);
+template void launch_canon_gather<double>(const Geo&, const double*, double*, int64_t, int64_t, cudaStream_t);
+template void launch_canon_gather<float>(const Geo&, const float*, double*, int64_t, int64_t, cudaStream_t);
 
 #define HHG_INST(T)                                                                                              \
   template void launch_apply<T>(const Geo&, const OpDev&, int, const T*, const T*, T*, double, cudaStream_t);     \

@@ -31,6 +31,14 @@ void launch_prolong(const Geo& gf, const Geo& gc, const XferDev& X, int base_f, 
                     bool interior_only, const T* xc, T* xf, cudaStream_t s);
 
 // rc[base_c..] = I^T rf (interior_only: Dirichlet rows set to 0)
+// canonical host order (3 velocity components over the velocity nodes, then
+// the pressure nodes) <-> padded layout; the scatter writes only the nodes
+// (only boundary velocity nodes if boundary_only), the target is pre-zeroed
+template <class T>
+void launch_canon_scatter(const Geo& g, const double* src, T* dst, int64_t nvn, int64_t npn, bool with_pressure,
+                          bool boundary_only, cudaStream_t s);
+template <class T>
+void launch_canon_gather(const Geo& g, const T* src, double* dst, int64_t nvn, int64_t npn, cudaStream_t s);
 template <class T>
 void launch_restrict(const Geo& gf, const Geo& gc, const XferDev& X, int base_f, int base_c, int ncomp, int G,
                      bool interior_only, const T* rf, T* rc, cudaStream_t s);

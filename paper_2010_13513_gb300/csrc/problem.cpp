@@ -484,39 +484,10 @@ void for_each_pressure_node(const Geo& g, F f) {
       for (int i = 0; i <= g.nx; ++i, ++c) f(c, int64_t(i + 1) + int64_t(j + 1) * g.sx + int64_t(k + 1) * g.sy);
 }
 
-void canonical_to_layout(const Level& lv, const double* host, std::vector<double>& out) {
-  const Geo& g = lv.g;
-  out.assign(size_t(lv.nvec()), 0.0);
-  int64_t nvn = g.G == 1 ? int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1)
-                         : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
-  for (int c = 0; c < 3; ++c)
-    for_each_velocity_node(g, [&](int64_t ci, int gg, int64_t site, bool) {
-      out[size_t((c * g.G + gg) * g.arr + site)] = host[c * nvn + ci];
-    });
-  for_each_pressure_node(g, [&](int64_t ci, int64_t site) { out[size_t(3 * g.G * g.arr + site)] = host[3 * nvn + ci]; });
-}
-
-void layout_to_canonical(const Level& lv, const std::vector<double>& in, double* host) {
-  const Geo& g = lv.g;
-  int64_t nvn = g.G == 1 ? int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1)
-                         : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
-  for (int c = 0; c < 3; ++c)
-    for_each_velocity_node(g, [&](int64_t ci, int gg, int64_t site, bool) {
-      host[c * nvn + ci] = in[size_t((c * g.G + gg) * g.arr + site)];
-    });
-  for_each_pressure_node(g, [&](int64_t ci, int64_t site) { host[3 * nvn + ci] = in[size_t(3 * g.G * g.arr + site)]; });
-}
-
-int upload(hhg_problem* pb, const std::vector<double>& h, int prec, void* dev) {
-  if (prec == HHG_FP64) {
-    HHG_CUDA(cudaMemcpyAsync(dev, h.data(), h.size() * 8, cudaMemcpyHostToDevice, pb->stream));
-  } else {
-    std::vector<float> f(h.begin(), h.end());
-    HHG_CUDA(cudaMemcpyAsync(dev, f.data(), f.size() * 4, cudaMemcpyHostToDevice, pb->stream));
-    HHG_CUDA(cudaStreamSynchronize(pb->stream));
-  }
-  HHG_CUDA(cudaStreamSynchronize(pb->stream));
-  return HHG_OK;
+int check_prec(const hhg_problem* pb, int prec) {
+  if (prec == HHG_FP64) return HHG_OK;
+  if (prec == HHG_FP32 && pb->desc.solve == HHG_SOLVE_MIXED) return HHG_OK;
+  return fail(HHG_EINVAL, "FP32 operations need a problem created with HHG_SOLVE_MIXED");
 }
 
 int check_level(const hhg_problem* pb, int level, bool allow_error_level = false) {
@@ -529,29 +500,47 @@ int check_level(const hhg_problem* pb, int level, bool allow_error_level = false
 
 }  // namespace
 
+namespace {
+int64_t velocity_nodes(const Geo& g) {
+  return g.G == 1 ? int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1)
+                  : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
+}
+int64_t pressure_nodes(const Geo& g) { return int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1); }
+}  // namespace
+
+// Canonical host data cross the bus as they are (one copy each way, fast from
+// pinned host memory) and are scattered to / gathered from the padded layout
+// on the device, staged in the level's scratch vector bw64.
 extern "C" int hhg_vector_from_host(hhg_problem* pb, int level, int prec, const double* host, void* dev) {
   HHG_TRY(check_level(pb, level, true));
+  HHG_TRY(check_prec(pb, prec));
   if (!host || !dev) return fail(HHG_EINVAL, "null vector");
-  std::vector<double> h;
-  canonical_to_layout(pb->L(level), host, h);
-  return upload(pb, h, prec, dev);
+  Level& lv = pb->L(level);
+  const int64_t nvn = velocity_nodes(lv.g), npn = pressure_nodes(lv.g);
+  HHG_CUDA(cudaMemcpyAsync(lv.bw64, host, size_t(3 * nvn + npn) * 8, cudaMemcpyHostToDevice, pb->stream));
+  if (prec == HHG_FP64) {
+    HHG_CUDA(cudaMemsetAsync(dev, 0, size_t(lv.nvec()) * 8, pb->stream));
+    launch_canon_scatter<double>(lv.g, lv.bw64, static_cast<double*>(dev), nvn, npn, true, false, pb->stream);
+  } else {
+    HHG_CUDA(cudaMemsetAsync(dev, 0, size_t(lv.nvec()) * 4, pb->stream));
+    launch_canon_scatter<float>(lv.g, lv.bw64, static_cast<float*>(dev), nvn, npn, true, false, pb->stream);
+  }
+  HHG_CHECK_LAUNCH();
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  return HHG_OK;
 }
 
 extern "C" int hhg_vector_to_host(hhg_problem* pb, int level, int prec, const void* dev, double* host) {
   HHG_TRY(check_level(pb, level, true));
+  HHG_TRY(check_prec(pb, prec));
   if (!host || !dev) return fail(HHG_EINVAL, "null vector");
-  const Level& lv = pb->L(level);
-  std::vector<double> h(size_t(lv.nvec()));
-  if (prec == HHG_FP64) {
-    HHG_CUDA(cudaMemcpyAsync(h.data(), dev, h.size() * 8, cudaMemcpyDeviceToHost, pb->stream));
-    HHG_CUDA(cudaStreamSynchronize(pb->stream));
-  } else {
-    std::vector<float> f(h.size());
-    HHG_CUDA(cudaMemcpyAsync(f.data(), dev, f.size() * 4, cudaMemcpyDeviceToHost, pb->stream));
-    HHG_CUDA(cudaStreamSynchronize(pb->stream));
-    std::copy(f.begin(), f.end(), h.begin());
-  }
-  layout_to_canonical(lv, h, host);
+  Level& lv = pb->L(level);
+  const int64_t nvn = velocity_nodes(lv.g), npn = pressure_nodes(lv.g);
+  if (prec == HHG_FP64) launch_canon_gather<double>(lv.g, static_cast<const double*>(dev), lv.bw64, nvn, npn, pb->stream);
+  else launch_canon_gather<float>(lv.g, static_cast<const float*>(dev), lv.bw64, nvn, npn, pb->stream);
+  HHG_CHECK_LAUNCH();
+  HHG_CUDA(cudaMemcpyAsync(host, lv.bw64, size_t(3 * nvn + npn) * 8, cudaMemcpyDeviceToHost, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));
   return HHG_OK;
 }
 
@@ -1186,16 +1175,15 @@ extern "C" int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, co
   if (!f_nodal || !w_nodal) return fail(HHG_EINVAL, "null nodal data");
   Level& lv = pb->L(level);
   const Geo& g = lv.g;
-  const int64_t nvn = g.G == 1 ? int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1)
-                               : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
-  std::vector<double> F(size_t(lv.nvec()), 0.0), W(size_t(lv.nvec()), 0.0);
-  for (int c = 0; c < 3; ++c)
-    for_each_velocity_node(g, [&](int64_t ci, int gg, int64_t site, bool bnd) {
-      F[size_t((c * g.G + gg) * g.arr + site)] = f_nodal[c * nvn + ci];
-      if (bnd) W[size_t((c * g.G + gg) * g.arr + site)] = w_nodal[c * nvn + ci];
-    });
-  HHG_CUDA(cudaMemcpyAsync(lv.tmp64, F.data(), F.size() * 8, cudaMemcpyHostToDevice, pb->stream));
-  HHG_CUDA(cudaMemcpyAsync(lv.W, W.data(), W.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  const int64_t nvn = velocity_nodes(g), npn = pressure_nodes(g);
+  // nodal data to the layout: F at every velocity node, W at the boundary ones
+  HHG_CUDA(cudaMemsetAsync(lv.tmp64, 0, size_t(lv.nvec()) * 8, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(lv.W, 0, size_t(lv.nvec()) * 8, pb->stream));
+  HHG_CUDA(cudaMemcpyAsync(lv.bw64, f_nodal, size_t(3 * nvn) * 8, cudaMemcpyHostToDevice, pb->stream));
+  launch_canon_scatter<double>(g, lv.bw64, lv.tmp64, nvn, npn, false, false, pb->stream);
+  HHG_CUDA(cudaMemcpyAsync(lv.bw64, w_nodal, size_t(3 * nvn) * 8, cudaMemcpyHostToDevice, pb->stream));
+  launch_canon_scatter<double>(g, lv.bw64, lv.W, nvn, npn, false, true, pb->stream);
+  HHG_CHECK_LAUNCH();
   HHG_CUDA(cudaMemsetAsync(lv.rhs, 0, size_t(lv.nvec()) * 8, pb->stream));
   // f = M f_h - A w_h (interior velocity rows)
   HHG_TRY(apply_op<double>(pb, lv, OP_MVINT, MODE_SET, lv.tmp64, nullptr, lv.rhs));
@@ -1208,7 +1196,8 @@ extern "C" int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, co
   launch_sub_scalar_p<double>(g, lv.rhs + po, pb->scal, 1.0 / double((g.nx + 1) * int64_t(g.ny + 1) * (g.nz + 1)), pb->stream);
   HHG_CHECK_LAUNCH();
   HHG_CUDA(cudaMemsetAsync(lv.tmp64, 0, size_t(lv.nvec()) * 8, pb->stream));
-  HHG_CUDA(cudaStreamSynchronize(pb->stream));
+  HHG_CUDA(cudaMemsetAsync(lv.bw64, 0, size_t(lv.nvec()) * 8, pb->stream));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));    // the host buffers may be reused on return
   lv.has_rhs = true;
   return HHG_OK;
 }
@@ -1232,11 +1221,6 @@ int check_params(const hhg_params* prm) {
       (prm->ahat != HHG_AHAT_F && prm->ahat != HHG_AHAT_S) || !(prm->omega_inv > 0))
     return fail(HHG_EINVAL, "invalid FMG parameters");
   return HHG_OK;
-}
-int check_prec(const hhg_problem* pb, int prec) {
-  if (prec == HHG_FP64) return HHG_OK;
-  if (prec == HHG_FP32 && pb->desc.solve == HHG_SOLVE_MIXED) return HHG_OK;
-  return fail(HHG_EINVAL, "FP32 operations need a problem created with HHG_SOLVE_MIXED");
 }
 }  // namespace
 
@@ -1905,15 +1889,11 @@ extern "C" int hhg_error_norms(hhg_problem* pb, int level, const void* x, const 
   HHG_CUDA(cudaMemsetAsync(f.x64, 0, size_t(f.nvec()) * 8, pb->stream));
   HHG_TRY(prolong_add<double>(pb, level + 1, c.tmp64, f.x64, false));
   // exact nodal values on level l+1
-  const int64_t nvn = g.G == 1 ? int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1)
-                               : int64_t(2 * g.nx + 1) * (2 * g.ny + 1) * (2 * g.nz + 1);
-  const int64_t npn = int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
-  std::vector<double> can(size_t(3 * nvn + npn));
-  std::copy(u_exact, u_exact + 3 * nvn, can.begin());
-  std::copy(p_exact, p_exact + npn, can.begin() + 3 * nvn);
-  std::vector<double> h;
-  canonical_to_layout(f, can.data(), h);
-  HHG_CUDA(cudaMemcpyAsync(f.tmp64, h.data(), h.size() * 8, cudaMemcpyHostToDevice, pb->stream));
+  const int64_t nvn = velocity_nodes(g), npn = pressure_nodes(g);
+  HHG_CUDA(cudaMemcpyAsync(f.bw64, u_exact, size_t(3 * nvn) * 8, cudaMemcpyHostToDevice, pb->stream));
+  HHG_CUDA(cudaMemcpyAsync(f.bw64 + 3 * nvn, p_exact, size_t(npn) * 8, cudaMemcpyHostToDevice, pb->stream));
+  HHG_CUDA(cudaMemsetAsync(f.tmp64, 0, size_t(f.nvec()) * 8, pb->stream));
+  launch_canon_scatter<double>(g, f.bw64, f.tmp64, nvn, npn, true, false, pb->stream);
   launch_xpby<double>(f.tmp64, -1.0, f.x64, f.tmp64, f.nvec(), pb->stream);        // d = x* - I x
   HHG_TRY(project_pressure(pb, f, f.tmp64));
   HHG_TRY(apply_op<double>(pb, f, OP_MASS, MODE_SET, f.tmp64, nullptr, f.x64));    // M d

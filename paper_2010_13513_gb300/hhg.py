@@ -138,6 +138,19 @@ class HHGError(RuntimeError):
     pass
 
 
+def _host_ptr(a, n):
+    """(double pointer, object keeping it alive) of n contiguous host doubles:
+    a CPU float64 tensor is used in place, anything else through numpy."""
+    if isinstance(a, torch.Tensor):
+        if a.device.type != "cpu" or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() < n:
+            raise ValueError("host tensor must be a contiguous CPU float64 tensor of the canonical length")
+        return C.cast(a.data_ptr(), C.POINTER(C.c_double)), a
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size < n:
+        raise ValueError("host array shorter than the canonical length")
+    return _dp(a), a
+
+
 def _check(rc, what=""):
     if rc != 0:
         buf = C.create_string_buffer(1024)
@@ -229,11 +242,15 @@ class Problem:
         _check(load().hhg_vector_from_host(self.h, level, prec, _dp(host), _ptr(out)), "hhg_vector_from_host")
         return out
 
-    def to_host(self, level, dev, prec=None):
+    def to_host(self, level, dev, prec=None, out=None):
+        """Canonical FP64 host copy of a device vector; `out` may be a
+        contiguous CPU float64 tensor (pinned memory: one fast copy)."""
         prec = (FP64 if dev.dtype == torch.float64 else FP32) if prec is None else prec
         info = self.layout(level)
-        host = np.zeros(3 * info.n_velocity_nodes + info.n_pressure_nodes)
-        _check(load().hhg_vector_to_host(self.h, level, prec, _ptr(dev), _dp(host)), "hhg_vector_to_host")
+        n = 3 * info.n_velocity_nodes + info.n_pressure_nodes
+        host = np.zeros(n) if out is None else out
+        ptr, host = _host_ptr(host, n)
+        _check(load().hhg_vector_to_host(self.h, level, prec, _ptr(dev), ptr), "hhg_vector_to_host")
         return host
 
     def level_vector(self, level, which):
@@ -248,9 +265,12 @@ class Problem:
 
     # ------------------------------------------------------------------ rhs
     def set_rhs(self, level, f_nodal, w_nodal):
-        f = np.ascontiguousarray(f_nodal, dtype=np.float64)
-        w = np.ascontiguousarray(w_nodal, dtype=np.float64)
-        _check(load().hhg_set_rhs(self.h, level, _dp(f), _dp(w)), "hhg_set_rhs")
+        """Nodal forcing and Dirichlet data (3 x n_velocity_nodes each), numpy
+        arrays or contiguous CPU float64 tensors (pinned memory: fast copies)."""
+        n = 3 * self.layout(level).n_velocity_nodes
+        fp, f = _host_ptr(f_nodal, n)
+        wp, w = _host_ptr(w_nodal, n)
+        _check(load().hhg_set_rhs(self.h, level, fp, wp), "hhg_set_rhs")
 
     # ---------------------------------------------------------------- steps
     @staticmethod
