@@ -146,6 +146,16 @@ __device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restric
   }
 }
 
+// Programmatic dependent launch (Gauss-Seidel phases): a kernel launched with
+// the programmatic-serialization attribute may start while its predecessor in
+// the stream finishes; it waits here until the predecessor has completed and
+// its writes are visible (no-op for an ordinary launch), and each block
+// signals its own successor once its work is done.  (In the stencil-row
+// kernels the wait doubles the register count of the 25-way row dispatch, so
+// those launch plainly.)
+__device__ __forceinline__ void pdl_wait() { cudaGridDependencySynchronize(); }
+__device__ __forceinline__ void pdl_trigger() { cudaTriggerProgrammaticLaunchCompletion(); }
+
 template <int DISC, int VARNU, int OP, class T, int MODE>
 __global__ void __launch_bounds__(256)
     k_rows_fast(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, T alpha, OpDev op, int kp,
@@ -202,12 +212,34 @@ __global__ void __launch_bounds__(256)
   using S = gen::S<DISC, VARNU, OP_A>;
   constexpr gen::RowS rw = S::rows[GRP];       // component-0 row of the group; all terms in segment 1
   static_assert(rw.n0 == 0 && rw.n2 == 0, "A rows carry only nu-scaled terms");
+  pdl_wait();
   gs_site<DISC, VARNU, GRP, T, rw.t0, rw.n1>(g, u, rhs, inv_diag, colour, tab);
+  pdl_trigger();
 }
 
 }  // namespace
 
 // ================================================================= launchers
+// Launches of at most about one wave (152 SMs x 8 blocks) may overlap their
+// predecessor's tail (programmatic dependent launch): there the launch gap is
+// a large part of the kernel time.  Longer grids are launched plainly.
+constexpr int64_t kPdlMaxBlocks = 152 * 8;
+
+template <class K, class... A>
+void launch_pdl(K kernel, dim3 grd, dim3 blk, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grd;
+  cfg.blockDim = blk;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = int64_t(grd.x) * grd.y * grd.z <= kPdlMaxBlocks ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int DISC, int VARNU, int OP, class T>
 void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, const T* x, const T* b, T* y,
                       double alpha, const Shape& sh, cudaStream_t s) {
@@ -237,14 +269,14 @@ void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double i
   dim3 grd((plane + nt - 1) / nt, 1, g.nz + 1);
   ++g_launches;
   switch (grp) {
-    case 0: k_gs_fast<DISC, VARNU, 0, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
-    case 1: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 1, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
-    case 2: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 2, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
-    case 3: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 3, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
-    case 4: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 4, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
-    case 5: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 5, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
-    case 6: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 6, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
-    case 7: if constexpr (DISC == 2) k_gs_fast<DISC, VARNU, 7, T><<<grd, blk, 0, s>>>(g, u, rhs, T(inv_diag), colour, tb); break;
+    case 0: launch_pdl(k_gs_fast<DISC, VARNU, 0, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
+    case 1: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 1, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
+    case 2: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 2, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
+    case 3: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 3, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
+    case 4: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 4, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
+    case 5: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 5, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
+    case 6: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 6, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
+    case 7: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 7, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
     default: break;
   }
 }
