@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhhg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "fast.cu", "small.cu", "nn.cu", "noalloc.cu", "stencils.cpp", "problem.cpp"]
+SOURCES = ["kernels.cu", "fast.cu", "tile.cu", "small.cu", "nn.cu", "noalloc.cu", "stencils.cpp", "problem.cpp"]
 
 
 def _nvcc():

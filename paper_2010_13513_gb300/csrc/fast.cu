@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "fast.h"
+#include "tile.h"
 #include "kernels.h"
 #include "structure.inc"
 
@@ -295,6 +296,8 @@ int fast_terms(int disc, int varnu, int op) {
 template <class T>
 void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode, const T* x,
                const T* b, T* y, double alpha, const Shape& sh, cudaStream_t s) {
+  if constexpr (std::is_same_v<T, float>)
+    if (sh.row_tile && tile_rows(disc, varnu, op, mode, g, od, tab, x, b, y, alpha, s)) return;
 #define HHG_R(D, V, O) \
   if (disc == D && varnu == V && op == O) return launch_rows_fast<D, V, O, T>(g, od, tab, mode, x, b, y, alpha, sh, s);
   HHG_R(1, 0, OP_FULL) HHG_R(1, 0, OP_BT) HHG_R(1, 0, OP_BC)

@@ -21,6 +21,7 @@ struct Shape {
   int row_threads = 128;   // threads per block of the row kernels (64 / 128 / 256)
   int row_kplanes = 2;     // k planes per thread of the row kernels
   int gs_threads = 128;    // threads per block of the Gauss-Seidel kernels
+  int row_tile = 0;        // FP32 rows by the shared-memory-tiled kernels (tile.cu; autotuner candidate)
 };
 
 // number of interior terms of a specialised operator (-1 if none)

@@ -18,6 +18,7 @@
 #include "kernels.h"
 #include "nn.h"
 #include "small.h"
+#include "tile.h"
 
 using namespace hhg;
 
@@ -1158,6 +1159,7 @@ extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, 
   }
   HHG_TRY(build_coarse(pb));
   if (pb->nn_h > 0) HHG_TRY(nn_setup(pb));
+  tile_init();
   for (Level& lv : pb->lv) {
     HHG_TRY(default_resident(pb, lv, HHG_FP64));
     HHG_TRY(default_resident(pb, lv, HHG_FP32));
@@ -1371,6 +1373,31 @@ extern "C" int hhg_get_level_smoother(hhg_problem* pb, int level, int prec, int*
   if (!ctas || !threads) return fail(HHG_EINVAL, "null argument");
   *ctas = pb->L(level).rctas[prec];
   *threads = pb->L(level).rthreads[prec];
+  return HHG_OK;
+}
+
+extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads, int row_kplanes, int gs_threads,
+                                    int row_tile) {
+  HHG_TRY(check_level(pb, level));
+  auto ok_threads = [](int t) { return t == 64 || t == 128 || t == 256; };
+  if (!ok_threads(row_threads) || !ok_threads(gs_threads) || row_kplanes < 1 || row_kplanes > 64 ||
+      (row_tile != 0 && row_tile != 1))
+    return fail(HHG_EINVAL, "invalid launch shape");
+  Shape& sh = pb->L(level).shape;
+  sh.row_threads = row_threads;
+  sh.row_kplanes = row_kplanes;
+  sh.gs_threads = gs_threads;
+  sh.row_tile = row_tile;
+  for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
+  pb->graphs.clear();
+  return HHG_OK;
+}
+
+extern "C" int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape4) {
+  HHG_TRY(check_level(pb, level));
+  if (!shape4) return fail(HHG_EINVAL, "null argument");
+  const Shape& sh = pb->L(level).shape;
+  shape4[0] = sh.row_threads; shape4[1] = sh.row_kplanes; shape4[2] = sh.gs_threads; shape4[3] = sh.row_tile;
   return HHG_OK;
 }
 
@@ -1642,12 +1669,23 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
       Shape sh = lv.shape;
       sh.row_threads = t;
       sh.row_kplanes = kp;
+      sh.row_tile = 0;
       const float ms = time_it([&] {
         fast_rows<T>(disc, varnu, OP_FULL, lv.g, lv.op[OP_FULL], ftab<T>(lv, OP_FULL), MODE_RES, xa, xa, xb, 1.0, sh,
                      pb->stream);
       });
       if (ms < best) { best = ms; bestS.row_threads = t; bestS.row_kplanes = kp; }
     }
+  // FP32 rows: the shared-memory-tiled kernels against the best plain shape
+  if (std::is_same<T, float>::value) {
+    Shape sh = bestS;
+    sh.row_tile = 1;
+    const float ms = time_it([&] {
+      fast_rows<T>(disc, varnu, OP_FULL, lv.g, lv.op[OP_FULL], ftab<T>(lv, OP_FULL), MODE_RES, xa, xa, xb, 1.0, sh,
+                   pb->stream);
+    });
+    bestS.row_tile = ms < best ? 1 : 0;
+  }
   // Gauss-Seidel kernels: one forward sweep
   best = 1e30f;
   for (int t : threads) {
@@ -1719,10 +1757,11 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       HHG_TRY(tune_smoother<double>(pb, lv, reps, lv.bw64, lv.rhs, lv.tmp64));
     }
     if (shapes_out) {
-      int* o = shapes_out + 5 * (l - pb->desc.coarse_level);
+      int* o = shapes_out + 6 * (l - pb->desc.coarse_level);
       o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
       o[3] = lv.rctas[mixed ? HHG_FP32 : HHG_FP64];
       o[4] = lv.rthreads[mixed ? HHG_FP32 : HHG_FP64];
+      o[5] = lv.shape.row_tile;
     }
   }
   pb->wu_counted = wu;

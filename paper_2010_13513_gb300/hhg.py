@@ -102,6 +102,8 @@ def load():
         "hhg_set_graph_mode": [P, I],
         "hhg_set_small_level_mode": [P, I],
         "hhg_set_level_smoother": [P, I, I, I, I],
+        "hhg_set_launch_shape": [P, I, I, I, I, I],
+        "hhg_get_launch_shape": [P, I, C.POINTER(C.c_int)],
         "hhg_get_level_smoother": [P, I, I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "hhg_error_norms": [P, I, VP, DP, DP, DP, DP],
         "hhg_block_norms_noalloc": [VP, I, C.c_int64, C.c_int64, VP, VP],
@@ -361,11 +363,21 @@ class Problem:
 
     def autotune(self, reps=5):
         """Per-level launch choices; returns {level: (row_threads,
-        row_kplanes, gs_threads, resident_ctas, resident_threads)}."""
+        row_kplanes, gs_threads, resident_ctas, resident_threads, row_tile)}."""
         n = self.L - self.lc + 1
-        out = (C.c_int * (5 * n))()
+        out = (C.c_int * (6 * n))()
         _check(load().hhg_autotune(self.h, reps, out), "hhg_autotune")
-        return {self.lc + i: tuple(out[5 * i:5 * i + 5]) for i in range(n)}
+        return {self.lc + i: tuple(out[6 * i:6 * i + 6]) for i in range(n)}
+
+    def set_launch_shape(self, level, row_threads, row_kplanes, gs_threads, row_tile):
+        _check(load().hhg_set_launch_shape(self.h, level, row_threads, row_kplanes, gs_threads, int(row_tile)),
+               "hhg_set_launch_shape")
+
+    def launch_shape(self, level):
+        """(row_threads, row_kplanes, gs_threads, row_tile) of a level."""
+        out = (C.c_int * 4)()
+        _check(load().hhg_get_launch_shape(self.h, level, out), "hhg_get_launch_shape")
+        return tuple(out)
 
     def set_small_level_mode(self, on):
         _check(load().hhg_set_small_level_mode(self.h, int(on)), "hhg_set_small_level_mode")

@@ -135,6 +135,38 @@ def test_resident_smoother_every_cta_count(disc, L, nu_a, ahat, xi):
         assert rel(v, ref) < 1e-4
 
 
+@pytest.mark.parametrize("disc,box,L,nu_a", [("P2P1", (1, 1, 1), 3, 0.0), ("P2P1", (1, 2, 1), 3, 1.1),
+                                              ("P1P1", (1, 1, 2), 4, 0.0), ("P1P1", (2, 1, 1), 4, 1.4)])
+def test_tiled_rows_match_plain_rows(disc, box, L, nu_a):
+    """The shared-memory-tiled FP32 rows (full operator apply and residual,
+    the smoother's B^T and (B, -C) residual rows) give the plain kernels'
+    results, and the FP64 apply within FP32 rounding; tiles cover partial
+    32 x 4 x 4 blocks at the lattice edges."""
+    from paper_2010_13513_gb300 import hhg
+    pb = lib_problem(box, L, disc, lc=1, nu_a=nu_a, solve="mixed")
+    hy = oracle_hierarchy(box, L, disc, lc=1, nu_a=nu_a)
+    lev = hy.lv[L]
+    x, b = random_vector(lev, 21), random_vector(lev, 22)
+    x32, b32 = pb.to_device(L, x, prec=hhg.FP32), pb.to_device(L, b, prec=hhg.FP32)
+    out = {}
+    for tile in (0, 1):
+        pb.set_launch_shape(L, 128, 2, 128, tile)
+        assert pb.launch_shape(L)[3] == tile
+        y = pb.new_vector(L, hhg.FP32)
+        pb.apply(L, "FULL", x32, y)
+        r = pb.new_vector(L, hhg.FP32)
+        pb.residual(L, x32, b32, r)
+        xs = x32.clone()
+        pb.set_level_smoother(L, 0)                      # per-phase smoother: B^T and (B, -C) residual rows
+        pb.smooth(L, hhg.Params.make(ahat="f", xi=1, omega_inv=OMEGA_INV[disc]), 1, xs, b32)
+        out[tile] = [pb.to_host(L, v) for v in (y, r, xs)]
+    for a, c in zip(out[0], out[1]):
+        assert rel(c, a) < 1e-6
+    y64 = pb.new_vector(L)
+    pb.apply(L, "FULL", pb.to_device(L, x), y64)
+    assert rel(out[1][0], pb.to_host(L, y64)) < 1e-5
+
+
 def test_resident_smoother_rejects_what_does_not_fit():
     from paper_2010_13513_gb300 import hhg
     pb = lib_problem((1, 1, 1), 3, "P2P1", lc=1)
@@ -369,9 +401,9 @@ def test_autotune_keeps_results():
     pb.fmg_solve(prm, x1, stats=False)
     shapes = pb.autotune(reps=2)
     assert set(shapes) == {1, 2, 3, 4}
-    for t, kp, gs, rc, rt in shapes.values():
+    for t, kp, gs, rc, rt, tile in shapes.values():
         assert t in (64, 128, 256) and kp in (1, 2, 4, 8, 16) and gs in (64, 128, 256)
-        assert rc in (0, 1, 2, 4, 8, 16) and rt in (256, 512, 1024)
+        assert rc in (0, 1, 2, 4, 8, 16) and rt in (256, 512, 1024) and tile in (0, 1)
     x2 = pb.new_vector(4)
     pb.fmg_solve(prm, x2, stats=False)
     torch.cuda.synchronize()
