@@ -490,6 +490,70 @@ def run_p2_l7(args):
                                       "val_rel_err": rep.val_rel_err, "train_ms": rep.train_ms, **out}}}))
 
 
+def run_tme(args):
+    """The paper's parameter study (Sec. 5.1, Table 3) on the GPU: for P1-P1
+    at level 6 and P2-P1 at level 5 on the 6-tetrahedron cube with the cube
+    solution of Sec. 5.1.1, omega^{-1} by 100 power iterations, then one FMG
+    solve for every tuple of the search space S with kappa = 1 (384 tuples),
+    gamma_u and gamma_p against the discrete solution's error (Eq. gamma), the
+    model work W(FMG(s)), and the minimal-work tuple under the three bound
+    pairs of Table 3.  (The paper's mesh has 24 macro tetrahedra; the study and
+    the work model are the same.)"""
+    import itertools
+    import torch
+    from hhg_inputs import Workload
+    from paper_2010_13513_gb300 import hhg
+    torch.cuda.set_stream(torch.cuda.Stream())
+    bounds = [(1.1, 2.0), (1.1, 5.0), (2.0, 10.0)]
+    pairs = [("f", 1), ("f", 2), ("f", 3), ("f", 4), ("s", 1), ("s", 2)]
+    out = {}
+    t0 = time.perf_counter()
+    for disc, L, lc in (("P1P1", 6, 0), ("P2P1", 5, 1)):
+        wl = Workload("paper")
+        pb = hhg.Problem(hhg.Mesh.box(1, 1, 1, 1.0), disc=disc, L=L, coarse_level=lc, solve="fp64", error_level=True)
+        hhg.set_workload_rhs(pb, wl)
+        pb.set_graph_mode(False)                 # one solve per tuple: no graph per tuple
+        info = pb.layout(L)
+        om = pb.estimate_omega(L, np.random.default_rng(0).uniform(-1, 1, info.n_pressure_nodes), 100)
+        fine = pb.layout(L + 1)
+        ue = wl.exact_velocity(hhg.velocity_coords(fine)).T.ravel()
+        pe = wl.exact_pressure(hhg.pressure_coords(fine))
+        # the discrete solution's error (residuals below 1e-12)
+        prm0 = hhg.Params.make(3, 3, 0, 1, "s", 2, om)
+        xs = pb.new_vector(L)
+        b = pb.level_vector(L, "rhs")
+        r = pb.new_vector(L)
+        for _ in range(300):
+            pb.vcycle(L, prm0, xs, b)
+            if max(pb.residual(L, xs, b, r, norms=True)) < 1e-12:
+                break
+        e_disc = pb.error_norms(L, xs, ue, pe)
+        rows = []
+        x = pb.new_vector(L)
+        for npre, npost, ninc, (ah, xi) in itertools.product(range(4), range(4), range(4), pairs):
+            prm = hhg.Params.make(npre, npost, ninc, 1, ah, xi, om)
+            st = pb.fmg_solve(prm, x)
+            eu, ep = pb.error_norms(L, x, ue, pe)
+            rows.append({"s": [npre, npost, ninc, 1, ah, xi], "wu": st.wu_model,
+                         "gamma_u": eu / e_disc[0], "gamma_p": ep / e_disc[1]})
+        best = []
+        for gu, gp in bounds:
+            ok = [q for q in rows if q["gamma_u"] <= gu and q["gamma_p"] <= gp]
+            q = min(ok, key=lambda q: q["wu"]) if ok else None
+            best.append({"bounds": [gu, gp], **(q or {"s": None})})
+        out[f"{disc}_L{L}"] = {"dofs": info.n_dofs, "omega_inv": om, "err_disc": e_disc, "tuples": len(rows),
+                               "solved_gamma_le_2": sum(q["gamma_u"] <= 2 and q["gamma_p"] <= 2 for q in rows),
+                               "min_gamma_p": min(q["gamma_p"] for q in rows), "table3": best}
+        del pb
+    dt = time.perf_counter() - t0
+    print(json.dumps({"metric": "TME parameter study (Table 3): minimal W(FMG(s)) under gamma bounds",
+                      "value": dt, "unit": "s (whole study)", "n_gpus": 1, "higher_is_better": False,
+                      "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "6-tet cube, cube solution of Sec. 5.1.1, S with kappa = 1 "
+                                             "(4 x 4 x 4 x 6 = 384 tuples per discretisation), FP64 solves",
+                                 "results": out}}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -526,7 +590,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hhg", choices=["hhg", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="p2-l6", choices=["p2-l6", "batched", "p1-visc", "p2-l7"])
+    ap.add_argument("--workload", default="p2-l6", choices=["p2-l6", "batched", "p1-visc", "p2-l7", "tme"])
     ap.add_argument("--profile-region", action="store_true",
                     help="only set-up, warm-up and the timed FMG steps, bracketed by cudaProfilerStart/Stop")
     ap.add_argument("--profile-apply", action="store_true",
@@ -542,6 +606,8 @@ def main():
         return run_p1_visc(args)
     if args.workload == "p2-l7":
         return run_p2_l7(args)
+    if args.workload == "tme":
+        return run_tme(args)
 
     import torch
     import torch.distributed as dist
