@@ -705,7 +705,8 @@ def main():
                    "mixed_vs_fp64_rel_diff": mixed_vs_fp64},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": measured_traffic(),
-                     "kernel": "FP32 operator apply y = calA x, level 6 (k_rows_fast, FULL)",
+                     "kernel": "FP32 operator apply y = calA x, level 6 (%s, FULL)" % (
+                         "k_rows_vec, 4 sites per thread" if pb.launch_shape(L)[4] == 4 else "k_rows_fast"),
                      "alg_bytes": alg_bytes, "avg_launch_us": t_apply * 1e6, "peak_source": src},
         "e2e": {"value": e2e_v, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,

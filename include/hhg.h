@@ -216,10 +216,11 @@ int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats
  * hhg_set_level_smoother): every candidate is timed `reps` times with CUDA
  * events on the problem's stream in the precision of the V-cycles, the
  * fastest is kept.  Uses only the library's scratch vectors; cached graphs
- * are dropped.  shapes_out (optional) receives 6 ints per level (coarse ..
+ * are dropped.  shapes_out (optional) receives 7 ints per level (coarse ..
  * L): row threads, row k planes, Gauss-Seidel threads, resident CTAs,
- * resident threads per CTA, and whether the FP32 stencil rows use the
- * shared-memory-tiled kernels.  Synchronises. */
+ * resident threads per CTA, whether the FP32 stencil rows use the
+ * shared-memory-tiled kernels, and the row kernels' sites per thread.
+ * Synchronises. */
 int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
 /* Not in the paper (GPU launch choices): the launch shape of the stencil
  * kernels of one level -- threads per block of the row kernels (64/128/256),
@@ -228,10 +229,15 @@ int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
  * operator (apply, residual) and of the smoother's B^T and (B, -C) residuals
  * in shared-memory tiles (a block loads a 32 x 4 x 4 tile of lattice sites
  * plus halo of the input arrays of one group of rows; default off, an
- * autotuner candidate).  Results agree up to rounding.  Drops
- * cached graphs.  hhg_get_launch_shape returns the four values. */
-int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads, int row_kplanes, int gs_threads, int row_tile);
-int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape4);
+ * autotuner candidate), and row_sites = 1 or 4 sites per thread of the
+ * row kernels (4: each warp evaluates four runs of 32 consecutive
+ * positions of the padded (i, j) plane, sharing each term's address
+ * between the runs; row_tile = 1 takes precedence for FP32).
+ * Results agree up to rounding.  Drops cached graphs.
+ * hhg_get_launch_shape writes the five values to shape5. */
+int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads, int row_kplanes, int gs_threads, int row_tile,
+                         int row_sites);
+int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape5);
 
 /* ------------------------------------------- learned coarse-grid correction */
 /* Not in the paper: a small MLP  y = W3 relu(W2 relu(W1 x + b1) + b2) + b3

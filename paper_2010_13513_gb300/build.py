@@ -20,7 +20,11 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhhg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "fast.cu", "tile.cu", "small.cu", "nn.cu", "noalloc.cu", "stencils.cpp", "problem.cpp"]
+# (source, object, extra flags): fast.cu is compiled once per precision
+SOURCES = [("kernels.cu", "kernels", []), ("fast.cu", "fast64", ["-DHHG_FAST_ONLY=64"]),
+           ("fast.cu", "fast32", ["-DHHG_FAST_ONLY=32"]), ("tile.cu", "tile", []), ("small.cu", "small", []),
+           ("nn.cu", "nn", []), ("noalloc.cu", "noalloc", []), ("stencils.cpp", "stencils", []),
+           ("problem.cpp", "problem", [])]
 
 
 def _nvcc():
@@ -30,11 +34,12 @@ def _nvcc():
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src, verbose):
+def _compile(unit, verbose):
+    src, name, extra = unit
     nvcc = _nvcc()
-    obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
+    obj = os.path.join(OUT, name + ".o")
     cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-I", OUT]
+           "-I", os.path.join(ROOT, "include"), "-I", OUT] + extra
     if src.endswith(".cu"):
         cmd += ARCH + ["-lineinfo", "--expt-relaxed-constexpr"]
         if verbose:

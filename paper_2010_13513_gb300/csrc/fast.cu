@@ -73,6 +73,13 @@ __device__ __forceinline__ T boundary_seg2(const Geo& g, const OpDev& op, int r,
   return a;
 }
 
+// the same as an out-of-line call (rare boundary sites of unrolled code)
+template <class T>
+__device__ __noinline__ T boundary_seg2_call(const Geo& g, const OpDev& op, int r, int i, int j, int k, const T* x,
+                                            int64_t idx) {
+  return boundary_seg2<T>(g, op, r, i, j, k, x, idx);
+}
+
 template <class S, int R, class F>
 __device__ __forceinline__ void dispatch(int r, F&& f) {
   if constexpr (R < S::R) {
@@ -90,10 +97,64 @@ __device__ __forceinline__ T seg_sum(const Tab& tab, const T* __restrict__ xs) {
   return a;
 }
 
-// launch shapes (threads per block, k planes per thread) are run-time
-// parameters chosen per level by the autotuner (hhg_autotune)
+// the same sums at V sites 32 apart (xs + 32 v): per term one address and V
+// loads at compile-time distances
+template <int T0, int N, int V, class T, class Tab>
+__device__ __forceinline__ void seg_sum_v(const Tab& tab, const T* __restrict__ xs, T (&a)[V]) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) a[v] = T(0);
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    const T wt = tab.w[T0 + t];
+    const T* p = xs + tab.off[T0 + t];
+#pragma unroll
+    for (int v = 0; v < V; ++v) a[v] += wt * __ldg(p + 32 * v);
+  }
+}
+
+// launch shapes (threads per block, k planes per thread, sites per thread)
+// are run-time parameters chosen per level by the autotuner (hhg_autotune)
 
 // ------------------------------------------------------------- row kernels
+// one row at site (i, j, k); bij: the site lies on an i or j face of the box
+template <int VARNU, class T, int MODE, int OUT, int OG, int ALL, int T0, int N0, int N1, int N2, class Tab>
+__device__ __forceinline__ void row_site(const Geo& g, int R, int i, int j, int k, bool bij, const T* __restrict__ x,
+                                         const T* __restrict__ b, T* __restrict__ y, T alpha, const OpDev& op,
+                                         const Tab& tab) {
+  constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
+  const int64_t idx = fsite(g, i, j, k);
+  T* yo = y + int64_t(OUT) * g.arr + idx;
+  const bool bnd = bij || 2 * k + oz == 0 || 2 * k + oz == 2 * g.nz;
+  T a0, a1, a2;
+  if (!bnd) {
+    const T* xs = x + idx;
+    a0 = seg_sum<T0, N0, T>(tab, xs);
+    a1 = seg_sum<T0 + N0, N1, T>(tab, xs);
+    a2 = seg_sum<T0 + N0 + N1, N2, T>(tab, xs);
+  } else if (ALL) {
+    // boundary pressure row: with zero Dirichlet velocity entries the merged
+    // B terms are exact (every tetrahedron containing an interior velocity
+    // DoF lies inside the domain; boundary and halo velocity values are 0);
+    // only the C terms need the per-cube restriction to the domain
+    const T* xs = x + idx;
+    a0 = seg_sum<T0, N0, T>(tab, xs);
+    a1 = seg_sum<T0 + N0, N1, T>(tab, xs);
+    a2 = N2 > 0 ? boundary_seg2<T>(g, op, R, i, j, k, x, idx) : T(0);
+  } else {
+    if (MODE != MODE_ADD) *yo = T(0);
+    return;
+  }
+  T v = a0;
+  if (VARNU) {
+    v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
+  } else {
+    v += a1 + a2;
+  }
+  if (MODE == MODE_SET) *yo = v;
+  else if (MODE == MODE_RES) *yo = b[int64_t(OUT) * g.arr + idx] - v;
+  else *yo += alpha * v;
+}
+
 // grid: x over the (i, j) plane of sites (flat, i fastest), y = groups of
 // kp planes, z = row.  The row is the slowest grid dimension, so the
 // blocks resident at the same time run the same (fully unrolled) row code.
@@ -112,38 +173,87 @@ __device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restric
   const int k0 = blockIdx.y * kp;
   const bool bij = 2 * i + ox == 0 || 2 * i + ox == 2 * g.nx || 2 * j + oy == 0 || 2 * j + oy == 2 * g.ny;
 #pragma unroll 1
-  for (int k = k0; k < k0 + kp && k <= g.nz - oz; ++k) {
-    const int64_t idx = fsite(g, i, j, k);
-    T* yo = y + int64_t(OUT) * g.arr + idx;
-    const bool bnd = bij || 2 * k + oz == 0 || 2 * k + oz == 2 * g.nz;
-    T a0, a1, a2;
-    if (!bnd) {
-      const T* xs = x + idx;
-      a0 = seg_sum<T0, N0, T>(tab, xs);
-      a1 = seg_sum<T0 + N0, N1, T>(tab, xs);
-      a2 = seg_sum<T0 + N0 + N1, N2, T>(tab, xs);
-    } else if (ALL) {
-      // boundary pressure row: with zero Dirichlet velocity entries the merged
-      // B terms are exact (every tetrahedron containing an interior velocity
-      // DoF lies inside the domain; boundary and halo velocity values are 0);
-      // only the C terms need the per-cube restriction to the domain
-      const T* xs = x + idx;
-      a0 = seg_sum<T0, N0, T>(tab, xs);
-      a1 = seg_sum<T0 + N0, N1, T>(tab, xs);
-      a2 = N2 > 0 ? boundary_seg2<T>(g, op, R, i, j, k, x, idx) : T(0);
-    } else {
-      if (MODE != MODE_ADD) *yo = T(0);
-      continue;
-    }
-    T v = a0;
+  for (int k = k0; k < k0 + kp && k <= g.nz - oz; ++k)
+    row_site<VARNU, T, MODE, OUT, OG, ALL, T0, N0, N1, N2>(g, R, i, j, k, bij, x, b, y, alpha, op, tab);
+}
+
+// V sites per thread: a warp takes V runs of 32 consecutive positions
+// m = i + j sx of the padded (i, j) plane (lane l: m0 + l + 32 v).  The site
+// index is m + 1 + sx + (k+1) sy, so the V sites of a term are V coalesced
+// loads at fixed distances from one address.  Positions in the row padding
+// (i > nx - ox) are evaluated but not stored (their reads stay inside the
+// plane's halo rows); a warp whose last run passes the group's last site
+// evaluates its sites one by one (its runs would read past the plane).
+template <int DISC, int VARNU, int OP, class T, int MODE, int V, int OUT, int OG, int ALL, int T0, int N0, int N1,
+          int N2, class Tab>
+__device__ __forceinline__ void eval_row_vec(const Geo& g, int R, const T* __restrict__ x, const T* __restrict__ b,
+                                             T* __restrict__ y, T alpha, const OpDev& op, const Tab& tab, int kp) {
+  constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
+  constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
+  constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
+  const int m0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * V);
+  const int lane = int(threadIdx.x & 31);
+  const int mlast = (g.ny - oy) * g.sx + (g.nx - ox);   // position of the group's last site in the plane
+  if (m0 > mlast) return;
+  const int k0 = blockIdx.y * kp, k1 = min(k0 + kp, g.nz - oz + 1);
+  if (m0 + 32 * V - 1 > mlast) {                     // warp-uniform: the plane's last warp
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k)
+#pragma unroll 1
+      for (int v = 0; v < V; ++v) {
+        const int m = m0 + lane + 32 * v;
+        const int j = m / g.sx, i = m - j * g.sx;
+        if (m > mlast || i > g.nx - ox) continue;
+        const bool bij = 2 * i + ox == 0 || 2 * i + ox == 2 * g.nx || 2 * j + oy == 0 || 2 * j + oy == 2 * g.ny;
+        row_site<VARNU, T, MODE, OUT, OG, ALL, T0, N0, N1, N2>(g, R, i, j, k, bij, x, b, y, alpha, op, tab);
+      }
+    return;
+  }
+  int iv[V], jv[V];
+  bool okv[V], bijv[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int m = m0 + lane + 32 * v;
+    jv[v] = m / g.sx;
+    iv[v] = m - jv[v] * g.sx;
+    okv[v] = iv[v] <= g.nx - ox;
+    bijv[v] = 2 * iv[v] + ox == 0 || 2 * iv[v] + ox == 2 * g.nx || 2 * jv[v] + oy == 0 || 2 * jv[v] + oy == 2 * g.ny;
+  }
+#pragma unroll 1
+  for (int k = k0; k < k1; ++k) {
+    const int64_t idx = int64_t(m0 + lane) + 1 + g.sx + int64_t(k + 1) * g.sy;
+    const T* xs = x + idx;
+    T a0[V], a1[V], a2[V];
+    seg_sum_v<T0, N0, V>(tab, xs, a0);
+    seg_sum_v<T0 + N0, N1, V>(tab, xs, a1);
+    seg_sum_v<T0 + N0 + N1, N2, V>(tab, xs, a2);
+    const bool bk = 2 * k + oz == 0 || 2 * k + oz == 2 * g.nz;
+    T es = T(1), eis = T(1);
     if (VARNU) {
-      v += T(g.esc[k]) * a1 + T(g.eisc[k]) * a2;
-    } else {
-      v += a1 + a2;
+      es = T(g.esc[k]);
+      eis = T(g.eisc[k]);
     }
-    if (MODE == MODE_SET) *yo = v;
-    else if (MODE == MODE_RES) *yo = b[int64_t(OUT) * g.arr + idx] - v;
-    else *yo += alpha * v;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (!okv[v]) continue;
+      const bool bnd = bijv[v] || bk;
+      const int64_t iy = int64_t(OUT) * g.arr + idx + 32 * v;
+      if (bnd && !ALL) {                             // Dirichlet velocity row
+        if (MODE != MODE_ADD) y[iy] = T(0);
+        continue;
+      }
+      T s2 = a2[v];
+      if (N2 > 0 && bnd) s2 = boundary_seg2_call<T>(g, op, R, iv[v], jv[v], k, x, idx + 32 * v);
+      T val = a0[v];
+      if (VARNU) {
+        val += es * a1[v] + eis * s2;
+      } else {
+        val += a1[v] + s2;
+      }
+      if (MODE == MODE_SET) y[iy] = val;
+      else if (MODE == MODE_RES) y[iy] = b[iy] - val;
+      else y[iy] += alpha * val;
+    }
   }
 }
 
@@ -156,6 +266,21 @@ __device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restric
 // those launch plainly.)
 __device__ __forceinline__ void pdl_wait() { cudaGridDependencySynchronize(); }
 __device__ __forceinline__ void pdl_trigger() { cudaTriggerProgrammaticLaunchCompletion(); }
+
+// FP32 P2-P1 rows: at most 80 registers (three 256-thread blocks per SM);
+// the shorter P1-P1 rows, and FP64 (bound by its arithmetic), uncapped
+template <int DISC, int VARNU, int OP, class T, int MODE, int V>
+__global__ void __launch_bounds__(256, DISC == 2 && sizeof(T) == 4 ? 3 : 1)
+    k_rows_vec(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, T alpha, OpDev op, int kp,
+               const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP>::N> tab) {
+  using S = gen::S<DISC, VARNU, OP>;
+  dispatch<S, 0>(int(blockIdx.z), [&](auto rc) {
+    constexpr int R = decltype(rc)::value;
+    constexpr gen::RowS rw = S::rows[R];
+    eval_row_vec<DISC, VARNU, OP, T, MODE, V, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, x, b, y, alpha,
+                                                                                                op, tab, kp);
+  });
+}
 
 template <int DISC, int VARNU, int OP, class T, int MODE>
 __global__ void __launch_bounds__(256)
@@ -249,9 +374,21 @@ void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, 
   const Tab& tb = *static_cast<const Tab*>(tab);
   const int nt = sh.row_threads, kp = sh.row_kplanes;
   dim3 blk(nt, 1, 1);
+  ++g_launches;
+  if (sh.row_sites == 4 && mode != MODE_ADD) {
+    // warps of 4 x 32 positions over the padded plane up to the last site
+    const int64_t warps = ((int64_t(g.ny) * g.sx + g.nx + 1) + 127) / 128;
+    dim3 grd(unsigned((warps * 32 + nt - 1) / nt), (g.nz + 1 + kp - 1) / kp, S::R);
+    auto go = [&](auto vc) {
+      constexpr int V = decltype(vc)::value;
+      if (mode == MODE_SET) k_rows_vec<DISC, VARNU, OP, T, MODE_SET, V><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+      else k_rows_vec<DISC, VARNU, OP, T, MODE_RES, V><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+    };
+    go(std::integral_constant<int, 4>{});
+    return;
+  }
   const int plane = (g.nx + 1) * (g.ny + 1);
   dim3 grd((plane + nt - 1) / nt, (g.nz + 1 + kp - 1) / kp, S::R);
-  ++g_launches;
   if (mode == MODE_SET) k_rows_fast<DISC, VARNU, OP, T, MODE_SET><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
   else if (mode == MODE_RES) k_rows_fast<DISC, VARNU, OP, T, MODE_RES><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
   else k_rows_fast<DISC, VARNU, OP, T, MODE_ADD><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
@@ -282,6 +419,7 @@ void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double i
   }
 }
 
+#if !defined(HHG_FAST_ONLY) || HHG_FAST_ONLY == 64
 int fast_terms(int disc, int varnu, int op) {
 #define HHG_N(D, V, O) if (disc == D && varnu == V && op == O) return gen::S<D, V, O>::N;
   HHG_N(1, 0, OP_FULL) HHG_N(1, 0, OP_A) HHG_N(1, 0, OP_BT) HHG_N(1, 0, OP_BC)
@@ -291,6 +429,8 @@ int fast_terms(int disc, int varnu, int op) {
 #undef HHG_N
   return -1;
 }
+
+#endif
 
 // run-time dispatch over (disc, varnu, op)
 template <class T>
@@ -316,13 +456,19 @@ void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int co
   else launch_gs_fast<2, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, s);
 }
 
+// HHG_FAST_ONLY = 64 / 32 compiles one precision (the build compiles this
+// file once per precision, in parallel)
+#if !defined(HHG_FAST_ONLY) || HHG_FAST_ONLY == 64
 template void fast_rows<double>(int, int, int, const Geo&, const OpDev&, const void*, int, const double*, const double*,
                                 double*, double, const Shape&, cudaStream_t);
-template void fast_rows<float>(int, int, int, const Geo&, const OpDev&, const void*, int, const float*, const float*,
-                               float*, double, const Shape&, cudaStream_t);
 template void fast_gs<double>(int, int, const Geo&, const void*, int, int, double, double*, const double*, const Shape&,
                               cudaStream_t);
+#endif
+#if !defined(HHG_FAST_ONLY) || HHG_FAST_ONLY == 32
+template void fast_rows<float>(int, int, int, const Geo&, const OpDev&, const void*, int, const float*, const float*,
+                               float*, double, const Shape&, cudaStream_t);
 template void fast_gs<float>(int, int, const Geo&, const void*, int, int, double, float*, const float*, const Shape&,
                              cudaStream_t);
+#endif
 
 }  // namespace hhg

@@ -1377,27 +1377,29 @@ extern "C" int hhg_get_level_smoother(hhg_problem* pb, int level, int prec, int*
 }
 
 extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads, int row_kplanes, int gs_threads,
-                                    int row_tile) {
+                                    int row_tile, int row_sites) {
   HHG_TRY(check_level(pb, level));
   auto ok_threads = [](int t) { return t == 64 || t == 128 || t == 256; };
   if (!ok_threads(row_threads) || !ok_threads(gs_threads) || row_kplanes < 1 || row_kplanes > 64 ||
-      (row_tile != 0 && row_tile != 1))
+      (row_tile != 0 && row_tile != 1) || (row_sites != 1 && row_sites != 4))
     return fail(HHG_EINVAL, "invalid launch shape");
   Shape& sh = pb->L(level).shape;
   sh.row_threads = row_threads;
   sh.row_kplanes = row_kplanes;
   sh.gs_threads = gs_threads;
   sh.row_tile = row_tile;
+  sh.row_sites = row_sites;
   for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
   pb->graphs.clear();
   return HHG_OK;
 }
 
-extern "C" int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape4) {
+extern "C" int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape5) {
   HHG_TRY(check_level(pb, level));
-  if (!shape4) return fail(HHG_EINVAL, "null argument");
+  if (!shape5) return fail(HHG_EINVAL, "null argument");
   const Shape& sh = pb->L(level).shape;
-  shape4[0] = sh.row_threads; shape4[1] = sh.row_kplanes; shape4[2] = sh.gs_threads; shape4[3] = sh.row_tile;
+  shape5[0] = sh.row_threads; shape5[1] = sh.row_kplanes; shape5[2] = sh.gs_threads; shape5[3] = sh.row_tile;
+  shape5[4] = sh.row_sites;
   return HHG_OK;
 }
 
@@ -1660,22 +1662,26 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
     return ms;
   };
   const int disc = pb->desc.disc, varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
-  // row kernels: FULL residual
+  // row kernels: FULL residual, one site per thread or four runs of 32
+  // sites per warp
   const int threads[3] = {64, 128, 256}, planes[5] = {1, 2, 4, 8, 16};
   float best = 1e30f;
   Shape bestS = lv.shape;
-  for (int t : threads)
-    for (int kp : planes) {
-      Shape sh = lv.shape;
-      sh.row_threads = t;
-      sh.row_kplanes = kp;
-      sh.row_tile = 0;
-      const float ms = time_it([&] {
-        fast_rows<T>(disc, varnu, OP_FULL, lv.g, lv.op[OP_FULL], ftab<T>(lv, OP_FULL), MODE_RES, xa, xa, xb, 1.0, sh,
-                     pb->stream);
-      });
-      if (ms < best) { best = ms; bestS.row_threads = t; bestS.row_kplanes = kp; }
-    }
+  for (int v : {1, 4})
+    for (int t : threads)
+      for (int kp : planes) {
+        if (v > 1 && (t == 64 || kp > 4)) continue;
+        Shape sh = lv.shape;
+        sh.row_threads = t;
+        sh.row_kplanes = kp;
+        sh.row_tile = 0;
+        sh.row_sites = v;
+        const float ms = time_it([&] {
+          fast_rows<T>(disc, varnu, OP_FULL, lv.g, lv.op[OP_FULL], ftab<T>(lv, OP_FULL), MODE_RES, xa, xa, xb, 1.0,
+                       sh, pb->stream);
+        });
+        if (ms < best) { best = ms; bestS.row_threads = t; bestS.row_kplanes = kp; bestS.row_sites = v; }
+      }
   // FP32 rows: the shared-memory-tiled kernels against the best plain shape
   if (std::is_same<T, float>::value) {
     Shape sh = bestS;
@@ -1757,11 +1763,12 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       HHG_TRY(tune_smoother<double>(pb, lv, reps, lv.bw64, lv.rhs, lv.tmp64));
     }
     if (shapes_out) {
-      int* o = shapes_out + 6 * (l - pb->desc.coarse_level);
+      int* o = shapes_out + 7 * (l - pb->desc.coarse_level);
       o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
       o[3] = lv.rctas[mixed ? HHG_FP32 : HHG_FP64];
       o[4] = lv.rthreads[mixed ? HHG_FP32 : HHG_FP64];
       o[5] = lv.shape.row_tile;
+      o[6] = lv.shape.row_sites;
     }
   }
   pb->wu_counted = wu;

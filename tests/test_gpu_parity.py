@@ -167,6 +167,45 @@ def test_tiled_rows_match_plain_rows(disc, box, L, nu_a):
     assert rel(out[1][0], pb.to_host(L, y64)) < 1e-5
 
 
+@pytest.mark.parametrize("disc,box,L,nu_a", [("P2P1", (1, 1, 1), 4, 0.0), ("P2P1", (2, 1, 1), 3, 1.1),
+                                              ("P1P1", (1, 2, 1), 4, 0.0), ("P1P1", (1, 1, 2), 3, 1.7)])
+def test_row_sites_match_oracle(disc, box, L, nu_a):
+    """Row kernels with 4 sites per thread (four runs of 32 positions of the
+    padded plane per warp): the FP64 apply against the oracle, and apply,
+    residual and the per-phase smoother's B^T and (B, -C) residual rows
+    against one site per thread in FP64 and FP32.  The boxes give planes of
+    97 to 625 positions: whole runs, a partial last warp, and warps with only
+    the per-site tail."""
+    from paper_2010_13513_gb300 import hhg
+    pb = lib_problem(box, L, disc, lc=1, nu_a=nu_a, solve="mixed")
+    hy = oracle_hierarchy(box, L, disc, lc=1, nu_a=nu_a)
+    lev = hy.lv[L]
+    x, b = random_vector(lev, 31), random_vector(lev, 32)
+    ref = lev.apply(x)
+    prm = hhg.Params.make(ahat="s", xi=1, omega_inv=OMEGA_INV[disc])
+    pb.set_level_smoother(L, 0, prec=hhg.FP64)
+    pb.set_level_smoother(L, 0, prec=hhg.FP32)
+    out = {}
+    for sites, threads, kp in ((1, 128, 2), (4, 64, 4), (4, 256, 1), (4, 128, 3)):
+        pb.set_launch_shape(L, threads, kp, 128, 0, sites)
+        assert pb.launch_shape(L) == (threads, kp, 128, 0, sites)
+        res = []
+        for prec in (hhg.FP64, hhg.FP32):
+            xd, bd = pb.to_device(L, x, prec=prec), pb.to_device(L, b, prec=prec)
+            y, r = pb.new_vector(L, prec), pb.new_vector(L, prec)
+            pb.apply(L, "FULL", xd, y)
+            pb.residual(L, xd, bd, r)
+            pb.smooth(L, prm, 1, xd, bd)
+            res += [pb.to_host(L, v) for v in (y, r, xd)]
+        assert rel(res[0], ref) < 1e-12, (sites, rel(res[0], ref))
+        assert rel(res[3], ref) < 1e-5
+        out[(sites, threads, kp)] = res
+    base = out[(1, 128, 2)]
+    for key, res in out.items():
+        for n, (a, c) in enumerate(zip(res, base)):
+            assert rel(a, c) < (1e-14 if n < 3 else 1e-6), (key, n, rel(a, c))
+
+
 def test_resident_smoother_rejects_what_does_not_fit():
     from paper_2010_13513_gb300 import hhg
     pb = lib_problem((1, 1, 1), 3, "P2P1", lc=1)
@@ -401,9 +440,9 @@ def test_autotune_keeps_results():
     pb.fmg_solve(prm, x1, stats=False)
     shapes = pb.autotune(reps=2)
     assert set(shapes) == {1, 2, 3, 4}
-    for t, kp, gs, rc, rt, tile in shapes.values():
+    for t, kp, gs, rc, rt, tile, sites in shapes.values():
         assert t in (64, 128, 256) and kp in (1, 2, 4, 8, 16) and gs in (64, 128, 256)
-        assert rc in (0, 1, 2, 4, 8, 16) and rt in (256, 512, 1024) and tile in (0, 1)
+        assert rc in (0, 1, 2, 4, 8, 16) and rt in (256, 512, 1024) and tile in (0, 1) and sites in (1, 4)
     x2 = pb.new_vector(4)
     pb.fmg_solve(prm, x2, stats=False)
     torch.cuda.synchronize()
