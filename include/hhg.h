@@ -232,7 +232,8 @@ int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
  * autotuner candidate), and row_sites = 1 or 4 sites per thread of the
  * row kernels (4: each warp evaluates four runs of 32 consecutive
  * positions of the padded (i, j) plane, sharing each term's address
- * between the runs; row_tile = 1 takes precedence for FP32).
+ * between the runs; row_tile = 1 takes precedence for FP32; sets the FP32
+ * and FP64 rows, which hhg_autotune chooses separately).
  * Results agree up to rounding.  Drops cached graphs.
  * hhg_get_launch_shape writes the five values to shape5. */
 int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads, int row_kplanes, int gs_threads, int row_tile,

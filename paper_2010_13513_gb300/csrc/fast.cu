@@ -375,7 +375,7 @@ void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, 
   const int nt = sh.row_threads, kp = sh.row_kplanes;
   dim3 blk(nt, 1, 1);
   ++g_launches;
-  if (sh.row_sites == 4 && mode != MODE_ADD) {
+  if ((sizeof(T) == 8 ? sh.row_sites64 : sh.row_sites) == 4 && mode != MODE_ADD) {
     // warps of 4 x 32 positions over the padded plane up to the last site
     const int64_t warps = ((int64_t(g.ny) * g.sx + g.nx + 1) + 127) / 128;
     dim3 grd(unsigned((warps * 32 + nt - 1) / nt), (g.nz + 1 + kp - 1) / kp, S::R);

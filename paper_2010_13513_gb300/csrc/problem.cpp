@@ -1389,6 +1389,7 @@ extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads,
   sh.gs_threads = gs_threads;
   sh.row_tile = row_tile;
   sh.row_sites = row_sites;
+  sh.row_sites64 = row_sites;
   for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
   pb->graphs.clear();
   return HHG_OK;
@@ -1682,6 +1683,22 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
         });
         if (ms < best) { best = ms; bestS.row_threads = t; bestS.row_kplanes = kp; bestS.row_sites = v; }
       }
+  if (std::is_same<T, double>::value) {
+    bestS.row_sites64 = bestS.row_sites;
+  } else {
+    // the FP64 residual of the mixed solve's refinement: its own choice of
+    // sites per thread (FP64 arithmetic, not the loads, bounds it)
+    float best64 = 1e30f;
+    for (int v : {1, 4}) {
+      Shape sh = bestS;
+      sh.row_sites64 = v;
+      const float ms = time_it([&] {
+        fast_rows<double>(disc, varnu, OP_FULL, lv.g, lv.op[OP_FULL], ftab<double>(lv, OP_FULL), MODE_RES, lv.tmp64,
+                          lv.tmp64, lv.bw64, 1.0, sh, pb->stream);
+      });
+      if (ms < best64) { best64 = ms; bestS.row_sites64 = v; }
+    }
+  }
   // FP32 rows: the shared-memory-tiled kernels against the best plain shape
   if (std::is_same<T, float>::value) {
     Shape sh = bestS;
