@@ -73,13 +73,6 @@ __device__ __forceinline__ T boundary_seg2(const Geo& g, const OpDev& op, int r,
   return a;
 }
 
-// the same as an out-of-line call (rare boundary sites of unrolled code)
-template <class T>
-__device__ __noinline__ T boundary_seg2_call(const Geo& g, const OpDev& op, int r, int i, int j, int k, const T* x,
-                                            int64_t idx) {
-  return boundary_seg2<T>(g, op, r, i, j, k, x, idx);
-}
-
 template <class S, int R, class F>
 __device__ __forceinline__ void dispatch(int r, F&& f) {
   if constexpr (R < S::R) {
@@ -243,7 +236,7 @@ __device__ __forceinline__ void eval_row_vec(const Geo& g, int R, const T* __res
         continue;
       }
       T s2 = a2[v];
-      if (N2 > 0 && bnd) s2 = boundary_seg2_call<T>(g, op, R, iv[v], jv[v], k, x, idx + 32 * v);
+      if (N2 > 0 && bnd) s2 = boundary_seg2<T>(g, op, R, iv[v], jv[v], k, x, idx + 32 * v);
       T val = a0[v];
       if (VARNU) {
         val += es * a1[v] + eis * s2;
