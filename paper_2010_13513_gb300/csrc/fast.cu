@@ -289,32 +289,67 @@ __global__ void __launch_bounds__(256)
 }
 
 // -------------------------------------------------- Gauss-Seidel phase kernel
-// grid: x over the (i', j) plane (i' = i, or i / 4 for a vertex colour), z = k
-template <int DISC, int VARNU, int GRP, class T, int T0, int N1, class Tab>
+// sum over the 2^LP lanes of a group of consecutive lanes (all lanes of the
+// warp take part)
+template <int LP, class T>
+__device__ __forceinline__ T lane_sum(T v) {
+#pragma unroll
+  for (int m = (1 << LP) >> 1; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// grid: x over the (i', j) plane (i' = i, or i / 4 for a vertex colour) times
+// 2^LP lanes per site, z = k.  With LP > 0 the lanes of a site take every
+// 2^LP-th term and add their sums by shuffles: shorter dependent chains and
+// more threads for the small levels, whose phases are latency-bound.
+template <int DISC, int VARNU, int GRP, class T, int LP, int T0, int N1, class Tab>
 __device__ __forceinline__ void gs_site(const Geo& g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag,
                                         int colour, const Tab& tab) {
   constexpr int ox = GRP == 1 || GRP == 4 || GRP == 5 || GRP == 7;
   constexpr int oy = GRP == 2 || GRP == 4 || GRP == 6 || GRP == 7;
   constexpr int oz = GRP == 3 || GRP == 5 || GRP == 6 || GRP == 7;
+  constexpr int P = 1 << LP;
   const int k = blockIdx.z;
   const int w = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1 - ox;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = q / w;
-  int i = q - j * w;
+  const int site = q >> LP, p = q & (P - 1);
+  const int j = site / w;
+  int i = site - j * w;
   if (colour >= 0) i = 4 * i + (((colour - j - k) % 4) + 4) % 4;
   const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
-  if (Px <= 0 || Py <= 0 || Pz <= 0 || Px >= 2 * g.nx || Py >= 2 * g.ny || Pz >= 2 * g.nz) return;
-  const int64_t idx = fsite(g, i, j, k);
+  const bool ok = Px > 0 && Py > 0 && Pz > 0 && Px < 2 * g.nx && Py < 2 * g.ny && Pz < 2 * g.nz;
+  if (LP == 0 && !ok) return;
+  const int64_t idx = ok ? fsite(g, i, j, k) : 0;
   const int64_t cs = int64_t(g.G) * g.arr;
   const T* us = u + idx;
   T a0 = T(0), a1 = T(0), a2 = T(0);
+  if constexpr (LP == 0) {
 #pragma unroll
-  for (int t = 1; t < N1; ++t) {               // the diagonal is the first term
-    const T wt = tab.w[T0 + t];
-    const int o = tab.off[T0 + t];
-    a0 += wt * us[o];
-    a1 += wt * us[o + cs];
-    a2 += wt * us[o + 2 * cs];
+    for (int t = 1; t < N1; ++t) {             // the diagonal is the first term
+      const T wt = tab.w[T0 + t];
+      const int o = tab.off[T0 + t];
+      a0 += wt * us[o];
+      a1 += wt * us[o + cs];
+      a2 += wt * us[o + 2 * cs];
+    }
+  } else {
+    if (ok) {
+#pragma unroll
+      for (int t0 = 1; t0 < N1; t0 += P) {
+        const int t = t0 + p;
+        if (t < N1) {
+          const T wt = tab.w[T0 + t];
+          const int o = tab.off[T0 + t];
+          a0 += wt * us[o];
+          a1 += wt * us[o + cs];
+          a2 += wt * us[o + 2 * cs];
+        }
+      }
+    }
+    a0 = lane_sum<LP>(a0);                     // whole warps: the grid covers whole blocks
+    a1 = lane_sum<LP>(a1);
+    a2 = lane_sum<LP>(a2);
+    if (!ok || p != 0) return;
   }
   T einv = T(1);
   if (VARNU) einv = T(g.eisc[k]);
@@ -324,7 +359,7 @@ __device__ __forceinline__ void gs_site(const Geo& g, T* __restrict__ u, const T
   u[o0 + 2 * cs] = (rhs[o0 + 2 * cs] * einv - a2) * inv_diag;
 }
 
-template <int DISC, int VARNU, int GRP, class T>
+template <int DISC, int VARNU, int GRP, class T, int LP>
 __global__ void __launch_bounds__(256)
     k_gs_fast(Geo g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag, int colour,
               const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP_A>::N> tab) {
@@ -332,7 +367,7 @@ __global__ void __launch_bounds__(256)
   constexpr gen::RowS rw = S::rows[GRP];       // component-0 row of the group; all terms in segment 1
   static_assert(rw.n0 == 0 && rw.n2 == 0, "A rows carry only nu-scaled terms");
   pdl_wait();
-  gs_site<DISC, VARNU, GRP, T, rw.t0, rw.n1>(g, u, rhs, inv_diag, colour, tab);
+  gs_site<DISC, VARNU, GRP, T, LP, rw.t0, rw.n1>(g, u, rhs, inv_diag, colour, tab);
   pdl_trigger();
 }
 
@@ -394,20 +429,31 @@ void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double i
   using Tab = FastTab<T, S::N>;
   const Tab& tb = *static_cast<const Tab*>(tab);
   const int nt = sh.gs_threads;
+  const int lp = sh.gs_lanes == 4 ? 2 : sh.gs_lanes == 2 ? 1 : 0;
   dim3 blk(nt, 1, 1);
   const int ni = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1;
-  const int plane = ni * (g.ny + 1);
-  dim3 grd((plane + nt - 1) / nt, 1, g.nz + 1);
+  const int64_t plane = int64_t(ni) * (g.ny + 1) << lp;
+  dim3 grd(unsigned((plane + nt - 1) / nt), 1, g.nz + 1);
   ++g_launches;
+  auto go = [&](auto gc, auto lc) {
+    constexpr int GRP = decltype(gc)::value, LP = decltype(lc)::value;
+    if constexpr (DISC == 2 || GRP == 0)
+      launch_pdl(k_gs_fast<DISC, VARNU, GRP, T, LP>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb);
+  };
+  auto by_lanes = [&](auto gc) {
+    if (lp == 2) go(gc, std::integral_constant<int, 2>{});
+    else if (lp == 1) go(gc, std::integral_constant<int, 1>{});
+    else go(gc, std::integral_constant<int, 0>{});
+  };
   switch (grp) {
-    case 0: launch_pdl(k_gs_fast<DISC, VARNU, 0, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
-    case 1: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 1, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
-    case 2: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 2, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
-    case 3: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 3, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
-    case 4: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 4, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
-    case 5: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 5, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
-    case 6: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 6, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
-    case 7: if constexpr (DISC == 2) launch_pdl(k_gs_fast<DISC, VARNU, 7, T>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb); break;
+    case 0: by_lanes(std::integral_constant<int, 0>{}); break;
+    case 1: by_lanes(std::integral_constant<int, 1>{}); break;
+    case 2: by_lanes(std::integral_constant<int, 2>{}); break;
+    case 3: by_lanes(std::integral_constant<int, 3>{}); break;
+    case 4: by_lanes(std::integral_constant<int, 4>{}); break;
+    case 5: by_lanes(std::integral_constant<int, 5>{}); break;
+    case 6: by_lanes(std::integral_constant<int, 6>{}); break;
+    case 7: by_lanes(std::integral_constant<int, 7>{}); break;
     default: break;
   }
 }

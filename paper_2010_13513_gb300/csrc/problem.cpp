@@ -1377,11 +1377,12 @@ extern "C" int hhg_get_level_smoother(hhg_problem* pb, int level, int prec, int*
 }
 
 extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads, int row_kplanes, int gs_threads,
-                                    int row_tile, int row_sites) {
+                                    int row_tile, int row_sites, int gs_lanes) {
   HHG_TRY(check_level(pb, level));
   auto ok_threads = [](int t) { return t == 64 || t == 128 || t == 256; };
   if (!ok_threads(row_threads) || !ok_threads(gs_threads) || row_kplanes < 1 || row_kplanes > 64 ||
-      (row_tile != 0 && row_tile != 1) || (row_sites != 1 && row_sites != 4))
+      (row_tile != 0 && row_tile != 1) || (row_sites != 1 && row_sites != 4) ||
+      (gs_lanes != 1 && gs_lanes != 2 && gs_lanes != 4))
     return fail(HHG_EINVAL, "invalid launch shape");
   Shape& sh = pb->L(level).shape;
   sh.row_threads = row_threads;
@@ -1390,17 +1391,18 @@ extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads,
   sh.row_tile = row_tile;
   sh.row_sites = row_sites;
   sh.row_sites64 = row_sites;
+  sh.gs_lanes = gs_lanes;
   for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
   pb->graphs.clear();
   return HHG_OK;
 }
 
-extern "C" int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape5) {
+extern "C" int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape6) {
   HHG_TRY(check_level(pb, level));
-  if (!shape5) return fail(HHG_EINVAL, "null argument");
+  if (!shape6) return fail(HHG_EINVAL, "null argument");
   const Shape& sh = pb->L(level).shape;
-  shape5[0] = sh.row_threads; shape5[1] = sh.row_kplanes; shape5[2] = sh.gs_threads; shape5[3] = sh.row_tile;
-  shape5[4] = sh.row_sites;
+  shape6[0] = sh.row_threads; shape6[1] = sh.row_kplanes; shape6[2] = sh.gs_threads; shape6[3] = sh.row_tile;
+  shape6[4] = sh.row_sites; shape6[5] = sh.gs_lanes;
   return HHG_OK;
 }
 
@@ -1709,17 +1711,19 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
     });
     bestS.row_tile = ms < best ? 1 : 0;
   }
-  // Gauss-Seidel kernels: one forward sweep
+  // Gauss-Seidel kernels: one forward sweep, 1, 2 or 4 lanes per site
   best = 1e30f;
-  for (int t : threads) {
-    Shape sh = bestS;
-    sh.gs_threads = t;
-    const float ms = time_it([&] {
-      for (int c = 0; c < 4; ++c) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), 0, c, 1.0, xb, xa, sh, pb->stream);
-      for (int gg = 1; gg < lv.g.G; ++gg) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), gg, -1, 1.0, xb, xa, sh, pb->stream);
-    });
-    if (ms < best) { best = ms; bestS.gs_threads = t; }
-  }
+  for (int nl : {1, 2, 4})
+    for (int t : threads) {
+      Shape sh = bestS;
+      sh.gs_threads = t;
+      sh.gs_lanes = nl;
+      const float ms = time_it([&] {
+        for (int c = 0; c < 4; ++c) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), 0, c, 1.0, xb, xa, sh, pb->stream);
+        for (int gg = 1; gg < lv.g.G; ++gg) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), gg, -1, 1.0, xb, xa, sh, pb->stream);
+      });
+      if (ms < best) { best = ms; bestS.gs_threads = t; bestS.gs_lanes = nl; }
+    }
   lv.shape = bestS;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1780,12 +1784,13 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       HHG_TRY(tune_smoother<double>(pb, lv, reps, lv.bw64, lv.rhs, lv.tmp64));
     }
     if (shapes_out) {
-      int* o = shapes_out + 7 * (l - pb->desc.coarse_level);
+      int* o = shapes_out + 8 * (l - pb->desc.coarse_level);
       o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
       o[3] = lv.rctas[mixed ? HHG_FP32 : HHG_FP64];
       o[4] = lv.rthreads[mixed ? HHG_FP32 : HHG_FP64];
       o[5] = lv.shape.row_tile;
       o[6] = lv.shape.row_sites;
+      o[7] = lv.shape.gs_lanes;
     }
   }
   pb->wu_counted = wu;

@@ -102,7 +102,7 @@ def load():
         "hhg_set_graph_mode": [P, I],
         "hhg_set_small_level_mode": [P, I],
         "hhg_set_level_smoother": [P, I, I, I, I],
-        "hhg_set_launch_shape": [P, I, I, I, I, I, I],
+        "hhg_set_launch_shape": [P, I, I, I, I, I, I, I],
         "hhg_get_launch_shape": [P, I, C.POINTER(C.c_int)],
         "hhg_get_level_smoother": [P, I, I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "hhg_error_norms": [P, I, VP, DP, DP, DP, DP],
@@ -364,19 +364,19 @@ class Problem:
     def autotune(self, reps=5):
         """Per-level launch choices; returns {level: (row_threads,
         row_kplanes, gs_threads, resident_ctas, resident_threads, row_tile,
-        row_sites)}."""
+        row_sites, gs_lanes)}."""
         n = self.L - self.lc + 1
-        out = (C.c_int * (7 * n))()
+        out = (C.c_int * (8 * n))()
         _check(load().hhg_autotune(self.h, reps, out), "hhg_autotune")
-        return {self.lc + i: tuple(out[7 * i:7 * i + 7]) for i in range(n)}
+        return {self.lc + i: tuple(out[8 * i:8 * i + 8]) for i in range(n)}
 
-    def set_launch_shape(self, level, row_threads, row_kplanes, gs_threads, row_tile=0, row_sites=1):
+    def set_launch_shape(self, level, row_threads, row_kplanes, gs_threads, row_tile=0, row_sites=1, gs_lanes=1):
         _check(load().hhg_set_launch_shape(self.h, level, row_threads, row_kplanes, gs_threads, int(row_tile),
-                                           int(row_sites)), "hhg_set_launch_shape")
+                                           int(row_sites), int(gs_lanes)), "hhg_set_launch_shape")
 
     def launch_shape(self, level):
-        """(row_threads, row_kplanes, gs_threads, row_tile, row_sites) of a level."""
-        out = (C.c_int * 5)()
+        """(row_threads, row_kplanes, gs_threads, row_tile, row_sites, gs_lanes) of a level."""
+        out = (C.c_int * 6)()
         _check(load().hhg_get_launch_shape(self.h, level, out), "hhg_get_launch_shape")
         return tuple(out)
 

@@ -89,6 +89,37 @@ def test_uzawa_parity(disc, ahat, xi, nu_a):
     assert rel(pb.to_host(L, xd), ref) < 1e-12
 
 
+@pytest.mark.parametrize("disc,box,L,nu_a,ahat,xi", [("P2P1", (1, 1, 1), 3, 0.0, "f", 2),
+                                                      ("P2P1", (2, 1, 1), 3, 1.1, "s", 1),
+                                                      ("P1P1", (1, 2, 1), 4, 0.0, "s", 1)])
+def test_gs_lanes_match_oracle(disc, box, L, nu_a, ahat, xi):
+    """Per-phase Gauss-Seidel launches with 1, 2 and 4 lanes per site (terms
+    split among the lanes, sums added by shuffles): two Uzawa iterations
+    against the oracle in FP64, and FP32 against FP64 one lane per site.
+    Vertex-colour planes of 27 to 153 sites leave partly filled warps."""
+    from oracle.stokes import Params
+    from paper_2010_13513_gb300 import hhg
+    pb = lib_problem(box, L, disc, lc=1, nu_a=nu_a, solve="mixed")
+    hy = oracle_hierarchy(box, L, disc, lc=1, nu_a=nu_a)
+    lev = hy.lv[L]
+    x, b = random_vector(lev, 41), random_vector(lev, 42)
+    om = OMEGA_INV[disc]
+    lprm = hhg.Params.make(ahat=ahat, xi=xi, omega_inv=om)
+    prm = Params(ahat=ahat, xi=xi, omega_inv=om)
+    ref = lev.uzawa(lev.uzawa(x, b, prm), b, prm)
+    pb.set_level_smoother(L, 0, prec=hhg.FP64)
+    pb.set_level_smoother(L, 0, prec=hhg.FP32)
+    for lanes, gs_threads in ((1, 128), (2, 64), (2, 256), (4, 64), (4, 128)):
+        pb.set_launch_shape(L, 128, 2, gs_threads, 0, 1, lanes)
+        assert pb.launch_shape(L)[5] == lanes
+        xd = pb.to_device(L, x)
+        pb.smooth(L, lprm, 2, xd, pb.to_device(L, b))
+        assert rel(pb.to_host(L, xd), ref) < 1e-12, (lanes, gs_threads)
+        x32 = pb.to_device(L, x, prec=hhg.FP32)
+        pb.smooth(L, lprm, 2, x32, pb.to_device(L, b, prec=hhg.FP32))
+        assert rel(pb.to_host(L, x32), ref) < 1e-4, (lanes, gs_threads)
+
+
 @pytest.mark.parametrize("disc,L,nu_a,ahat,xi", [("P2P1", 2, 0.0, "s", 2), ("P2P1", 2, 1.3, "f", 1),
                                                   ("P1P1", 3, 0.0, "s", 1), ("P1P1", 3, 0.8, "f", 2)])
 def test_resident_smoother_every_cta_count(disc, L, nu_a, ahat, xi):
@@ -188,7 +219,7 @@ def test_row_sites_match_oracle(disc, box, L, nu_a):
     out = {}
     for sites, threads, kp in ((1, 128, 2), (4, 64, 4), (4, 256, 1), (4, 128, 3)):
         pb.set_launch_shape(L, threads, kp, 128, 0, sites)
-        assert pb.launch_shape(L) == (threads, kp, 128, 0, sites)
+        assert pb.launch_shape(L) == (threads, kp, 128, 0, sites, 1)
         res = []
         for prec in (hhg.FP64, hhg.FP32):
             xd, bd = pb.to_device(L, x, prec=prec), pb.to_device(L, b, prec=prec)
@@ -440,9 +471,10 @@ def test_autotune_keeps_results():
     pb.fmg_solve(prm, x1, stats=False)
     shapes = pb.autotune(reps=2)
     assert set(shapes) == {1, 2, 3, 4}
-    for t, kp, gs, rc, rt, tile, sites in shapes.values():
+    for t, kp, gs, rc, rt, tile, sites, lanes in shapes.values():
         assert t in (64, 128, 256) and kp in (1, 2, 4, 8, 16) and gs in (64, 128, 256)
         assert rc in (0, 1, 2, 4, 8, 16) and rt in (256, 512, 1024) and tile in (0, 1) and sites in (1, 4)
+        assert lanes in (1, 2, 4)
     x2 = pb.new_vector(4)
     pb.fmg_solve(prm, x2, stats=False)
     torch.cuda.synchronize()
