@@ -42,6 +42,7 @@ from dataclasses import dataclass
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from . import fe
 from .mesh import Lattice, PERMS
@@ -132,6 +133,8 @@ class StokesLevel:
         self.vint = ~bnd
         self.Adiag = self.A.diagonal()
         self.phases = self._gs_phases()
+        self.gs_order = "multicolour"
+        self._lex = None
 
     # ---------------------------------------------------------------- layout
     @property
@@ -172,6 +175,31 @@ class StokesLevel:
             phases.append(np.nonzero(self.vint & g)[0])
         return phases
 
+    def set_gs_order(self, order):
+        """'multicolour' (the order above, shared with the GPU) or 'paper':
+        the order of the paper's Gauss-Seidel kernels (Sec. 5.2: one kernel
+        per DoF group) -- the interior vertex DoFs one after another in
+        lexicographic order (i fastest, then j, then k), then (P2) each edge
+        group at once as above.  Backward = exact reverse."""
+        if order not in ("multicolour", "paper"):
+            raise ValueError(order)
+        self.gs_order = order
+        if order == "paper" and self._lex is None:
+            V = np.sort(np.concatenate(self.phases[:4]))        # interior vertex DoFs, natural order
+            AVV = self.A[V][:, V].tocsr()
+            self._lex = (V, self.A[V].tocsr(), sp.tril(AVV, format="csr"), sp.triu(AVV, format="csr"))
+
+    def _gs_vertices_lex(self, u, rhs, backward):
+        """The vertex group, DoF by DoF in lexicographic order (reverse order
+        for backward): u_V solves (D + L) u_V = rhs_V - (A u)_V + (D + L) u_V
+        with the other DoFs fixed, L (or U) the strictly lower (upper)
+        triangle of A restricted to V in that order -- each DoF's update sees
+        the new values of the DoFs before it."""
+        V, AV, low, up = self._lex
+        T = up if backward else low
+        r = rhs[V] - AV @ u + T @ u[V]
+        u[V] = spla.spsolve_triangular(T, r, lower=not backward)
+
     # ------------------------------------------------------------ operators
     def apply(self, x):
         """y = calA x (Eq. stokes-discrete); Dirichlet velocity rows are 0."""
@@ -205,9 +233,20 @@ class StokesLevel:
 
     # ------------------------------------------------------------ smoother
     def gs_sweep(self, u, rhs, backward=False):
-        """One multicolour Gauss-Seidel sweep on A u = rhs (in place)."""
-        order = self.phases[::-1] if backward else self.phases
+        """One Gauss-Seidel sweep on A u = rhs (in place), in the level's
+        order (multicolour, or the paper's: see set_gs_order)."""
         A, d = self.A, self.Adiag
+        if self.gs_order == "paper":
+            edges = self.phases[4:]
+            if not backward:
+                self._gs_vertices_lex(u, rhs, False)
+            for S in (edges[::-1] if backward else edges):
+                if S.size:
+                    u[S] = (rhs[S] - A[S] @ u + d[S] * u[S]) / d[S]
+            if backward:
+                self._gs_vertices_lex(u, rhs, True)
+            return
+        order = self.phases[::-1] if backward else self.phases
         for S in order:
             if S.size == 0:
                 continue
@@ -322,9 +361,12 @@ def prolongation_matrix(fine: Lattice, coarse: Lattice, order):
 # the hierarchy, coarse solve, V-cycle and FMG (Algorithm 1)
 # =====================================================================
 class StokesHierarchy:
-    def __init__(self, box, H, L, disc, coarse_level=0, nu_a=0.0, pspg_rhs=True, workload=None):
+    def __init__(self, box, H, L, disc, coarse_level=0, nu_a=0.0, pspg_rhs=True, workload=None,
+                 gs_order="multicolour"):
         self.box, self.H, self.L, self.disc, self.lc = tuple(box), H, L, disc, coarse_level
         self.lv = {l: StokesLevel(box, H, l, disc, nu_a, pspg_rhs) for l in range(coarse_level, L + 1)}
+        for lev in self.lv.values():
+            lev.set_gs_order(gs_order)
         self.order_v = self.lv[L].order_v
         self.Pv, self.Pp = {}, {}
         for l in range(coarse_level + 1, L + 1):

@@ -126,7 +126,7 @@ constexpr int kPhaseLanes = 256;
 template <class T>
 __global__ void __launch_bounds__(kResidentThreads)
     k_uzawa_resident(Geo g, int arr_l, int arr_t, T* xg, const T* __restrict__ b, const double* __restrict__ inv_ml,
-                     SmallArgs a, OpDev bc_op, const __grid_constant__ ResTabs<T> tb) {
+                     const __grid_constant__ SmallArgs a, OpDev bc_op, const __grid_constant__ ResTabs<T> tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PhaseDesc sd[13];                     // GS phases 0..nph-1, then B^T, then (B, -C)
   __shared__ T sdiag[8];

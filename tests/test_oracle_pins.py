@@ -515,3 +515,42 @@ def test_mlp_gradients_match_finite_differences():
             flat[idx] = old
             fd = (lp - lm) / (2 * eps)
             assert abs(fd - g[pi].reshape(-1)[idx]) <= 1e-6 * max(1.0, abs(fd)), (pi, idx)
+
+
+@pytest.mark.parametrize("disc,L", [("P1P1", 2), ("P2P1", 1), ("P2P1", 2)])
+def test_paper_gs_order_is_textbook_gauss_seidel(disc, L):
+    """The oracle's 'paper' Gauss-Seidel order (Sec. 5.2: one kernel per DoF
+    group, the vertex DoFs in lexicographic order, then each edge group)
+    equals the textbook loop u_i <- (f_i - sum_{j != i} a_ij u_j) / a_ii over
+    the interior DoFs one at a time in that order, forward and backward --
+    which also checks that an edge group can be updated at once."""
+    from oracle.stokes import StokesLevel
+    lev = StokesLevel((1, 1, 1), 1.0, L, disc)
+    lev.set_gs_order("paper")
+    rng = np.random.default_rng(11)
+    u0 = np.where(lev.vint, rng.standard_normal(lev.nv), 0.0)
+    rhs = rng.standard_normal(lev.nv)
+    A = lev.A.toarray()
+    if disc == "P1P1":
+        vert = np.ones(lev.nv, dtype=bool)
+    else:
+        vert = np.all(lev.lat.p2_int_coords() % 2 == 0, axis=1)
+    order = [int(i) for i in np.nonzero(lev.vint & vert)[0]]          # ascending node number = lexicographic
+    for S in lev.phases[4:]:
+        order += [int(i) for i in S]
+    want = {}
+    for backward in (False, True):
+        w = u0.copy()
+        for i in (order[::-1] if backward else order):
+            w[i] = (rhs[i] - A[i] @ w + A[i, i] * w[i]) / A[i, i]
+        got = u0.copy()
+        lev.gs_sweep(got, rhs, backward=backward)
+        assert np.abs(got - w).max() <= 1e-12 * np.abs(w).max(), backward
+        want[backward] = w
+    # with more than one interior vertex the multicolour order is a
+    # different sweep (same fixed point)
+    mc = u0.copy()
+    lev.set_gs_order("multicolour")
+    lev.gs_sweep(mc, rhs)
+    if np.count_nonzero(lev.vint & vert) > 1:
+        assert np.abs(mc - want[False]).max() > 1e-6
