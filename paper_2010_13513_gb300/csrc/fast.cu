@@ -26,8 +26,6 @@
 namespace hhg {
 namespace {
 
-__constant__ int f_goff[8][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
-
 __device__ __forceinline__ int64_t fsite(const Geo& g, int i, int j, int k) {
   return int64_t(i + 1) + int64_t(j + 1) * g.sx + int64_t(k + 1) * g.sy;
 }
