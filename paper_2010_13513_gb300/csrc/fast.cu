@@ -427,7 +427,8 @@ void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double i
   using Tab = FastTab<T, S::N>;
   const Tab& tb = *static_cast<const Tab*>(tab);
   const int nt = sh.gs_threads;
-  const int lp = sh.gs_lanes == 4 ? 2 : sh.gs_lanes == 2 ? 1 : 0;
+  const int nl = grp == 0 ? sh.gs_lanes0 : sh.gs_lanes;
+  const int lp = nl == 4 ? 2 : nl == 2 ? 1 : 0;
   dim3 blk(nt, 1, 1);
   const int ni = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1;
   const int64_t plane = int64_t(ni) * (g.ny + 1) << lp;

@@ -21,7 +21,8 @@ struct Shape {
   int row_threads = 128;   // threads per block of the row kernels (64 / 128 / 256)
   int row_kplanes = 2;     // k planes per thread of the row kernels
   int gs_threads = 128;    // threads per block of the Gauss-Seidel kernels
-  int gs_lanes = 1;        // lanes sharing the terms of one Gauss-Seidel site (1, 2, 4)
+  int gs_lanes = 1;        // lanes sharing the terms of one Gauss-Seidel site (1, 2, 4): edge groups
+  int gs_lanes0 = 1;       // the same for the vertex group (its colour phases)
   int row_tile = 0;        // FP32 rows by the shared-memory-tiled kernels (tile.cu; autotuner candidate)
   int row_sites = 1;       // sites per thread of the FP32 row kernels (1, or 4: four runs of 32 positions per warp)
   int row_sites64 = 1;     // the same for the FP64 row kernels

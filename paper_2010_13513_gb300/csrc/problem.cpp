@@ -1392,6 +1392,7 @@ extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads,
   sh.row_sites = row_sites;
   sh.row_sites64 = row_sites;
   sh.gs_lanes = gs_lanes;
+  sh.gs_lanes0 = gs_lanes;
   for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
   pb->graphs.clear();
   return HHG_OK;
@@ -1711,19 +1712,37 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
     });
     bestS.row_tile = ms < best ? 1 : 0;
   }
-  // Gauss-Seidel kernels: one forward sweep, 1, 2 or 4 lanes per site
+  // Gauss-Seidel kernels: one forward sweep, 1, 2 or 4 lanes per site; the
+  // lanes of the vertex colours and of the edge groups are then chosen apart
   best = 1e30f;
+  auto sweep = [&](const Shape& sh, bool vertex, bool edges) {
+    if (vertex)
+      for (int c = 0; c < 4; ++c) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), 0, c, 1.0, xb, xa, sh, pb->stream);
+    if (edges)
+      for (int gg = 1; gg < lv.g.G; ++gg) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), gg, -1, 1.0, xb, xa, sh, pb->stream);
+  };
   for (int nl : {1, 2, 4})
     for (int t : threads) {
       Shape sh = bestS;
       sh.gs_threads = t;
-      sh.gs_lanes = nl;
-      const float ms = time_it([&] {
-        for (int c = 0; c < 4; ++c) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), 0, c, 1.0, xb, xa, sh, pb->stream);
-        for (int gg = 1; gg < lv.g.G; ++gg) fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), gg, -1, 1.0, xb, xa, sh, pb->stream);
-      });
-      if (ms < best) { best = ms; bestS.gs_threads = t; bestS.gs_lanes = nl; }
+      sh.gs_lanes = sh.gs_lanes0 = nl;
+      const float ms = time_it([&] { sweep(sh, true, true); });
+      if (ms < best) { best = ms; bestS.gs_threads = t; bestS.gs_lanes = bestS.gs_lanes0 = nl; }
     }
+  if (lv.g.G > 1) {
+    float bv = 1e30f, be = 1e30f;
+    int lv0 = bestS.gs_lanes0, le = bestS.gs_lanes;
+    for (int nl : {1, 2, 4}) {
+      Shape sh = bestS;
+      sh.gs_lanes = sh.gs_lanes0 = nl;
+      const float mv = time_it([&] { sweep(sh, true, false); });
+      const float me = time_it([&] { sweep(sh, false, true); });
+      if (mv < bv) { bv = mv; lv0 = nl; }
+      if (me < be) { be = me; le = nl; }
+    }
+    bestS.gs_lanes0 = lv0;
+    bestS.gs_lanes = le;
+  }
   lv.shape = bestS;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1784,13 +1803,14 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       HHG_TRY(tune_smoother<double>(pb, lv, reps, lv.bw64, lv.rhs, lv.tmp64));
     }
     if (shapes_out) {
-      int* o = shapes_out + 8 * (l - pb->desc.coarse_level);
+      int* o = shapes_out + 9 * (l - pb->desc.coarse_level);
       o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
       o[3] = lv.rctas[mixed ? HHG_FP32 : HHG_FP64];
       o[4] = lv.rthreads[mixed ? HHG_FP32 : HHG_FP64];
       o[5] = lv.shape.row_tile;
       o[6] = lv.shape.row_sites;
       o[7] = lv.shape.gs_lanes;
+      o[8] = lv.shape.gs_lanes0;
     }
   }
   pb->wu_counted = wu;
