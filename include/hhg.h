@@ -216,12 +216,14 @@ int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats
  * hhg_set_level_smoother): every candidate is timed `reps` times with CUDA
  * events on the problem's stream in the precision of the V-cycles, the
  * fastest is kept.  Uses only the library's scratch vectors; cached graphs
- * are dropped.  shapes_out (optional) receives 9 ints per level (coarse ..
+ * are dropped.  shapes_out (optional) receives 15 ints per level (coarse ..
  * L): row threads, row k planes, Gauss-Seidel threads, resident CTAs,
  * resident threads per CTA, whether the FP32 stencil rows use the
- * shared-memory-tiled kernels, the row kernels' sites per thread, and the
+ * shared-memory-tiled kernels, the row kernels' sites per thread, the
  * lanes per Gauss-Seidel site of the edge groups and of the vertex colours
- * (tuned apart).  Synchronises. */
+ * (tuned apart), and the threads, k planes and sites per thread of the
+ * smoother's B^T rows and of its (B, -C) rows (tuned apart from the full
+ * operator's).  Synchronises. */
 int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
 /* Not in the paper (GPU launch choices): the launch shape of the stencil
  * kernels of one level -- threads per block of the row kernels (64/128/256),
@@ -237,7 +239,8 @@ int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
  * and FP64 rows, which hhg_autotune chooses separately), and gs_lanes = 1, 2
  * or 4 lanes per Gauss-Seidel site (the lanes take every gs_lanes-th term
  * of the site's rows and add their sums by shuffles; sets the vertex colours
- * and the edge groups, which hhg_autotune chooses apart).  Results agree up to
+ * and the edge groups, which hhg_autotune chooses apart; the B^T and
+ * (B, -C) rows take this shape too until hhg_autotune gives them their own).  Results agree up to
  * rounding.  Drops cached graphs.  hhg_get_launch_shape writes the six
  * values to shape6. */
 int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads, int row_kplanes, int gs_threads, int row_tile,

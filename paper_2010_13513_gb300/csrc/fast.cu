@@ -398,10 +398,15 @@ void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, 
   using S = gen::S<DISC, VARNU, OP>;
   using Tab = FastTab<T, S::N>;
   const Tab& tb = *static_cast<const Tab*>(tab);
-  const int nt = sh.row_threads, kp = sh.row_kplanes;
+  int nt = sh.row_threads, kp = sh.row_kplanes, sites = sizeof(T) == 8 ? sh.row_sites64 : sh.row_sites;
+  if (OP == OP_BT && sh.bt_threads) {
+    nt = sh.bt_threads; kp = sh.bt_kplanes; sites = sh.bt_sites;
+  } else if (OP == OP_BC && sh.bc_threads) {
+    nt = sh.bc_threads; kp = sh.bc_kplanes; sites = sh.bc_sites;
+  }
   dim3 blk(nt, 1, 1);
   ++g_launches;
-  if ((sizeof(T) == 8 ? sh.row_sites64 : sh.row_sites) == 4 && mode != MODE_ADD) {
+  if (sites == 4 && mode != MODE_ADD) {
     // warps of 4 x 32 positions over the padded plane up to the last site
     const int64_t warps = ((int64_t(g.ny) * g.sx + g.nx + 1) + 127) / 128;
     dim3 grd(unsigned((warps * 32 + nt - 1) / nt), (g.nz + 1 + kp - 1) / kp, S::R);

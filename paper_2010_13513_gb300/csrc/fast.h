@@ -23,6 +23,10 @@ struct Shape {
   int gs_threads = 128;    // threads per block of the Gauss-Seidel kernels
   int gs_lanes = 1;        // lanes sharing the terms of one Gauss-Seidel site (1, 2, 4): edge groups
   int gs_lanes0 = 1;       // the same for the vertex group (its colour phases)
+  // own row shapes (threads, k planes, sites per thread) of the B^T and the
+  // (B, -C) rows in the V-cycle precision; 0 = the full operator's
+  int bt_threads = 0, bt_kplanes = 0, bt_sites = 0;
+  int bc_threads = 0, bc_kplanes = 0, bc_sites = 0;
   int row_tile = 0;        // FP32 rows by the shared-memory-tiled kernels (tile.cu; autotuner candidate)
   int row_sites = 1;       // sites per thread of the FP32 row kernels (1, or 4: four runs of 32 positions per warp)
   int row_sites64 = 1;     // the same for the FP64 row kernels

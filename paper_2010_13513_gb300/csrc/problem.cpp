@@ -1393,6 +1393,8 @@ extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads,
   sh.row_sites64 = row_sites;
   sh.gs_lanes = gs_lanes;
   sh.gs_lanes0 = gs_lanes;
+  sh.bt_threads = sh.bt_kplanes = sh.bt_sites = 0;
+  sh.bc_threads = sh.bc_kplanes = sh.bc_sites = 0;
   for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
   pb->graphs.clear();
   return HHG_OK;
@@ -1702,6 +1704,27 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
       if (ms < best64) { best64 = ms; bestS.row_sites64 = v; }
     }
   }
+  // the smoother's B^T and (B, -C) residual rows: their own shapes (24 short
+  // rows on one input array; one long row on all of them)
+  for (int op : {OP_BT, OP_BC}) {
+    float bo = 1e30f;
+    int bt = 0, bk = 0, bs = 0;
+    for (int v : {1, 4})
+      for (int t : threads)
+        for (int kp : {1, 2, 4}) {
+          if (v > 1 && t == 64) continue;
+          Shape sh = bestS;
+          sh.row_tile = 0;
+          if (op == OP_BT) { sh.bt_threads = t; sh.bt_kplanes = kp; sh.bt_sites = v; }
+          else { sh.bc_threads = t; sh.bc_kplanes = kp; sh.bc_sites = v; }
+          const float ms = time_it([&] {
+            fast_rows<T>(disc, varnu, op, lv.g, lv.op[op], ftab<T>(lv, op), MODE_RES, xa, xa, xb, 1.0, sh, pb->stream);
+          });
+          if (ms < bo) { bo = ms; bt = t; bk = kp; bs = v; }
+        }
+    if (op == OP_BT) { bestS.bt_threads = bt; bestS.bt_kplanes = bk; bestS.bt_sites = bs; }
+    else { bestS.bc_threads = bt; bestS.bc_kplanes = bk; bestS.bc_sites = bs; }
+  }
   // FP32 rows: the shared-memory-tiled kernels against the best plain shape
   if (std::is_same<T, float>::value) {
     Shape sh = bestS;
@@ -1803,7 +1826,7 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       HHG_TRY(tune_smoother<double>(pb, lv, reps, lv.bw64, lv.rhs, lv.tmp64));
     }
     if (shapes_out) {
-      int* o = shapes_out + 9 * (l - pb->desc.coarse_level);
+      int* o = shapes_out + 15 * (l - pb->desc.coarse_level);
       o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
       o[3] = lv.rctas[mixed ? HHG_FP32 : HHG_FP64];
       o[4] = lv.rthreads[mixed ? HHG_FP32 : HHG_FP64];
@@ -1811,6 +1834,8 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       o[6] = lv.shape.row_sites;
       o[7] = lv.shape.gs_lanes;
       o[8] = lv.shape.gs_lanes0;
+      o[9] = lv.shape.bt_threads; o[10] = lv.shape.bt_kplanes; o[11] = lv.shape.bt_sites;
+      o[12] = lv.shape.bc_threads; o[13] = lv.shape.bc_kplanes; o[14] = lv.shape.bc_sites;
     }
   }
   pb->wu_counted = wu;
