@@ -216,14 +216,15 @@ int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats
  * hhg_set_level_smoother): every candidate is timed `reps` times with CUDA
  * events on the problem's stream in the precision of the V-cycles, the
  * fastest is kept.  Uses only the library's scratch vectors; cached graphs
- * are dropped.  shapes_out (optional) receives 15 ints per level (coarse ..
- * L): row threads, row k planes, Gauss-Seidel threads, resident CTAs,
+ * are dropped.  shapes_out (optional) receives 16 ints per level (coarse ..
+ * L): row threads, row k planes, Gauss-Seidel threads (edge groups), resident CTAs,
  * resident threads per CTA, whether the FP32 stencil rows use the
  * shared-memory-tiled kernels, the row kernels' sites per thread, the
  * lanes per Gauss-Seidel site of the edge groups and of the vertex colours
  * (tuned apart), and the threads, k planes and sites per thread of the
  * smoother's B^T rows and of its (B, -C) rows (tuned apart from the full
- * operator's).  Synchronises. */
+ * operator's), and the Gauss-Seidel threads of the vertex colours.
+ * Synchronises. */
 int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
 /* Not in the paper (GPU launch choices): the launch shape of the stencil
  * kernels of one level -- threads per block of the row kernels (64/128/256),

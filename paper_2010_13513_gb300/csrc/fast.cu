@@ -431,7 +431,7 @@ void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double i
   using S = gen::S<DISC, VARNU, OP_A>;
   using Tab = FastTab<T, S::N>;
   const Tab& tb = *static_cast<const Tab*>(tab);
-  const int nt = sh.gs_threads;
+  const int nt = grp == 0 && sh.gs_threads0 ? sh.gs_threads0 : sh.gs_threads;
   const int nl = grp == 0 ? sh.gs_lanes0 : sh.gs_lanes;
   const int lp = nl == 4 ? 2 : nl == 2 ? 1 : 0;
   dim3 blk(nt, 1, 1);

@@ -23,6 +23,7 @@ struct Shape {
   int gs_threads = 128;    // threads per block of the Gauss-Seidel kernels
   int gs_lanes = 1;        // lanes sharing the terms of one Gauss-Seidel site (1, 2, 4): edge groups
   int gs_lanes0 = 1;       // the same for the vertex group (its colour phases)
+  int gs_threads0 = 0;     // threads per block of the vertex colour phases (0 = gs_threads)
   // own row shapes (threads, k planes, sites per thread) of the B^T and the
   // (B, -C) rows in the V-cycle precision; 0 = the full operator's
   int bt_threads = 0, bt_kplanes = 0, bt_sites = 0;

@@ -1393,6 +1393,7 @@ extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads,
   sh.row_sites64 = row_sites;
   sh.gs_lanes = gs_lanes;
   sh.gs_lanes0 = gs_lanes;
+  sh.gs_threads0 = 0;
   sh.bt_threads = sh.bt_kplanes = sh.bt_sites = 0;
   sh.bc_threads = sh.bc_kplanes = sh.bc_sites = 0;
   for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -1754,17 +1755,22 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
     }
   if (lv.g.G > 1) {
     float bv = 1e30f, be = 1e30f;
-    int lv0 = bestS.gs_lanes0, le = bestS.gs_lanes;
-    for (int nl : {1, 2, 4}) {
-      Shape sh = bestS;
-      sh.gs_lanes = sh.gs_lanes0 = nl;
-      const float mv = time_it([&] { sweep(sh, true, false); });
-      const float me = time_it([&] { sweep(sh, false, true); });
-      if (mv < bv) { bv = mv; lv0 = nl; }
-      if (me < be) { be = me; le = nl; }
-    }
+    int lv0 = bestS.gs_lanes0, tv0 = bestS.gs_threads, le = bestS.gs_lanes, te = bestS.gs_threads;
+    for (int nl : {1, 2, 4})
+      for (int t : threads) {
+        Shape sh = bestS;
+        sh.gs_lanes = sh.gs_lanes0 = nl;
+        sh.gs_threads = t;
+        sh.gs_threads0 = 0;
+        const float mv = time_it([&] { sweep(sh, true, false); });
+        const float me = time_it([&] { sweep(sh, false, true); });
+        if (mv < bv) { bv = mv; lv0 = nl; tv0 = t; }
+        if (me < be) { be = me; le = nl; te = t; }
+      }
     bestS.gs_lanes0 = lv0;
+    bestS.gs_threads0 = tv0;
     bestS.gs_lanes = le;
+    bestS.gs_threads = te;
   }
   lv.shape = bestS;
   cudaEventDestroy(e0);
@@ -1826,7 +1832,7 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       HHG_TRY(tune_smoother<double>(pb, lv, reps, lv.bw64, lv.rhs, lv.tmp64));
     }
     if (shapes_out) {
-      int* o = shapes_out + 15 * (l - pb->desc.coarse_level);
+      int* o = shapes_out + 16 * (l - pb->desc.coarse_level);
       o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
       o[3] = lv.rctas[mixed ? HHG_FP32 : HHG_FP64];
       o[4] = lv.rthreads[mixed ? HHG_FP32 : HHG_FP64];
@@ -1836,6 +1842,7 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       o[8] = lv.shape.gs_lanes0;
       o[9] = lv.shape.bt_threads; o[10] = lv.shape.bt_kplanes; o[11] = lv.shape.bt_sites;
       o[12] = lv.shape.bc_threads; o[13] = lv.shape.bc_kplanes; o[14] = lv.shape.bc_sites;
+      o[15] = lv.shape.gs_threads0 ? lv.shape.gs_threads0 : lv.shape.gs_threads;
     }
   }
   pb->wu_counted = wu;

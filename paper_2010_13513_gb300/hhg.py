@@ -365,11 +365,11 @@ class Problem:
         """Per-level launch choices; returns {level: (row_threads,
         row_kplanes, gs_threads, resident_ctas, resident_threads, row_tile,
         row_sites, gs_lanes, gs_lanes_vertex, bt_threads, bt_kplanes, bt_sites,
-        bc_threads, bc_kplanes, bc_sites)}."""
+        bc_threads, bc_kplanes, bc_sites, gs_threads_vertex)}."""
         n = self.L - self.lc + 1
-        out = (C.c_int * (15 * n))()
+        out = (C.c_int * (16 * n))()
         _check(load().hhg_autotune(self.h, reps, out), "hhg_autotune")
-        return {self.lc + i: tuple(out[15 * i:15 * i + 15]) for i in range(n)}
+        return {self.lc + i: tuple(out[16 * i:16 * i + 16]) for i in range(n)}
 
     def set_launch_shape(self, level, row_threads, row_kplanes, gs_threads, row_tile=0, row_sites=1, gs_lanes=1):
         _check(load().hhg_set_launch_shape(self.h, level, row_threads, row_kplanes, gs_threads, int(row_tile),

@@ -471,12 +471,12 @@ def test_autotune_keeps_results():
     pb.fmg_solve(prm, x1, stats=False)
     shapes = pb.autotune(reps=2)
     assert set(shapes) == {1, 2, 3, 4}
-    for t, kp, gs, rc, rt, tile, sites, lanes, lanes_v, btt, btk, bts, bct, bck, bcs in shapes.values():
+    for t, kp, gs, rc, rt, tile, sites, lanes, lanes_v, btt, btk, bts, bct, bck, bcs, gsv in shapes.values():
         assert t in (64, 128, 256) and kp in (1, 2, 4, 8, 16) and gs in (64, 128, 256)
         assert rc in (0, 1, 2, 4, 8, 16) and rt in (256, 512, 1024) and tile in (0, 1) and sites in (1, 4)
         assert lanes in (1, 2, 4) and lanes_v in (1, 2, 4)
         assert btt in (64, 128, 256) and bct in (64, 128, 256) and btk in (1, 2, 4) and bck in (1, 2, 4)
-        assert bts in (1, 4) and bcs in (1, 4)
+        assert bts in (1, 4) and bcs in (1, 4) and gsv in (64, 128, 256)
     x2 = pb.new_vector(4)
     pb.fmg_solve(prm, x2, stats=False)
     torch.cuda.synchronize()
