@@ -41,7 +41,7 @@ __constant__ int c_goff[8][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1,
 // ------------------------------------------------------------------ apply
 template <class T, int MODE>
 __global__ void __launch_bounds__(128) k_apply(Geo g, OpDev op, const T* __restrict__ x, const T* __restrict__ b,
-                                               T* __restrict__ y, T alpha, int shell) {
+                                               T* __restrict__ y, T alpha) {
   const int nzp = g.nz + 1;
   const int r = blockIdx.z / nzp;
   const int k = blockIdx.z - r * nzp;
@@ -50,12 +50,6 @@ __global__ void __launch_bounds__(128) k_apply(Geo g, OpDev op, const T* __restr
   const DRow row = op.rows[r];
   const int ox = c_goff[row.og][0], oy = c_goff[row.og][1], oz = c_goff[row.og][2];
   if (!dof_valid(g, i, j, k, ox, oy, oz)) return;
-  if (MODE == MODE_ADD && shell) {
-    // doubled-lattice coordinates: a row whose stencil stays strictly inside
-    // reads only interior nodes, where x is zero
-    const int Px = 2 * i + ox, Py = 2 * j + oy, Pz = 2 * k + oz;
-    if (Px > 2 && Px < 2 * g.nx - 2 && Py > 2 && Py < 2 * g.ny - 2 && Pz > 2 && Pz < 2 * g.nz - 2) return;
-  }
   const int64_t idx = site_index(g, i, j, k);
   T* yo = y + int64_t(row.out_arr) * g.arr + idx;
   const bool bnd = dof_boundary(g, i, j, k, ox, oy, oz);
@@ -371,14 +365,14 @@ inline int lin_blocks(int64_t n) { return int(std::min<int64_t>((n + 255) / 256,
 // ============================================================ host wrappers
 template <class T>
 void launch_apply(const Geo& g, const OpDev& op, int mode, const T* x, const T* b, T* y, double alpha,
-                  cudaStream_t s, bool shell) {
+                  cudaStream_t s) {
   dim3 blk(32, 4, 1);
   if (op.nrows == 0) return;
   dim3 grd((g.nx + 1 + 31) / 32, (g.ny + 1 + 3) / 4, (g.nz + 1) * op.nrows);
   ++g_launches;
-  if (mode == MODE_SET) k_apply<T, MODE_SET><<<grd, blk, 0, s>>>(g, op, x, b, y, T(alpha), 0);
-  else if (mode == MODE_RES) k_apply<T, MODE_RES><<<grd, blk, 0, s>>>(g, op, x, b, y, T(alpha), 0);
-  else k_apply<T, MODE_ADD><<<grd, blk, 0, s>>>(g, op, x, b, y, T(alpha), shell ? 1 : 0);
+  if (mode == MODE_SET) k_apply<T, MODE_SET><<<grd, blk, 0, s>>>(g, op, x, b, y, T(alpha));
+  else if (mode == MODE_RES) k_apply<T, MODE_RES><<<grd, blk, 0, s>>>(g, op, x, b, y, T(alpha));
+  else k_apply<T, MODE_ADD><<<grd, blk, 0, s>>>(g, op, x, b, y, T(alpha));
 }
 
 template <class T>
@@ -498,7 +492,7 @@ template void launch_canon_gather<double>(const Geo&, const double*, double*, in
 template void launch_canon_gather<float>(const Geo&, const float*, double*, int64_t, int64_t, cudaStream_t);
 
 #define HHG_INST(T)                                                                                              \
-  template void launch_apply<T>(const Geo&, const OpDev&, int, const T*, const T*, T*, double, cudaStream_t, bool); \
+  template void launch_apply<T>(const Geo&, const OpDev&, int, const T*, const T*, T*, double, cudaStream_t);     \
   template void launch_gs<T>(const Geo&, const OpDev&, int, int, double, T*, const T*, cudaStream_t);              \
   template void launch_pupdate<T>(const Geo&, T*, const T*, const double*, double, cudaStream_t);                 \
   template void launch_sub_scalar_p<T>(const Geo&, T*, const double*, double, cudaStream_t);                      \

@@ -10,13 +10,10 @@ namespace hhg {
 enum ApplyMode { MODE_SET = 0, MODE_RES = 1, MODE_ADD = 2 };
 enum ReduceMode { RED_SQ = 0, RED_DOT = 1, RED_WSUM = 2, RED_SUM = 3 };
 
-// stencil rows: y (=, b -, += alpha) Op x over all rows of `op`.  shell
-// (MODE_ADD only): x is zero away from the Dirichlet boundary, so only the
-// rows whose stencil (one lattice cell) reaches a boundary node are
-// evaluated; the others would add exactly zero
+// stencil rows: y (=, b -, += alpha) Op x over all rows of `op`
 template <class T>
 void launch_apply(const Geo& g, const OpDev& op, int mode, const T* x, const T* b, T* y, double alpha,
-                  cudaStream_t s, bool shell = false);
+                  cudaStream_t s);
 
 // one multicolour Gauss-Seidel phase on the three velocity components:
 // group `grp`, colour `colour` (0..3 for the vertex group, -1 = whole group)

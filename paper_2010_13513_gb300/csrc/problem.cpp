@@ -1187,13 +1187,11 @@ extern "C" int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, co
   launch_canon_scatter<double>(g, lv.bw64, lv.W, nvn, npn, false, true, pb->stream);
   HHG_CHECK_LAUNCH();
   HHG_CUDA(cudaMemsetAsync(lv.rhs, 0, size_t(lv.nvec()) * 8, pb->stream));
-  // f = M f_h - A w_h (interior velocity rows; w_h lives on the boundary, so
-  // the lifting terms only need the rows next to it)
+  // f = M f_h - A w_h (interior velocity rows)
   HHG_TRY(apply_op<double>(pb, lv, OP_MVINT, MODE_SET, lv.tmp64, nullptr, lv.rhs));
-  launch_apply<double>(g, lv.op[OP_A], MODE_ADD, lv.W, nullptr, lv.rhs, -1.0, pb->stream, true);
+  HHG_TRY(apply_op<double>(pb, lv, OP_A, MODE_ADD, lv.W, nullptr, lv.rhs, -1.0));
   // g = -B w_h (+ PSPG load), projected to sum zero
-  launch_apply<double>(g, lv.op[OP_B], MODE_ADD, lv.W, nullptr, lv.rhs, -1.0, pb->stream, true);
-  HHG_CHECK_LAUNCH();
+  HHG_TRY(apply_op<double>(pb, lv, OP_B, MODE_ADD, lv.W, nullptr, lv.rhs, -1.0));
   if (pb->ov == 1 && pb->desc.pspg_rhs) HHG_TRY(apply_op<double>(pb, lv, OP_LOAD, MODE_ADD, lv.tmp64, nullptr, lv.rhs, 1.0));
   const int64_t po = p_offset(lv);
   launch_reduce<double>(RED_SUM, lv.rhs + po, nullptr, nullptr, g.arr, pb->partials, pb->max_blocks, pb->scal, pb->stream);
