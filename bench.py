@@ -224,8 +224,8 @@ def profile_apply():
 
 def e2e_steps(pb, wl, prm, steps):
     """Through the public API with host data: nodal forcing/Dirichlet data from
-    host memory (hhg_set_rhs on every level, assembled on the GPU), the FMG
-    solve, and the solution copied back to the host."""
+    host memory (hhg_set_rhs_levels: every level, assembled on the GPU, one
+    synchronisation), the FMG solve, and the solution copied back to the host."""
     import torch
     from paper_2010_13513_gb300 import hhg
     L = WORKLOAD["L"]
@@ -245,8 +245,7 @@ def e2e_steps(pb, wl, prm, steps):
     for _ in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for l, (f, w) in host.items():
-            pb.set_rhs(l, f, w)
+        pb.set_rhs_levels(WORKLOAD["lc"], [host[l][0] for l in sorted(host)], [host[l][1] for l in sorted(host)])
         pb.fmg_solve(prm, x, stats=False)
         pb.to_host(L, x, out=out)
         ts.append(time.perf_counter() - t0)

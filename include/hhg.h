@@ -182,6 +182,12 @@ int hhg_vector_to_host(hhg_problem* pb, int level, int prec, const void* dev, do
  * nodes (only boundary entries are read).  Kept inside the workspace.  Both
  * arrays are copied as they are and placed by a device kernel; synchronous. */
 int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal);
+/* The same for levels l0 .. l1 (f_nodal[l - l0], w_nodal[l - l0] per level):
+ * every level's copies and assembly are queued on the problem's stream and
+ * the call waits once at the end (instead of once per level).  Synchronous;
+ * HHG_EINVAL for an empty range, a level outside the hierarchy or a null
+ * pointer (levels before it are then assembled). */
+int hhg_set_rhs_levels(hhg_problem* pb, int l0, int l1, const double* const* f_nodal, const double* const* w_nodal);
 /* Device pointer of a library-owned FP64 level vector: 0 = rhs, 1 = boundary
  * lifting w_h, 2 = FMG solution x. */
 int hhg_level_vector(hhg_problem* pb, int level, int which, void** dev);

@@ -1172,7 +1172,10 @@ extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, 
 }
 
 // ------------------------------------------------------------------- rhs
-extern "C" int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal) {
+namespace {
+// enqueues the assembly of one level's right-hand side on the problem's
+// stream (the caller synchronises before the host buffers are reused)
+int enqueue_rhs(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal) {
   HHG_TRY(check_level(pb, level));
   if (!f_nodal || !w_nodal) return fail(HHG_EINVAL, "null nodal data");
   Level& lv = pb->L(level);
@@ -1199,8 +1202,23 @@ extern "C" int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, co
   HHG_CHECK_LAUNCH();
   HHG_CUDA(cudaMemsetAsync(lv.tmp64, 0, size_t(lv.nvec()) * 8, pb->stream));
   HHG_CUDA(cudaMemsetAsync(lv.bw64, 0, size_t(lv.nvec()) * 8, pb->stream));
-  HHG_CUDA(cudaStreamSynchronize(pb->stream));    // the host buffers may be reused on return
   lv.has_rhs = true;
+  return HHG_OK;
+}
+}  // namespace
+
+extern "C" int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal) {
+  HHG_TRY(enqueue_rhs(pb, level, f_nodal, w_nodal));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));    // the host buffers may be reused on return
+  return HHG_OK;
+}
+
+extern "C" int hhg_set_rhs_levels(hhg_problem* pb, int l0, int l1, const double* const* f_nodal,
+                                  const double* const* w_nodal) {
+  if (!pb) return fail(HHG_EINVAL, "null problem");
+  if (!f_nodal || !w_nodal || l1 < l0) return fail(HHG_EINVAL, "invalid level range or null pointer arrays");
+  for (int l = l0; l <= l1; ++l) HHG_TRY(enqueue_rhs(pb, l, f_nodal[l - l0], w_nodal[l - l0]));
+  HHG_CUDA(cudaStreamSynchronize(pb->stream));    // one wait for all levels
   return HHG_OK;
 }
 

@@ -89,6 +89,7 @@ def load():
         "hhg_vector_from_host": [P, I, I, DP, VP],
         "hhg_vector_to_host": [P, I, I, VP, DP],
         "hhg_set_rhs": [P, I, DP, DP],
+        "hhg_set_rhs_levels": [P, I, I, C.POINTER(DP), C.POINTER(DP)],
         "hhg_level_vector": [P, I, I, C.POINTER(VP)],
         "hhg_apply": [P, I, I, I, VP, VP],
         "hhg_residual": [P, I, I, VP, VP, VP, DP],
@@ -273,6 +274,22 @@ class Problem:
         fp, f = _host_ptr(f_nodal, n)
         wp, w = _host_ptr(w_nodal, n)
         _check(load().hhg_set_rhs(self.h, level, fp, wp), "hhg_set_rhs")
+
+    def set_rhs_levels(self, l0, f_list, w_list):
+        """set_rhs for levels l0 .. l0 + len(f_list) - 1 in one call (one
+        synchronisation for all levels)."""
+        n = len(f_list)
+        if n == 0 or len(w_list) != n:
+            raise ValueError("need one forcing and one Dirichlet array per level")
+        dp = C.POINTER(C.c_double)
+        keep, fps, wps = [], (dp * n)(), (dp * n)()
+        for i in range(n):
+            m = 3 * self.layout(l0 + i).n_velocity_nodes
+            fp, f = _host_ptr(f_list[i], m)
+            wp, w = _host_ptr(w_list[i], m)
+            keep += [f, w]
+            fps[i], wps[i] = fp, wp
+        _check(load().hhg_set_rhs_levels(self.h, l0, l0 + n - 1, fps, wps), "hhg_set_rhs_levels")
 
     # ---------------------------------------------------------------- steps
     @staticmethod
