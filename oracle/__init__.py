@@ -13,7 +13,9 @@ Modules:
                   power iteration for omega^{-1}
   * workmodel  -- the paper's work-unit model
 
-Parity status of each function is listed in the design notes; every function
-here is pinned by a test in tests/test_oracle_*.py against values the paper
-prints, closed forms, invariants or brute force.
+Every function here is pinned by a test in tests/test_oracle_pins.py against
+values the paper prints, closed forms, invariants, dense linear algebra or
+brute force (e.g. the error norms by exact L2 norms of polynomials, the
+omega^{-1} power iteration by the dense eigenvalue, the Uzawa step by dense
+splitting matrices).
 """

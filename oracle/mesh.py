@@ -61,6 +61,12 @@ class Lattice:
         k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
         return np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
 
+    def p1_int_coords_of(self, index):
+        """(i, j, k) of one P1 node index (the inverse of p1_index)."""
+        nx, ny, _ = self.p1_shape()
+        index = int(index)
+        return np.array([index % nx, (index // nx) % ny, index // (nx * ny)], dtype=np.int64)
+
     # ---- P2 nodes (doubled lattice)
     def p2_shape(self):
         return tuple(2 * d + 1 for d in self.dims)
@@ -78,6 +84,12 @@ class Lattice:
         a, b, c = self.p2_shape()
         k, j, i = np.meshgrid(np.arange(c), np.arange(b), np.arange(a), indexing="ij")
         return np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+
+    def p2_int_coords_of(self, index):
+        """(I, J, K) of one P2 node index (the inverse of p2_index)."""
+        a, b, _ = self.p2_shape()
+        index = int(index)
+        return np.array([index % a, (index // a) % b, index // (a * b)], dtype=np.int64)
 
     def p2_coords(self):
         return self.p2_int_coords() * (0.5 * self.h)

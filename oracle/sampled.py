@@ -58,7 +58,7 @@ def sample_rows(box, H, level, disc, x, rows, nu_a=0.0, with_abs=False):
     out, absout = [], []
     for field, node in rows:
         if field < 3:
-            IJK = (lat.p1_int_coords() if order == 1 else lat.p2_int_coords())[node]
+            IJK = lat.p1_int_coords_of(node) if order == 1 else lat.p2_int_coords_of(node)
             twice = IJK * (2 if order == 1 else 1)          # doubled-lattice position
             lim = 2 * dims
             if np.any(twice == 0) or np.any(twice == lim):
@@ -66,7 +66,7 @@ def sample_rows(box, H, level, disc, x, rows, nu_a=0.0, with_abs=False):
                 absout.append(0.0)
                 continue
         else:
-            twice = lat.p1_int_coords()[node] * 2
+            twice = lat.p1_int_coords_of(node) * 2
         lo = np.maximum((twice - 2) // 2, 0)
         hi = np.minimum(twice // 2, dims - 1)
         val = 0.0

@@ -26,8 +26,10 @@ Smoother (Sec. 3.2, Eq. uzawa-iteration/-velocity/-pressure):
             A_s: forward + backward) on A u = f'
     p-step: p_{k+1} = p_k - S_hat^{-1} (g - B u_{k+1} + C p_k)
 with S_hat = omega^{-1} M_L (lumped P1 pressure mass; with a variable
-viscosity the lumped mass of 1/nu), see the readings listed in the design
-notes.  Gauss-Seidel uses the multicolour order shared with the GPU: vertex
+viscosity the lumped mass of 1/nu).  This is the positive, well-defined
+reading of Sec. 3.2: omega^{-1} diag(-C) would be negative for P1-P1 and zero
+for P2-P1 (C = 0), while the eigenproblem that defines omega^{-1} is
+normalised by M_L.  Gauss-Seidel uses the multicolour order shared with the GPU: vertex
 DoFs in 4 colours c = (i + j + k) mod 4, then (P2 only) the seven edge groups
 x, y, z, xy, xz, yz, xyz, each of which has no coupling inside the group.
 

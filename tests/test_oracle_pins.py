@@ -554,3 +554,131 @@ def test_paper_gs_order_is_textbook_gauss_seidel(disc, L):
     lev.gs_sweep(mc, rhs)
     if np.count_nonzero(lev.vint & vert) > 1:
         assert np.abs(mc - want[False]).max() > 1e-6
+
+
+# --------------------------------------------------------------------------
+# closed-form pins of the error norms (Eq. error), the omega^{-1} power
+# iteration (Eq. omega-eigenvalue-problem) and the Uzawa pressure update
+# --------------------------------------------------------------------------
+class _PolyWorkload:
+    """Polynomial exact solution with zero Dirichlet data (only exact_* and
+    the rhs hooks the hierarchy calls are needed)."""
+
+    def __init__(self, u, p):
+        self.u, self.p = u, p
+
+    def forcing(self, X):
+        return np.zeros((X.shape[0], 3))
+
+    def dirichlet(self, X):
+        return np.zeros((X.shape[0], 3))
+
+    def exact_velocity(self, X):
+        return self.u(X)
+
+    def exact_pressure(self, X):
+        return self.p(X)
+
+
+def test_lattice_index_inverse():
+    lat = Lattice((2, 1, 3), 0.5, 2)
+    for idx in (0, 7, lat.p1_count() - 1, 123):
+        assert np.array_equal(lat.p1_int_coords_of(idx), lat.p1_int_coords()[idx])
+    for idx in (0, 11, lat.p2_count() - 1, 2345):
+        assert np.array_equal(lat.p2_int_coords_of(idx), lat.p2_int_coords()[idx])
+
+
+@pytest.mark.parametrize("disc", ["P1P1", "P2P1"])
+def test_error_norms_closed_forms(disc):
+    """Eq. error with x = 0 is the M-norm of the exact fields on level l+1.
+    The consistent mass matrix integrates the interpolant exactly, so for
+    u* = (x, 0, 0) (P1) or (x^2, 0, 0) (P2) the velocity part is sqrt(1/3)
+    or sqrt(1/5), and for p* = x the mean-zero pressure part is
+    ||x - 1/2||_L2 = sqrt(1/12) (sqrt(1/3) if the mean were not removed; a
+    lumped mass gives neither).  With x = the interpolant of (u*, p*) on
+    level l, I x reproduces the polynomials and both parts vanish."""
+    if disc == "P1P1":
+        u = lambda X: np.stack([X[:, 0], 0 * X[:, 0], 0 * X[:, 0]], axis=1)
+        ref_u = math.sqrt(1.0 / 3.0)
+    else:
+        u = lambda X: np.stack([X[:, 0] ** 2, 0 * X[:, 0], 0 * X[:, 0]], axis=1)
+        ref_u = math.sqrt(1.0 / 5.0)
+    p = lambda X: X[:, 0].copy()
+    wl = _PolyWorkload(u, p)
+    hy = StokesHierarchy((1, 1, 1), 1.0, 2, disc, coarse_level=2, workload=wl)
+    lev = hy.lv[2]
+    eu, ep = hy.error_norms(np.zeros(lev.size))
+    assert eu == pytest.approx(ref_u, rel=1e-12)
+    assert ep == pytest.approx(math.sqrt(1.0 / 12.0), rel=1e-12)
+    uv = u(lev.vcoords())
+    x = lev.join([uv[:, c] for c in range(3)], p(lev.pcoords()))
+    eu0, ep0 = hy.error_norms(x)
+    assert eu0 < 1e-13 and ep0 < 1e-13
+
+
+def _dense_sgs_inverse(lev):
+    """A_s^{-1} of the interior velocity block as a dense matrix: forward
+    Gauss-Seidel (D + L)^{-1} in the stated order followed by the backward
+    sweep, written as the two-step splitting form with triangular solves
+    (not the oracle's phase loop)."""
+    order = np.concatenate(lev.phases)
+    A = lev.A[order][:, order].toarray()
+    n = A.shape[0]
+    low, up = np.tril(A), np.triu(A)
+    F = np.linalg.solve(low, np.eye(n))                      # forward sweep from zero
+    S = F + np.linalg.solve(up, np.eye(n) - A @ F)           # then the backward sweep
+    return order, S
+
+
+@pytest.mark.parametrize("disc,L", [("P1P1", 2), ("P2P1", 1)])
+def test_omega_estimate_equals_dense_eigenvalue(disc, L):
+    """The power iteration returns the largest eigenvalue of
+    M_L^{-1}(C + B A_s^{-1} B^T), computed here densely with numpy.linalg.eigvals."""
+    hy = StokesHierarchy((1, 1, 1), 1.0, L, disc, coarse_level=L, workload=Workload("curl"))
+    lev = hy.lv[L]
+    order, S = _dense_sgs_inverse(lev)
+    B = [lev.B[c][:, order].toarray() for c in range(3)]
+    T = lev.C.toarray() + sum(B[c] @ S @ B[c].T for c in range(3))
+    T = T / lev.ML_hat[:, None]
+    lam = np.max(np.abs(np.linalg.eigvals(T)))
+    v0 = np.random.default_rng(0).uniform(-1, 1, lev.np)
+    est = hy.estimate_omega_inv(v0, iters=400)
+    assert est == pytest.approx(lam, rel=1e-6), (est, lam)
+
+
+@pytest.mark.parametrize("disc,ahat", [("P1P1", "s"), ("P1P1", "f"), ("P2P1", "f")])
+def test_uzawa_fixed_point_and_pressure_step(disc, ahat):
+    """Eqs. uzawa-velocity / uzawa-pressure: the discrete solution (dense
+    bordered solve) is a fixed point; and from (u*, p* + d) with a mean-zero
+    pressure perturbation d, one iteration gives exactly
+    u' = u* - A_hat^{-1} B^T d (dense splitting matrices) and
+    p' = p* + d - S_hat^{-1}(B (u* - u') + C d), S_hat = omega^{-1} M_L."""
+    L = 2 if disc == "P1P1" else 1
+    hy = StokesHierarchy((1, 1, 1), 1.0, L, disc, coarse_level=L, workload=Workload("curl"))
+    lev = hy.lv[L]
+    b = hy.rhs[L]
+    xs = lev.project_pressure(hy.coarse_solve(b))
+    prm = Params(ahat=ahat, xi=1, omega_inv=0.7)
+    x1 = lev.uzawa(xs, b, prm)
+    assert np.linalg.norm(x1 - xs) <= 1e-11 * np.linalg.norm(xs)
+    rng = np.random.default_rng(5)
+    d = rng.uniform(-1, 1, lev.np)
+    d -= np.dot(lev.ML, d) / lev.ML.sum()
+    us, ps = lev.split(xs)
+    x2 = lev.uzawa(lev.join(us, ps + d), b, prm)
+    u2, p2 = lev.split(x2)
+    order = np.concatenate(lev.phases)
+    A = lev.A[order][:, order].toarray()
+    if ahat == "f":
+        Ainv = np.linalg.solve(np.tril(A), np.eye(A.shape[0]))
+    else:
+        _, Ainv = _dense_sgs_inverse(lev)
+    Bd = [lev.B[c][:, order].toarray() for c in range(3)]
+    du = []
+    for c in range(3):
+        ref = us[c].copy()
+        ref[order] = us[c][order] - Ainv @ (Bd[c].T @ d)
+        assert np.abs(u2[c] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+        du.append(us[c] - u2[c])
+    pref = ps + d - (sum(lev.B[c] @ du[c] for c in range(3)) + lev.C @ d) / (0.7 * lev.ML_hat)
+    assert np.abs(p2 - pref).max() <= 1e-12 * max(1.0, np.abs(pref).max())
