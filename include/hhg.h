@@ -184,9 +184,13 @@ int hhg_vector_to_host(hhg_problem* pb, int level, int prec, const void* dev, do
 int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal);
 /* The same for levels l0 .. l1 (f_nodal[l - l0], w_nodal[l - l0] per level):
  * every level's copies and assembly are queued on the problem's stream and
- * the call waits once at the end (instead of once per level).  Synchronous;
- * HHG_EINVAL for an empty range, a level outside the hierarchy or a null
- * pointer (levels before it are then assembled). */
+ * the call waits once at the end (instead of once per level).  Synchronous.
+ * Every level and pointer is checked before anything is queued: HHG_EINVAL
+ * for an empty range, a level outside the hierarchy or a null pointer, and
+ * then no level's right-hand side has changed.  If a CUDA call fails after
+ * work was queued, the call waits for the queued work before it returns the
+ * error (the host buffers are then free; the levels are in an undefined
+ * state). */
 int hhg_set_rhs_levels(hhg_problem* pb, int l0, int l1, const double* const* f_nodal, const double* const* w_nodal);
 /* Device pointer of a library-owned FP64 level vector: 0 = rhs, 1 = boundary
  * lifting w_h, 2 = FMG solution x. */
@@ -224,8 +228,9 @@ int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats
  * fastest is kept.  Uses only the library's scratch vectors; cached graphs
  * are dropped.  shapes_out (optional) receives 16 ints per level (coarse ..
  * L): row threads, row k planes, Gauss-Seidel threads (edge groups), resident CTAs,
- * resident threads per CTA, whether the FP32 stencil rows use the
- * shared-memory-tiled kernels, the row kernels' sites per thread, the
+ * resident threads per CTA, the threads per block of the streaming kernel
+ * of the full operator (0 = the plain kernels), the row kernels' sites per
+ * thread, the
  * lanes per Gauss-Seidel site of the edge groups and of the vertex colours
  * (tuned apart), and the threads, k planes and sites per thread of the
  * smoother's B^T rows and of its (B, -C) rows (tuned apart from the full
@@ -235,14 +240,19 @@ int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
 /* Not in the paper (GPU launch choices): the launch shape of the stencil
  * kernels of one level -- threads per block of the row kernels (64/128/256),
  * k planes per thread (1..64), threads per block of the Gauss-Seidel kernels
- * (64/128/256), and row_tile = 1 to evaluate the FP32 rows of the full
- * operator (apply, residual) and of the smoother's B^T and (B, -C) residuals
- * in shared-memory tiles (a block loads a 32 x 4 x 4 tile of lattice sites
- * plus halo of the input arrays of one group of rows; default off, an
- * autotuner candidate), and row_sites = 1 or 4 sites per thread of the
+ * (64/128/256), and row_tile = 64, 128 or 256 (1 = 128) to evaluate the
+ * rows of the full operator (apply, residual) and of the smoother's B^T and
+ * (B, -C) residuals, in both precisions, by the streaming kernels with that
+ * many threads per block (a block owns 4 x threads positions of the (i, j)
+ * plane, stages the planes of its input arrays in shared memory as it marches
+ * along k, and loads each line of a thread's stencil footprint once per
+ * plane; the grid is one wave of blocks with equal runs of planes; only on
+ * levels with nx >= 64, whose pitch sx is a multiple of four; 0 = the plain
+ * kernels), and
+ * row_sites = 1 or 4 sites per thread of the
  * row kernels (4: each warp evaluates four runs of 32 consecutive
  * positions of the padded (i, j) plane, sharing each term's address
- * between the runs; row_tile = 1 takes precedence for FP32; sets the FP32
+ * between the runs; row_tile != 0 takes precedence; sets the FP32
  * and FP64 rows, which hhg_autotune chooses separately), and gs_lanes = 1, 2
  * or 4 lanes per Gauss-Seidel site (the lanes take every gs_lanes-th term
  * of the site's rows and add their sums by shuffles; sets the vertex colours
@@ -253,6 +263,18 @@ int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
 int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads, int row_kplanes, int gs_threads, int row_tile,
                          int row_sites, int gs_lanes);
 int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape6);
+
+/* Not in the paper (a GPU execution choice): the launch order of the
+ * per-phase Gauss-Seidel kernels of `level` (levels whose smoother runs one
+ * launch per phase).  order 0: every phase updates the three velocity
+ * components; order 1: component by component -- all xi sweeps (forward, and
+ * backward for A_s) of u_1, then of u_2, then of u_3, so that one component's
+ * group arrays stay in L2 through its sweeps on levels whose vectors exceed
+ * L2.  A = diag(A, A, A) (Eq. stokes-discrete) couples no two components, so
+ * both orders give the same iterates.  hhg_autotune chooses it by timing;
+ * default 0.  Drops cached graphs. */
+int hhg_set_level_sweep_order(hhg_problem* pb, int level, int order);
+int hhg_get_level_sweep_order(hhg_problem* pb, int level, int* order);
 
 /* ------------------------------------------- learned coarse-grid correction */
 /* Not in the paper: a small MLP  y = W3 relu(W2 relu(W1 x + b1) + b2) + b3
@@ -368,7 +390,10 @@ int hhg_error_norms(hhg_problem* pb, int level, const void* x, const double* u_e
  * holds until exit.  Each part may hold at most 2^31 - 1 elements (larger
  * sizes return HHG_EINVAL).  The first call on a device looks the array up
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls that overlap
+ * before any stream capture.  The looked-up address belongs to the device's
+ * primary context: after a cudaDeviceReset (or anything else that replaces
+ * that context) it is stale, and the process must not call this entry point
+ * on that device again.  All calls share the array: calls that overlap
  * on the GPU (other streams, other threads) race and must be serialised by
  * the caller.  Every call writes all partial sums it reads, so nothing needs
  * clearing between calls. */

@@ -19,7 +19,6 @@
 #include <type_traits>
 
 #include "fast.h"
-#include "tile.h"
 #include "kernels.h"
 #include "structure.inc"
 
@@ -300,7 +299,9 @@ __device__ __forceinline__ T lane_sum(T v) {
 // 2^LP lanes per site, z = k.  With LP > 0 the lanes of a site take every
 // 2^LP-th term and add their sums by shuffles: shorter dependent chains and
 // more threads for the small levels, whose phases are latency-bound.
-template <int DISC, int VARNU, int GRP, class T, int LP, int T0, int N1, class Tab>
+// NC = 3: the three velocity components at once (u, rhs: block vectors);
+// NC = 1: one component (u, rhs point to that component's first group array)
+template <int DISC, int VARNU, int GRP, class T, int LP, int NC, int T0, int N1, class Tab>
 __device__ __forceinline__ void gs_site(const Geo& g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag,
                                         int colour, const Tab& tab) {
   constexpr int ox = GRP == 1 || GRP == 4 || GRP == 5 || GRP == 7;
@@ -327,8 +328,10 @@ __device__ __forceinline__ void gs_site(const Geo& g, T* __restrict__ u, const T
       const T wt = tab.w[T0 + t];
       const int o = tab.off[T0 + t];
       a0 += wt * us[o];
-      a1 += wt * us[o + cs];
-      a2 += wt * us[o + 2 * cs];
+      if (NC == 3) {
+        a1 += wt * us[o + cs];
+        a2 += wt * us[o + 2 * cs];
+      }
     }
   } else {
     if (ok) {
@@ -339,25 +342,31 @@ __device__ __forceinline__ void gs_site(const Geo& g, T* __restrict__ u, const T
           const T wt = tab.w[T0 + t];
           const int o = tab.off[T0 + t];
           a0 += wt * us[o];
-          a1 += wt * us[o + cs];
-          a2 += wt * us[o + 2 * cs];
+          if (NC == 3) {
+            a1 += wt * us[o + cs];
+            a2 += wt * us[o + 2 * cs];
+          }
         }
       }
     }
     a0 = lane_sum<LP>(a0);                     // whole warps: the grid covers whole blocks
-    a1 = lane_sum<LP>(a1);
-    a2 = lane_sum<LP>(a2);
+    if (NC == 3) {
+      a1 = lane_sum<LP>(a1);
+      a2 = lane_sum<LP>(a2);
+    }
     if (!ok || p != 0) return;
   }
   T einv = T(1);
   if (VARNU) einv = T(g.eisc[k]);
   const int64_t o0 = int64_t(GRP) * g.arr + idx;
   u[o0] = (rhs[o0] * einv - a0) * inv_diag;
-  u[o0 + cs] = (rhs[o0 + cs] * einv - a1) * inv_diag;
-  u[o0 + 2 * cs] = (rhs[o0 + 2 * cs] * einv - a2) * inv_diag;
+  if (NC == 3) {
+    u[o0 + cs] = (rhs[o0 + cs] * einv - a1) * inv_diag;
+    u[o0 + 2 * cs] = (rhs[o0 + 2 * cs] * einv - a2) * inv_diag;
+  }
 }
 
-template <int DISC, int VARNU, int GRP, class T, int LP>
+template <int DISC, int VARNU, int GRP, class T, int LP, int NC>
 __global__ void __launch_bounds__(256)
     k_gs_fast(Geo g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag, int colour,
               const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP_A>::N> tab) {
@@ -365,7 +374,7 @@ __global__ void __launch_bounds__(256)
   constexpr gen::RowS rw = S::rows[GRP];       // component-0 row of the group; all terms in segment 1
   static_assert(rw.n0 == 0 && rw.n2 == 0, "A rows carry only nu-scaled terms");
   pdl_wait();
-  gs_site<DISC, VARNU, GRP, T, LP, rw.t0, rw.n1>(g, u, rhs, inv_diag, colour, tab);
+  gs_site<DISC, VARNU, GRP, T, LP, NC, rw.t0, rw.n1>(g, u, rhs, inv_diag, colour, tab);
   pdl_trigger();
 }
 
@@ -427,7 +436,7 @@ void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, 
 
 template <int DISC, int VARNU, class T>
 void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u, const T* rhs,
-                    const Shape& sh, cudaStream_t s) {
+                    const Shape& sh, int comp, cudaStream_t s) {
   using S = gen::S<DISC, VARNU, OP_A>;
   using Tab = FastTab<T, S::N>;
   const Tab& tb = *static_cast<const Tab*>(tab);
@@ -441,8 +450,14 @@ void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double i
   ++g_launches;
   auto go = [&](auto gc, auto lc) {
     constexpr int GRP = decltype(gc)::value, LP = decltype(lc)::value;
-    if constexpr (DISC == 2 || GRP == 0)
-      launch_pdl(k_gs_fast<DISC, VARNU, GRP, T, LP>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb);
+    if constexpr (DISC == 2 || GRP == 0) {
+      if (comp < 0) {
+        launch_pdl(k_gs_fast<DISC, VARNU, GRP, T, LP, 3>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb);
+      } else {
+        const int64_t cs = int64_t(comp) * g.G * g.arr;   // the component's first group array
+        launch_pdl(k_gs_fast<DISC, VARNU, GRP, T, LP, 1>, grd, blk, s, g, u + cs, rhs + cs, T(inv_diag), colour, tb);
+      }
+    }
   };
   auto by_lanes = [&](auto gc) {
     if (lp == 2) go(gc, std::integral_constant<int, 2>{});
@@ -479,8 +494,6 @@ int fast_terms(int disc, int varnu, int op) {
 template <class T>
 void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode, const T* x,
                const T* b, T* y, double alpha, const Shape& sh, cudaStream_t s) {
-  if constexpr (std::is_same_v<T, float>)
-    if (sh.row_tile && tile_rows(disc, varnu, op, mode, g, od, tab, x, b, y, alpha, s)) return;
 #define HHG_R(D, V, O) \
   if (disc == D && varnu == V && op == O) return launch_rows_fast<D, V, O, T>(g, od, tab, mode, x, b, y, alpha, sh, s);
   HHG_R(1, 0, OP_FULL) HHG_R(1, 0, OP_BT) HHG_R(1, 0, OP_BC)
@@ -492,11 +505,11 @@ void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const
 
 template <class T>
 void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
-             const T* rhs, const Shape& sh, cudaStream_t s) {
-  if (disc == 1 && !varnu) launch_gs_fast<1, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, s);
-  else if (disc == 1) launch_gs_fast<1, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, s);
-  else if (!varnu) launch_gs_fast<2, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, s);
-  else launch_gs_fast<2, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, s);
+             const T* rhs, const Shape& sh, cudaStream_t s, int comp) {
+  if (disc == 1 && !varnu) launch_gs_fast<1, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp, s);
+  else if (disc == 1) launch_gs_fast<1, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp, s);
+  else if (!varnu) launch_gs_fast<2, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp, s);
+  else launch_gs_fast<2, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp, s);
 }
 
 // HHG_FAST_ONLY = 64 / 32 compiles one precision (the build compiles this
@@ -505,13 +518,13 @@ void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int co
 template void fast_rows<double>(int, int, int, const Geo&, const OpDev&, const void*, int, const double*, const double*,
                                 double*, double, const Shape&, cudaStream_t);
 template void fast_gs<double>(int, int, const Geo&, const void*, int, int, double, double*, const double*, const Shape&,
-                              cudaStream_t);
+                              cudaStream_t, int);
 #endif
 #if !defined(HHG_FAST_ONLY) || HHG_FAST_ONLY == 32
 template void fast_rows<float>(int, int, int, const Geo&, const OpDev&, const void*, int, const float*, const float*,
                                float*, double, const Shape&, cudaStream_t);
 template void fast_gs<float>(int, int, const Geo&, const void*, int, int, double, float*, const float*, const Shape&,
-                             cudaStream_t);
+                             cudaStream_t, int);
 #endif
 
 }  // namespace hhg

@@ -28,9 +28,18 @@ struct Shape {
   // (B, -C) rows in the V-cycle precision; 0 = the full operator's
   int bt_threads = 0, bt_kplanes = 0, bt_sites = 0;
   int bc_threads = 0, bc_kplanes = 0, bc_sites = 0;
-  int row_tile = 0;        // FP32 rows by the shared-memory-tiled kernels (tile.cu; autotuner candidate)
+  // streaming kernels (stream.cu) of the FULL, B^T and (B, -C) rows: threads
+  // per block (0 = the plain kernels), in the V-cycle precision (st_threads)
+  // and in FP64 (st64_threads; the mixed solve's outer residual)
+  int st_threads[3] = {0, 0, 0};
+  int st64_threads[3] = {0, 0, 0};
   int row_sites = 1;       // sites per thread of the FP32 row kernels (1, or 4: four runs of 32 positions per warp)
   int row_sites64 = 1;     // the same for the FP64 row kernels
+  // order of the per-phase Gauss-Seidel launches of a smoothing step: 0 = every
+  // phase on the three components at once; 1 = component by component (all
+  // sweeps of one component before the next: its arrays stay in L2 on levels
+  // whose vectors exceed it)
+  int gs_comp_major = 0;
 };
 
 // number of interior terms of a specialised operator (-1 if none)
@@ -42,10 +51,12 @@ template <class T>
 void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode, const T* x,
                const T* b, T* y, double alpha, const Shape& sh, cudaStream_t s);
 
-// one Gauss-Seidel phase (group, colour) on the three velocity components;
-// `tab` points to a host FastTab<T, fast_terms(disc, varnu, OP_A)>
+// one Gauss-Seidel phase (group, colour) on the three velocity components
+// (comp = -1) or on velocity component comp (0..2) only (A is block diagonal
+// over the components, so each component's iterates are the same either
+// way); `tab` points to a host FastTab<T, fast_terms(disc, varnu, OP_A)>
 template <class T>
 void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
-             const T* rhs, const Shape& sh, cudaStream_t s);
+             const T* rhs, const Shape& sh, cudaStream_t s, int comp = -1);
 
 }  // namespace hhg

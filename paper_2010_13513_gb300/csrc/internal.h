@@ -5,7 +5,9 @@
 // G = 1 for P1-P1 (vertex DoFs), G = 8 for P2-P1 (vertex + 7 edge groups,
 // Sec. 2.2).  Every group array is box-shaped over the coarse index (i,j,k),
 // 0 <= i <= nx (+1 halo layer on each side, zero), x fastest:
-//   index(i,j,k) = (i+1) + (j+1) sx + (k+1) sy.
+//   index(i,j,k) = (i+1) + (j+1) sx + (k+1) sy,
+// with the j pitch sx = nx + 3, rounded up to a multiple of four on levels
+// with nx >= 64 (the extra entries of a row are padding, zero).
 // Group g with parity offset o_g holds the DoF at doubled position
 // 2 (i,j,k) + o_g; entries past the group's extent are padding (zero).
 #pragma once
@@ -47,7 +49,11 @@ inline Geo make_geo(int mx, int my, int mz, int level, int G, double H, double n
   Geo g;
   const int n = 1 << level;
   g.nx = mx * n; g.ny = my * n; g.nz = mz * n;
+  // large levels: a multiple of four (16-byte aligned quads of sites for the
+  // streaming kernels); small levels keep the tight pitch (their smoother
+  // holds the whole level in shared memory)
   g.sx = g.nx + 3;
+  if (g.nx >= 64) g.sx = (g.sx + 3) / 4 * 4;
   g.sy = int64_t(g.sx) * (g.ny + 3);
   int64_t a = g.sy * (g.nz + 3);
   g.arr = (a + 63) / 64 * 64;

@@ -18,7 +18,7 @@
 #include "kernels.h"
 #include "nn.h"
 #include "small.h"
-#include "tile.h"
+#include "stream.h"
 
 using namespace hhg;
 
@@ -131,6 +131,9 @@ struct Level {
   // parameter blocks of the specialised kernels (FastTab<T, N> images)
   std::vector<char> ftab64[OP_COUNT], ftab32[OP_COUNT];
   bool has_fast[OP_COUNT] = {};
+  // parameter blocks of the streaming kernels (FULL, B^T, (B, -C))
+  std::vector<char> stab64[OP_COUNT], stab32[OP_COUNT];
+  bool has_stream[OP_COUNT] = {};
   // parameter blocks (ResTabs images) of the shared-memory-resident
   // smoother, per CTA count (the offsets depend on the slab stride)
   std::map<int, std::vector<char>> rtab64, rtab32;
@@ -333,6 +336,33 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
         };
         if (!image(0.0, lv.ftab64[o]) || !image(0.0f, lv.ftab32[o])) return fail(HHG_EINVAL, "level too large for 32-bit offsets");
         lv.has_fast[o] = true;
+      }
+      if (N >= 0 && (o == OP_FULL || o == OP_BT || o == OP_BC)) {
+        // streaming kernels: the weights, and the boundary C stencil of the
+        // pressure row summed per boundary class (27 classes: each of i, j, k
+        // on the low face, inside, or on the high face; a per-cube term
+        // counts where its cube lies inside the box)
+        std::vector<int> offs;
+        stream_c_offsets(desc->disc, varnu, o, offs);
+        const int ncb = int(offs.size()) / 3;
+        std::vector<double> wc(size_t(27) * ncb, 0.0);
+        for (const HRow& R : lv.st.op[o].rows)
+          if (R.all_rows)
+            for (const HTerm& t : R.bseg[2]) {
+              int slot = -1;
+              for (int q = 0; q < ncb; ++q)
+                if (offs[3 * q] == t.di && offs[3 * q + 1] == t.dj && offs[3 * q + 2] == t.dk) slot = q;
+              if (slot < 0) return fail(HHG_EINVAL, "internal: boundary stencil offset missing from the plan");
+              const int cc[3] = {t.cx, t.cy, t.cz};
+              for (int cls = 0; cls < 27; ++cls) {
+                const int c3[3] = {cls % 3, (cls / 3) % 3, cls / 9};
+                bool in = true;
+                for (int d = 0; d < 3; ++d) in = in && !(c3[d] == 0 && cc[d] < 0) && !(c3[d] == 2 && cc[d] >= 0);
+                if (in) wc[size_t(cls) * ncb + slot] += t.w;
+              }
+            }
+        lv.has_stream[o] = stream_image<double>(desc->disc, varnu, o, h.w64, wc, lv.stab64[o]) &&
+                           stream_image<float>(desc->disc, varnu, o, h.w64, wc, lv.stab32[o]);
       }
       std::vector<float> w32(h.w64.begin(), h.w64.end()), bw32(h.bw64.begin(), h.bw64.end());
       OpOffsets& of = lv.opoff[o];
@@ -571,8 +601,26 @@ template <class T> const void* ftab(Level& lv, int op);
 template <> const void* ftab<double>(Level& lv, int op) { return lv.ftab64[op].data(); }
 template <> const void* ftab<float>(Level& lv, int op) { return lv.ftab32[op].data(); }
 
+template <class T> const void* stab(Level& lv, int op);
+template <> const void* stab<double>(Level& lv, int op) { return lv.stab64[op].data(); }
+template <> const void* stab<float>(Level& lv, int op) { return lv.stab32[op].data(); }
+
+// the streaming kernels of op if the level's shape selects them (true if launched)
+template <class T>
+bool stream_op(hhg_problem* pb, Level& lv, const Shape& sh, int op, int mode, const T* x, const T* b, T* y) {
+  const int si = op == OP_FULL ? 0 : op == OP_BT ? 1 : op == OP_BC ? 2 : -1;
+  if (si < 0 || mode == MODE_ADD || !lv.has_stream[op]) return false;
+  const int nt = sizeof(T) == 8 ? sh.st64_threads[si] : sh.st_threads[si];
+  return nt && stream_rows<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, op, mode, lv.g, stab<T>(lv, op), x, b, y,
+                              nt, pb->stream);
+}
+
 template <class T>
 int apply_op(hhg_problem* pb, Level& lv, int op, int mode, const T* x, const T* b, T* y, double alpha = 1.0) {
+  if (stream_op<T>(pb, lv, lv.shape, op, mode, x, b, y)) {
+    HHG_CHECK_LAUNCH();
+    return HHG_OK;
+  }
   if (lv.has_fast[op] && op != OP_A)
     fast_rows<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, op, lv.g, lv.op[op], ftab<T>(lv, op), mode, x, b, y,
                  alpha, lv.shape, pb->stream);
@@ -719,14 +767,20 @@ int uzawa(hhg_problem* pb, Level& lv, const hhg_params& prm, int sweeps, T* x, c
     HHG_TRY(apply_op<T>(pb, lv, OP_BT, MODE_RES, x, b, tmp));
     const int disc = pb->desc.disc, varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
     const void* tabA = ftab<T>(lv, OP_A);
-    for (int s = 0; s < prm.xi; ++s) {
-      for (auto& ph : phases)
-        fast_gs<T>(disc, varnu, lv.g, tabA, ph.first, ph.second, lv.inv_diag[ph.first], x, tmp, lv.shape, pb->stream);
-      if (prm.ahat == HHG_AHAT_S)
-        for (auto it2 = phases.rbegin(); it2 != phases.rend(); ++it2)
-          fast_gs<T>(disc, varnu, lv.g, tabA, it2->first, it2->second, lv.inv_diag[it2->first], x, tmp, lv.shape,
-                     pb->stream);
-    }
+    // A is block diagonal over the velocity components: either every phase
+    // on all three components, or all sweeps of one component after another
+    // (the same iterates)
+    const bool cm = lv.shape.gs_comp_major != 0;
+    for (int c = cm ? 0 : -1; c < (cm ? 3 : 0); ++c)
+      for (int s = 0; s < prm.xi; ++s) {
+        for (auto& ph : phases)
+          fast_gs<T>(disc, varnu, lv.g, tabA, ph.first, ph.second, lv.inv_diag[ph.first], x, tmp, lv.shape, pb->stream,
+                     c);
+        if (prm.ahat == HHG_AHAT_S)
+          for (auto it2 = phases.rbegin(); it2 != phases.rend(); ++it2)
+            fast_gs<T>(disc, varnu, lv.g, tabA, it2->first, it2->second, lv.inv_diag[it2->first], x, tmp, lv.shape,
+                       pb->stream, c);
+      }
     HHG_CHECK_LAUNCH();
     // pressure step (Eq. uzawa-pressure): p -= S_hat^{-1} (g - B u_{k+1} + C p_k)
     HHG_TRY(apply_op<T>(pb, lv, OP_BC, MODE_RES, x, b, tmp));
@@ -1159,7 +1213,8 @@ extern "C" int hhg_problem_bind(hhg_problem* pb, void* workspace, size_t bytes, 
   }
   HHG_TRY(build_coarse(pb));
   if (pb->nn_h > 0) HHG_TRY(nn_setup(pb));
-  tile_init();
+  stream_init<float>();
+  stream_init<double>();
   for (Level& lv : pb->lv) {
     HHG_TRY(default_resident(pb, lv, HHG_FP64));
     HHG_TRY(default_resident(pb, lv, HHG_FP32));
@@ -1207,8 +1262,24 @@ int enqueue_rhs(hhg_problem* pb, int level, const double* f_nodal, const double*
 }
 }  // namespace
 
+// arguments of one level's rhs, checked before anything is queued
+static int check_rhs_args(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal) {
+  HHG_TRY(check_level(pb, level));
+  if (!f_nodal || !w_nodal) return fail(HHG_EINVAL, "null nodal data");
+  return HHG_OK;
+}
+
+// a failure after work was queued: wait for the queued copies, so that the
+// caller's host buffers are free when the error is returned
+static int fail_after_queue(hhg_problem* pb, int rc) {
+  cudaStreamSynchronize(pb->stream);
+  return rc;
+}
+
 extern "C" int hhg_set_rhs(hhg_problem* pb, int level, const double* f_nodal, const double* w_nodal) {
-  HHG_TRY(enqueue_rhs(pb, level, f_nodal, w_nodal));
+  HHG_TRY(check_rhs_args(pb, level, f_nodal, w_nodal));
+  const int rc = enqueue_rhs(pb, level, f_nodal, w_nodal);
+  if (rc != HHG_OK) return fail_after_queue(pb, rc);
   HHG_CUDA(cudaStreamSynchronize(pb->stream));    // the host buffers may be reused on return
   return HHG_OK;
 }
@@ -1217,7 +1288,12 @@ extern "C" int hhg_set_rhs_levels(hhg_problem* pb, int l0, int l1, const double*
                                   const double* const* w_nodal) {
   if (!pb) return fail(HHG_EINVAL, "null problem");
   if (!f_nodal || !w_nodal || l1 < l0) return fail(HHG_EINVAL, "invalid level range or null pointer arrays");
-  for (int l = l0; l <= l1; ++l) HHG_TRY(enqueue_rhs(pb, l, f_nodal[l - l0], w_nodal[l - l0]));
+  // every level and pointer is checked first: an invalid call changes nothing
+  for (int l = l0; l <= l1; ++l) HHG_TRY(check_rhs_args(pb, l, f_nodal[l - l0], w_nodal[l - l0]));
+  for (int l = l0; l <= l1; ++l) {
+    const int rc = enqueue_rhs(pb, l, f_nodal[l - l0], w_nodal[l - l0]);
+    if (rc != HHG_OK) return fail_after_queue(pb, rc);
+  }
   HHG_CUDA(cudaStreamSynchronize(pb->stream));    // one wait for all levels
   return HHG_OK;
 }
@@ -1399,14 +1475,15 @@ extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads,
   HHG_TRY(check_level(pb, level));
   auto ok_threads = [](int t) { return t == 64 || t == 128 || t == 256; };
   if (!ok_threads(row_threads) || !ok_threads(gs_threads) || row_kplanes < 1 || row_kplanes > 64 ||
-      (row_tile != 0 && row_tile != 1) || (row_sites != 1 && row_sites != 4) ||
+      (row_tile != 0 && row_tile != 1 && !ok_threads(row_tile)) || (row_sites != 1 && row_sites != 4) ||
       (gs_lanes != 1 && gs_lanes != 2 && gs_lanes != 4))
     return fail(HHG_EINVAL, "invalid launch shape");
   Shape& sh = pb->L(level).shape;
   sh.row_threads = row_threads;
   sh.row_kplanes = row_kplanes;
   sh.gs_threads = gs_threads;
-  sh.row_tile = row_tile;
+  const int st = row_tile == 1 ? 128 : row_tile;
+  for (int o = 0; o < 3; ++o) sh.st_threads[o] = sh.st64_threads[o] = st;
   sh.row_sites = row_sites;
   sh.row_sites64 = row_sites;
   sh.gs_lanes = gs_lanes;
@@ -1419,11 +1496,27 @@ extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads,
   return HHG_OK;
 }
 
+extern "C" int hhg_set_level_sweep_order(hhg_problem* pb, int level, int order) {
+  HHG_TRY(check_level(pb, level));
+  if (order != 0 && order != 1) return fail(HHG_EINVAL, "order must be 0 or 1");
+  pb->L(level).shape.gs_comp_major = order;
+  for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
+  pb->graphs.clear();
+  return HHG_OK;
+}
+
+extern "C" int hhg_get_level_sweep_order(hhg_problem* pb, int level, int* order) {
+  HHG_TRY(check_level(pb, level));
+  if (!order) return fail(HHG_EINVAL, "null argument");
+  *order = pb->L(level).shape.gs_comp_major;
+  return HHG_OK;
+}
+
 extern "C" int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape6) {
   HHG_TRY(check_level(pb, level));
   if (!shape6) return fail(HHG_EINVAL, "null argument");
   const Shape& sh = pb->L(level).shape;
-  shape6[0] = sh.row_threads; shape6[1] = sh.row_kplanes; shape6[2] = sh.gs_threads; shape6[3] = sh.row_tile;
+  shape6[0] = sh.row_threads; shape6[1] = sh.row_kplanes; shape6[2] = sh.gs_threads; shape6[3] = sh.st_threads[0];
   shape6[4] = sh.row_sites; shape6[5] = sh.gs_lanes;
   return HHG_OK;
 }
@@ -1691,6 +1784,8 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
   // sites per warp
   const int threads[3] = {64, 128, 256}, planes[5] = {1, 2, 4, 8, 16};
   float best = 1e30f;
+  // the plain kernels are timed first; the streaming kernels compete after
+  for (int o = 0; o < 3; ++o) lv.shape.st_threads[o] = lv.shape.st64_threads[o] = 0;
   Shape bestS = lv.shape;
   for (int v : {1, 4})
     for (int t : threads)
@@ -1699,7 +1794,6 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
         Shape sh = lv.shape;
         sh.row_threads = t;
         sh.row_kplanes = kp;
-        sh.row_tile = 0;
         sh.row_sites = v;
         const float ms = time_it([&] {
           fast_rows<T>(disc, varnu, OP_FULL, lv.g, lv.op[OP_FULL], ftab<T>(lv, OP_FULL), MODE_RES, xa, xa, xb, 1.0,
@@ -1733,7 +1827,6 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
         for (int kp : {1, 2, 4}) {
           if (v > 1 && t == 64) continue;
           Shape sh = bestS;
-          sh.row_tile = 0;
           if (op == OP_BT) { sh.bt_threads = t; sh.bt_kplanes = kp; sh.bt_sites = v; }
           else { sh.bc_threads = t; sh.bc_kplanes = kp; sh.bc_sites = v; }
           const float ms = time_it([&] {
@@ -1744,15 +1837,40 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
     if (op == OP_BT) { bestS.bt_threads = bt; bestS.bt_kplanes = bk; bestS.bt_sites = bs; }
     else { bestS.bc_threads = bt; bestS.bc_kplanes = bk; bestS.bc_sites = bs; }
   }
-  // FP32 rows: the shared-memory-tiled kernels against the best plain shape
-  if (std::is_same<T, float>::value) {
-    Shape sh = bestS;
-    sh.row_tile = 1;
-    const float ms = time_it([&] {
-      fast_rows<T>(disc, varnu, OP_FULL, lv.g, lv.op[OP_FULL], ftab<T>(lv, OP_FULL), MODE_RES, xa, xa, xb, 1.0, sh,
-                   pb->stream);
-    });
-    bestS.row_tile = ms < best ? 1 : 0;
+  // the streaming kernels (stream.cu) against the best plain shape, for the
+  // FULL residual and the smoother's B^T and (B, -C) rows (threads per block),
+  // in the V-cycle precision and, for the mixed solve, the FP64 residual
+  {
+    const int sops[3] = {OP_FULL, OP_BT, OP_BC};
+    for (int o = 0; o < 3; ++o) {
+      Shape sh = bestS;
+      sh.st_threads[o] = 0;
+      float bo = time_it([&] {
+        fast_rows<T>(disc, varnu, sops[o], lv.g, lv.op[sops[o]], ftab<T>(lv, sops[o]), MODE_RES, xa, xa, xb, 1.0, sh,
+                     pb->stream);
+      });
+      for (int t : threads) {
+        sh.st_threads[o] = t;
+        if (!stream_op<T>(pb, lv, sh, sops[o], MODE_RES, xa, xa, xb)) continue;
+        const float ms = time_it([&] { stream_op<T>(pb, lv, sh, sops[o], MODE_RES, xa, xa, xb); });
+        if (ms < bo) { bo = ms; bestS.st_threads[o] = t; }
+      }
+      if (std::is_same<T, double>::value) bestS.st64_threads[o] = bestS.st_threads[o];
+    }
+    if (!std::is_same<T, double>::value) {
+      Shape sh = bestS;
+      sh.st64_threads[0] = 0;
+      float bo = time_it([&] {
+        fast_rows<double>(disc, varnu, OP_FULL, lv.g, lv.op[OP_FULL], ftab<double>(lv, OP_FULL), MODE_RES, lv.tmp64,
+                          lv.tmp64, lv.bw64, 1.0, sh, pb->stream);
+      });
+      for (int t : threads) {
+        sh.st64_threads[0] = t;
+        if (!stream_op<double>(pb, lv, sh, OP_FULL, MODE_RES, lv.tmp64, lv.tmp64, lv.bw64)) continue;
+        const float ms = time_it([&] { stream_op<double>(pb, lv, sh, OP_FULL, MODE_RES, lv.tmp64, lv.tmp64, lv.bw64); });
+        if (ms < bo) { bo = ms; bestS.st64_threads[0] = t; }
+      }
+    }
   }
   // Gauss-Seidel kernels: one forward sweep, 1, 2 or 4 lanes per site; the
   // lanes of the vertex colours and of the edge groups are then chosen apart
@@ -1789,6 +1907,25 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
     bestS.gs_threads0 = tv0;
     bestS.gs_lanes = le;
     bestS.gs_threads = te;
+  }
+  // launch order of a smoothing step's phases: every phase on all three
+  // components, or component by component (two forward sweeps each)
+  {
+    auto sweeps = [&](const Shape& sh) {
+      for (int c = sh.gs_comp_major ? 0 : -1; c < (sh.gs_comp_major ? 3 : 0); ++c)
+        for (int r = 0; r < 2; ++r) {
+          for (int cc = 0; cc < 4; ++cc)
+            fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), 0, cc, 1.0, xb, xa, sh, pb->stream, c);
+          for (int gg = 1; gg < lv.g.G; ++gg)
+            fast_gs<T>(disc, varnu, lv.g, ftab<T>(lv, OP_A), gg, -1, 1.0, xb, xa, sh, pb->stream, c);
+        }
+    };
+    Shape sh = bestS;
+    sh.gs_comp_major = 0;
+    const float m0 = time_it([&] { sweeps(sh); });
+    sh.gs_comp_major = 1;
+    const float m1 = time_it([&] { sweeps(sh); });
+    bestS.gs_comp_major = m1 < m0 ? 1 : 0;
   }
   lv.shape = bestS;
   cudaEventDestroy(e0);
@@ -1854,7 +1991,7 @@ extern "C" int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out) {
       o[0] = lv.shape.row_threads; o[1] = lv.shape.row_kplanes; o[2] = lv.shape.gs_threads;
       o[3] = lv.rctas[mixed ? HHG_FP32 : HHG_FP64];
       o[4] = lv.rthreads[mixed ? HHG_FP32 : HHG_FP64];
-      o[5] = lv.shape.row_tile;
+      o[5] = lv.shape.st_threads[0];
       o[6] = lv.shape.row_sites;
       o[7] = lv.shape.gs_lanes;
       o[8] = lv.shape.gs_lanes0;

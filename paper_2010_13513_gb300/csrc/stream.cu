@@ -1,0 +1,591 @@
+// Streaming stencil rows: y = calA x and r = b - calA x over all rows of the
+// operator (Eq. stokes-discrete), and the B^T and (B, -C) rows of the inexact
+// Uzawa smoother (Sec. 3.2), on levels large enough to fill the GPU.
+//
+// Data reuse.  In the Kuhn-lattice layout an input value x(a, site) is read
+// by the rows of every DoF group at about 27 neighbouring sites, so a kernel
+// that loads every term on its own moves each input value from L2 into the SM
+// many times.  Here a block owns M consecutive positions of the flattened
+// (i, j) plane (M = 4 x threads; a thread owns four consecutive positions,
+// one 16-byte aligned quad, since the j pitch sx is a multiple of four) and a
+// run of consecutive k planes, and marches through the run plane by plane:
+//   * planes k-1, k, k+1 of the staged input arrays sit in a ring of four
+//     shared-memory buffers (positions [m0 - sx - 4, m0 + M + sx + 4) of each
+//     plane: the tile plus one lattice row and one quad of halo), and the
+//     fourth buffer is filled with plane k+2 by cp.async while plane k is
+//     evaluated, so every input value crosses from HBM/L2 once per pass;
+//   * a thread loads each line (array, dj, dk) of its stencil footprint once
+//     per plane -- a 16-byte shared load of its quad, and the i-1 / i+4
+//     neighbours from the neighbouring lanes by shuffles -- and applies every
+//     term of every row that reads that line to its four sites from
+//     registers.
+// The plan (which arrays a pass stages, which rows it evaluates, the terms of
+// each line with their row, segment and weight index) is emitted at build
+// time by gen_structure.cpp from the stencil builder: every term is a
+// compile-time register operation with a constant-bank weight.  Operators
+// that read more than nine arrays (P2-P1: the full operator and B u - C p)
+// take one launch per velocity component; the pressure row's first pass
+// writes it and the later passes add their terms to it.
+//
+// Work split: the grid is one wave of blocks (the blocks that fit on the GPU
+// at once); the (tile, plane) pairs of a pass, tile by tile, are cut into
+// equal runs, one per block, so no block waits for a second wave.
+//
+// Rows on the domain boundary: velocity Dirichlet rows are 0; pressure rows
+// keep the merged B terms (exact for inputs with zero Dirichlet velocity
+// entries) and take their C terms from the clipped stencil of their boundary
+// class (whether each of i, j, k lies on a low face, inside or on a high
+// face: 27 classes), whose weights the library sums from the per-cube terms
+// of the generic tables.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
+#include <utility>
+
+#include "fast.h"
+#include "internal.h"
+#include "kernels.h"
+#include "stream.h"
+#include "structure.inc"
+
+namespace hhg {
+namespace {
+
+// ------------------------------------------------------------ cp.async
+__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// the four values of a quad (16-byte aligned; two 16-byte loads for double)
+template <class T>
+__device__ __forceinline__ void load_quad(const T* p, T (&w)[6]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    w[1] = v.x; w[2] = v.y; w[3] = v.z; w[4] = v.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 c = *reinterpret_cast<const double2*>(p + 2);
+    w[1] = a.x; w[2] = a.y; w[3] = c.x; w[4] = c.y;
+  }
+}
+
+// ------------------------------------------------------ compile-time plan
+template <class SPT, int Q>
+constexpr int pass_e0() { return SPT::lines[SPT::passes[Q].l0].e0; }
+template <class SPT, int Q>
+constexpr int pass_e1() {
+  return SPT::lines[SPT::passes[Q].l0 + SPT::passes[Q].nl - 1].e0 +
+         SPT::lines[SPT::passes[Q].l0 + SPT::passes[Q].nl - 1].ne;
+}
+// whether part P of pass Q has C terms (segment 2)
+template <class SPT, int Q, int P>
+constexpr bool part_has_c() {
+  for (int e = pass_e0<SPT, Q>(); e < pass_e1<SPT, Q>(); ++e)
+    if (SPT::terms[e].part == P && SPT::terms[e].seg == 2) return true;
+  return false;
+}
+// shared-memory slot of input array A in pass Q (-1 if not staged)
+template <class SPT, int Q, int A>
+constexpr int slot_of() {
+  for (int a = 0; a < SPT::passes[Q].na; ++a)
+    if (SPT::arrs[SPT::passes[Q].a0 + a] == A) return a;
+  return -1;
+}
+
+template <int OG> struct Par {
+  static constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
+  static constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
+  static constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
+};
+
+// accumulators of a pass: row r = 3 * part + segment, four sites each
+template <class T, int NA> struct Acc {
+  T a[NA][4];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < NA; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = T(0);
+  }
+  __device__ __forceinline__ void get(int r, T (&v)[4]) const {
+    v[0] = a[r][0]; v[1] = a[r][1]; v[2] = a[r][2]; v[3] = a[r][3];
+  }
+};
+
+// ----------------------------------------------------------- term evaluation
+// with a constant viscosity the first two segments of a row (unscaled) share
+// one accumulator; the C terms (segment 2) keep their own, which the clipped
+// boundary stencil replaces on boundary pressure rows.  Every term is four
+// FMAs with the weight from the constant bank.
+template <class SPT, int E, int VARNU, class T, class Tab, int NA>
+__device__ __forceinline__ void term_fma(const T (&w)[6], Acc<T, NA>& acc, const Tab& tab) {
+  constexpr gen::TermE te = SPT::terms[E];
+  constexpr int a = 3 * te.part + (VARNU || te.seg == 2 ? te.seg : 0);
+  const T wt = tab.w[te.t];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) acc.a[a][s] = fma(wt, w[te.di + 1 + s], acc.a[a][s]);
+}
+
+template <class SPT, int E0, int VARNU, class T, class Tab, int NA, int... I>
+__device__ __forceinline__ void line_terms(const T (&w)[6], Acc<T, NA>& acc, const Tab& tab,
+                                           std::integer_sequence<int, I...>) {
+  (term_fma<SPT, E0 + I, VARNU>(w, acc, tab), ...);
+}
+
+// shared-memory buffer of plane kp (ring of four)
+__device__ __forceinline__ int64_t buf_of(int kp, int64_t bufsz) { return ((kp + 1) & 3) * bufsz; }
+
+// shared-memory loads with 32-bit shared addresses: a quad, and one value
+// loaded by one lane only (predicated, no branch)
+__device__ __forceinline__ void lds_quad(uint32_t a, float (&w)[6]) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(w[1]), "=f"(w[2]), "=f"(w[3]), "=f"(w[4]) : "r"(a));
+}
+__device__ __forceinline__ void lds_quad(uint32_t a, double (&w)[6]) {
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(w[1]), "=d"(w[2]) : "r"(a));
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(w[3]), "=d"(w[4]) : "r"(a + 16));
+}
+__device__ __forceinline__ void lds_if(bool on, uint32_t a, float& v) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f32 %0, [%2];\n}"
+               : "+f"(v) : "r"(unsigned(on)), "r"(a));
+}
+__device__ __forceinline__ void lds_if(bool on, uint32_t a, double& v) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f64 %0, [%2];\n}"
+               : "+d"(v) : "r"(unsigned(on)), "r"(a));
+}
+
+// one line (slot, dj, dk): the thread's quad and the neighbours the line's
+// terms need, then every term of the line.  pb[dk + 1] is the shared address
+// of the thread's quad in slot 0 of plane k + dk; lwb, sxb: the slot and row
+// strides in bytes.
+template <class SPT, int L, int VARNU, class T, class Tab, int NA>
+__device__ __forceinline__ void eval_line(const uint32_t (&pb)[3], int lwb, int sxb, int lane, Acc<T, NA>& acc,
+                                          const Tab& tab) {
+  constexpr gen::LineT ln = SPT::lines[L];
+  constexpr int es = int(sizeof(T));
+  const uint32_t a = pb[ln.dk + 1] + uint32_t(ln.slot * lwb + ln.dj * sxb);
+  T w[6];
+  lds_quad(a, w);
+  if constexpr (ln.lmin < 0) {
+    T v = __shfl_up_sync(0xffffffffu, w[4], 1);
+    lds_if(lane == 0, a - es, v);
+    w[0] = v;
+  }
+  if constexpr (ln.lmax > 0) {
+    T v = __shfl_down_sync(0xffffffffu, w[1], 1);
+    lds_if(lane == 31, a + 4 * es, v);
+    w[5] = v;
+  }
+  line_terms<SPT, ln.e0, VARNU>(w, acc, tab, std::make_integer_sequence<int, ln.ne>{});
+}
+
+template <class SPT, int L0, int VARNU, class T, class Tab, int NA, int... I>
+__device__ __forceinline__ void eval_lines(const uint32_t (&pb)[3], int lwb, int sxb, int lane, Acc<T, NA>& acc,
+                                           const Tab& tab, std::integer_sequence<int, I...>) {
+  (eval_line<SPT, L0 + I, VARNU>(pb, lwb, sxb, lane, acc, tab), ...);
+}
+
+// C terms of a boundary pressure row at site (i, j, k), staged position lf:
+// the clipped stencil of the site's boundary class applied to the pressure
+// values in shared memory (slot SLOTP)
+template <class SPT, int SLOTP, class T, class Tab, int... O>
+__device__ __forceinline__ T boundary_c(const Geo& g, const T* sm, int64_t bufsz, int lw, int lf, int i, int j, int k,
+                                        const Tab& tab, std::integer_sequence<int, O...>) {
+  const int cls = (i == 0 ? 0 : i == g.nx ? 2 : 1) + 3 * (j == 0 ? 0 : j == g.ny ? 2 : 1) +
+                  9 * (k == 0 ? 0 : k == g.nz ? 2 : 1);
+  const T* wc = tab.wc + cls * SPT::NCB;
+  T a = T(0);
+  ((a += wc[O] * sm[buf_of(k + SPT::cbo[O].dk, bufsz) + SLOTP * lw + lf + SPT::cbo[O].dj * g.sx + SPT::cbo[O].di]),
+   ...);
+  return a;
+}
+
+// --------------------------------------------------------------- outputs
+// the rows of part P at the thread's four sites (positions fk .. fk + 3 of
+// the k plane: coarse indices (i0 .. i0 + 3, j, k)), written to y as one
+// quad.  Positions of the quad outside the group's sites (the halo column,
+// the row padding) and Dirichlet velocity rows are written as 0: halo,
+// padding and Dirichlet entries of every vector are 0, so the quad store
+// never changes them.
+template <class SPT, int Q, int P, int VARNU, int PSLOT, class T, int MODE, class Tab, int NA>
+__device__ __forceinline__ void store_part(const Geo& g, const T* __restrict__ b, T* __restrict__ y, const T* sm,
+                                           int64_t bufsz, int lw, int lf, int k, int i0, int j, int64_t fk, T es, T eis,
+                                           const Acc<T, NA>& acc, const Tab& tab) {
+  constexpr gen::PartT pt = SPT::parts[SPT::passes[Q].p0 + P];
+  constexpr bool HAS_C = part_has_c<SPT, Q, P>();
+  using PP = Par<pt.og>;
+  if (j < 0 || j > g.ny - PP::oy || k > g.nz - PP::oz) return;
+  const bool bjk = 2 * j + PP::oy == 0 || 2 * j + PP::oy == 2 * g.ny || 2 * k + PP::oz == 0 ||
+                   2 * k + PP::oz == 2 * g.nz;
+  T a0[4], a1[4], a2[4], v[4];
+  acc.get(3 * P, a0);
+  if (VARNU) acc.get(3 * P + 1, a1);
+  if (HAS_C) acc.get(3 * P + 2, a2);
+  bool keep[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    v[s] = a0[s];
+    if (VARNU) v[s] += es * a1[s];
+    if (HAS_C) v[s] += VARNU ? eis * a2[s] : a2[s];
+    const int i = i0 + s;
+    const bool bnd = bjk || 2 * i + PP::ox == 0 || 2 * i + PP::ox == 2 * g.nx;
+    keep[s] = i >= 0 && i <= g.nx - PP::ox && (pt.all || !bnd);
+    if constexpr (HAS_C) {
+      if (keep[s] && bnd) {                            // boundary pressure row: clipped C stencil
+        static_assert(PSLOT >= 0, "the pressure array is staged with the C terms");
+        const T c = boundary_c<SPT, PSLOT, T>(g, sm, bufsz, lw, lf + s, i, j, k, tab,
+                                              std::make_integer_sequence<int, SPT::NCB>{});
+        v[s] = VARNU ? a0[s] + es * a1[s] + eis * c : a0[s] + c;
+      }
+    }
+  }
+  const int64_t iy = int64_t(pt.out) * g.arr + fk;
+  T o[4];
+  if (pt.first) {
+    if (MODE == MODE_RES) {
+      T bb[4];
+      if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(b + iy);
+        bb[0] = q.x; bb[1] = q.y; bb[2] = q.z; bb[3] = q.w;
+      } else {
+        const double2 q0 = *reinterpret_cast<const double2*>(b + iy);
+        const double2 q1 = *reinterpret_cast<const double2*>(b + iy + 2);
+        bb[0] = q0.x; bb[1] = q0.y; bb[2] = q1.x; bb[3] = q1.y;
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) o[s] = keep[s] ? bb[s] - v[s] : T(0);
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) o[s] = keep[s] ? v[s] : T(0);
+    }
+  } else {
+    T c[4];
+    if constexpr (sizeof(T) == 4) {
+      const float4 q = *reinterpret_cast<const float4*>(y + iy);
+      c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
+    } else {
+      const double2 q0 = *reinterpret_cast<const double2*>(y + iy);
+      const double2 q1 = *reinterpret_cast<const double2*>(y + iy + 2);
+      c[0] = q0.x; c[1] = q0.y; c[2] = q1.x; c[3] = q1.y;
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) o[s] = keep[s] ? (MODE == MODE_RES ? c[s] - v[s] : c[s] + v[s]) : c[s];
+  }
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(y + iy) = make_float4(o[0], o[1], o[2], o[3]);
+  } else {
+    reinterpret_cast<double2*>(y + iy)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2*>(y + iy)[1] = make_double2(o[2], o[3]);
+  }
+}
+
+template <class SPT, int Q, int VARNU, int PSLOT, class T, int MODE, class Tab, int NA, int... I>
+__device__ __forceinline__ void store_parts(const Geo& g, const T* __restrict__ b, T* __restrict__ y, const T* sm,
+                                            int64_t bufsz, int lw, int lf, int k, int i0, int j, int64_t fk, T es,
+                                            T eis, const Acc<T, NA>& acc, const Tab& tab,
+                                            std::integer_sequence<int, I...>) {
+  (store_part<SPT, Q, I, VARNU, PSLOT, T, MODE>(g, b, y, sm, bufsz, lw, lf, k, i0, j, fk, es, eis, acc, tab), ...);
+}
+
+// cp.async of plane kp of the pass's arrays (array slot A at buf + A lw);
+// chunks outside the vector are skipped (they feed only positions whose rows
+// are not stored)
+template <class SPT, int Q, class T, int... A>
+__device__ __forceinline__ void stage_plane(const T* __restrict__ x, T* buf, int64_t pbase, int64_t arr, int64_t vlen,
+                                            int lw, int nch, int tid, int nt, std::integer_sequence<int, A...>) {
+  constexpr int VE = 16 / int(sizeof(T));
+  auto one = [&](int slot, int64_t base) {
+    T* dst = buf + slot * lw;
+    if (base >= 0 && base + lw <= vlen) {            // the whole line lies in the vector (all but the ends)
+      const T* src = x + base;
+      for (int c = tid; c < nch; c += nt) cp16(dst + c * VE, src + c * VE);
+    } else {
+      for (int c = tid; c < nch; c += nt) {
+        const int64_t e = base + int64_t(c) * VE;
+        if (e >= 0 && e + VE <= vlen) cp16(dst + c * VE, x + e);
+      }
+    }
+  };
+  (one(A, int64_t(std::integral_constant<int, SPT::arrs[SPT::passes[Q].a0 + A]>::value) * arr + pbase), ...);
+}
+
+// ------------------------------------------------------------------ a pass
+// grid: one wave of blocks.  kc > 0 (lockstep): block b takes tile b % tiles
+// and planes [c kc, (c + 1) kc) with c = b / tiles, so that blocks on
+// neighbouring tiles march through the same planes at the same time and the
+// halo rows they share come from L2.  kc = 0 (balanced): block b takes the
+// (tile, plane) pairs [b U / grid, (b + 1) U / grid) of the U = tiles x
+// (nz + 1) pairs, tile by tile.  On each tile a block marches through its
+// planes.
+template <int DISC, int VARNU, int OP, int Q, class T, int MODE, class Tab>
+__global__ void __launch_bounds__(256, 2)
+    k_stream(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, int lw, int64_t units,
+             int64_t tiles, int kc, const __grid_constant__ Tab tab) {
+  using SPT = gen::SP<DISC, VARNU, OP>;
+  constexpr gen::PassT ps = SPT::passes[Q];
+  constexpr int PSLOT = slot_of<SPT, Q, (DISC == 2 ? 24 : 3)>();
+  constexpr int VE = 16 / int(sizeof(T));
+  extern __shared__ __align__(16) unsigned char stream_smem[];
+  T* sm = reinterpret_cast<T*>(stream_smem);
+  const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(stream_smem));
+  const int tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
+  const int M = 4 * nt, sx = g.sx;
+  const int nk = g.nz + 1;
+  const int nch = lw / VE;
+  const int64_t vlen = int64_t(3 * g.G + 1) * g.arr;
+  const int64_t bufsz = int64_t(SPT::NAMAX) * lw;
+  const int lf = 4 * tid + sx + 4;                   // the thread's quad in a staged line
+  int64_t u, uend;
+  if (kc > 0) {
+    const int64_t t = blockIdx.x % tiles, c = blockIdx.x / tiles;
+    u = t * nk + min(int64_t(nk), c * kc);
+    uend = t * nk + min(int64_t(nk), (c + 1) * kc);
+  } else {
+    u = int64_t(blockIdx.x) * units / gridDim.x;
+    uend = int64_t(blockIdx.x + 1) * units / gridDim.x;
+  }
+#pragma unroll 1
+  while (u < uend) {
+    const int64_t tile = u / nk;
+    const int k0 = int(u - tile * nk);
+    const int k1 = int(k0 + min(int64_t(nk - k0), uend - u));
+    u += k1 - k0;
+    const int64_t m0 = int64_t(sx) + tile * M;
+    const int64_t gbase = m0 - sx - 4;
+    const int64_t f = m0 + 4 * tid;                    // the thread's quad
+    const int j = int(f / sx) - 1;
+    const int i0 = int(f - int64_t(j + 1) * sx) - 1;
+    auto load = [&](int kp) {
+      stage_plane<SPT, Q>(x, sm + buf_of(kp, bufsz), int64_t(kp + 1) * g.sy + gbase, g.arr, vlen, lw, nch, tid, nt,
+                          std::make_integer_sequence<int, ps.na>{});
+    };
+    __syncthreads();                                   // the previous run no longer reads the ring
+    load(k0 - 1);
+    cp_commit();
+    load(k0);
+    cp_commit();
+    load(k0 + 1);
+    cp_commit();
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+      if (k + 1 < k1) load(k + 2);
+      cp_commit();
+      cp_wait1();                                      // planes k-1, k, k+1 are in place (this thread's copies)
+      __syncthreads();                                 // ... and every thread's
+      Acc<T, 3 * ps.np> acc;
+      acc.zero();
+      const uint32_t pb[3] = {sbase + uint32_t(buf_of(k - 1, bufsz) + lf) * uint32_t(sizeof(T)),
+                              sbase + uint32_t(buf_of(k, bufsz) + lf) * uint32_t(sizeof(T)),
+                              sbase + uint32_t(buf_of(k + 1, bufsz) + lf) * uint32_t(sizeof(T))};
+      eval_lines<SPT, ps.l0, VARNU>(pb, lw * int(sizeof(T)), sx * int(sizeof(T)), lane, acc, tab,
+                                    std::make_integer_sequence<int, ps.nl>{});
+      T es = T(1), eis = T(1);
+      if (VARNU) {
+        es = T(g.esc[k]);
+        eis = T(g.eisc[k]);
+      }
+      store_parts<SPT, Q, VARNU, PSLOT, T, MODE>(g, b, y, sm, bufsz, lw, lf, k, i0, j, int64_t(k + 1) * g.sy + f, es,
+                                                 eis, acc, tab, std::make_integer_sequence<int, ps.np>{});
+      __syncthreads();                                 // plane k-1's buffer is refilled next
+    }
+    cp_wait0();
+  }
+}
+
+// --------------------------------------------------------- launch support
+// parameter block of the streaming kernels of one operator
+template <class T, int N, int NCB> struct STab {
+  T w[N];                             // weights, in the order of the FastTab images
+  T wc[NCB > 0 ? 27 * NCB : 1];       // clipped boundary C stencils per class
+};
+
+template <int DISC, int VARNU, int OP, class T>
+using STabOf = STab<T, gen::S<DISC, VARNU, OP>::N, gen::SP<DISC, VARNU, OP>::NCB>;
+
+size_t smem_bytes(int namax, const Geo& g, int threads, size_t es) {
+  return size_t(4) * namax * size_t(4 * threads + 2 * g.sx + 8) * es;
+}
+
+// blocks of a kernel that fit on one SM, and the SM count (cached)
+int blocks_per_sm(const void* fn, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_tuple(fn, threads, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  cache[key] = n;
+  return n;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      n = 132;
+    }
+  }
+  return n;
+}
+
+template <int DISC, int VARNU, int OP, int Q, class T, int MODE>
+bool launch_pass(const Geo& g, const void* tab, const T* x, const T* b, T* y, int threads, cudaStream_t s) {
+  using SPT = gen::SP<DISC, VARNU, OP>;
+  using Tab = STabOf<DISC, VARNU, OP, T>;
+  const Tab& tb = *static_cast<const Tab*>(tab);
+  const size_t smem = smem_bytes(SPT::NAMAX, g, threads, sizeof(T));
+  auto fn = k_stream<DISC, VARNU, OP, Q, T, MODE, Tab>;
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(fn), threads, smem);
+  if (per_sm < 1) return false;
+  const int M = 4 * threads;
+  const int64_t tiles = (int64_t(g.ny + 1) * g.sx + M - 1) / M;
+  const int nk = g.nz + 1;
+  const int64_t units = tiles * nk;
+  const int64_t resident = int64_t(per_sm) * sm_count();
+  int64_t grid = std::min<int64_t>(units, resident);
+  int kc = 0;
+  // lockstep chunks if they fill at least 85 % of the resident blocks
+  const int64_t chunks = resident / tiles;
+  if (chunks >= 1 && tiles * chunks * 100 >= 85 * resident) {
+    kc = int((nk + chunks - 1) / chunks);
+    grid = tiles * ((nk + kc - 1) / kc);
+  }
+  ++g_launches;
+  fn<<<unsigned(grid), threads, smem, s>>>(g, x, b, y, int(M + 2 * g.sx + 8), units, tiles, kc, tb);
+  return true;
+}
+
+template <int DISC, int VARNU, int OP, class T, int MODE, int... Q>
+void launch_passes(const Geo& g, const void* tab, const T* x, const T* b, T* y, int threads, cudaStream_t s,
+                   std::integer_sequence<int, Q...>) {
+  (launch_pass<DISC, VARNU, OP, Q, T, MODE>(g, tab, x, b, y, threads, s), ...);
+}
+
+template <int DISC, int VARNU, int OP, class T>
+bool launch_stream(const Geo& g, const void* tab, int mode, const T* x, const T* b, T* y, int threads,
+                   cudaStream_t s) {
+  using SPT = gen::SP<DISC, VARNU, OP>;
+  if ((threads != 64 && threads != 128 && threads != 256) || (g.sx & 3) || (g.arr & 3)) return false;
+  // quads are read and written as 16-byte vectors
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(b)) & 15)
+    return false;
+  if (smem_bytes(SPT::NAMAX, g, threads, sizeof(T)) > kStreamMaxSmem) return false;
+  if (mode == MODE_SET)
+    launch_passes<DISC, VARNU, OP, T, MODE_SET>(g, tab, x, b, y, threads, s, std::make_integer_sequence<int, SPT::NP>{});
+  else
+    launch_passes<DISC, VARNU, OP, T, MODE_RES>(g, tab, x, b, y, threads, s, std::make_integer_sequence<int, SPT::NP>{});
+  return true;
+}
+
+template <int DISC, int VARNU, int OP, class T, int... Q>
+void init_passes(std::integer_sequence<int, Q...>) {
+  using Tab = STabOf<DISC, VARNU, OP, T>;
+  ((cudaFuncSetAttribute(k_stream<DISC, VARNU, OP, Q, T, MODE_SET, Tab>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(kStreamMaxSmem)),
+    cudaFuncSetAttribute(k_stream<DISC, VARNU, OP, Q, T, MODE_RES, Tab>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(kStreamMaxSmem))),
+   ...);
+}
+
+template <int DISC, int VARNU, int OP, class T>
+void init_stream() {
+  init_passes<DISC, VARNU, OP, T>(std::make_integer_sequence<int, gen::SP<DISC, VARNU, OP>::NP>{});
+}
+
+// the parameter block from the weights (FastTab order) and the class sums of
+// the boundary C stencils (27 x NCB, offsets in the order of cbo)
+template <int DISC, int VARNU, int OP, class T>
+void make_image(const std::vector<double>& w, const std::vector<double>& wc, std::vector<char>& out) {
+  using SPT = gen::SP<DISC, VARNU, OP>;
+  using Tab = STabOf<DISC, VARNU, OP, T>;
+  out.assign(sizeof(Tab), 0);
+  Tab* t = reinterpret_cast<Tab*>(out.data());
+  const int N = gen::S<DISC, VARNU, OP>::N;
+  for (int i = 0; i < N && i < int(w.size()); ++i) t->w[i] = T(w[i]);
+  for (int i = 0; i < 27 * SPT::NCB && i < int(wc.size()); ++i) t->wc[i] = T(wc[i]);
+}
+
+template <int DISC, int VARNU, int OP>
+void offsets_of(std::vector<int>& o) {
+  using SPT = gen::SP<DISC, VARNU, OP>;
+  o.clear();
+  if constexpr (SPT::NCB > 0)
+    for (int i = 0; i < SPT::NCB; ++i) {
+      o.push_back(SPT::cbo[i].di);
+      o.push_back(SPT::cbo[i].dj);
+      o.push_back(SPT::cbo[i].dk);
+    }
+}
+
+}  // namespace
+
+#define HHG_STREAM_CASES(X) \
+  X(1, 0, OP_FULL) X(1, 0, OP_BT) X(1, 0, OP_BC) X(1, 1, OP_FULL) X(1, 1, OP_BT) X(1, 1, OP_BC) \
+  X(2, 0, OP_FULL) X(2, 0, OP_BT) X(2, 0, OP_BC) X(2, 1, OP_FULL) X(2, 1, OP_BT) X(2, 1, OP_BC)
+
+template <class T>
+bool stream_rows(int disc, int varnu, int op, int mode, const Geo& g, const void* tab, const T* x, const T* b, T* y,
+                 int threads, cudaStream_t s) {
+  if (mode != MODE_SET && mode != MODE_RES) return false;
+#define HHG_S(D, V, O) \
+  if (disc == D && varnu == V && op == O) return launch_stream<D, V, O, T>(g, tab, mode, x, b, y, threads, s);
+  HHG_STREAM_CASES(HHG_S)
+#undef HHG_S
+  return false;
+}
+
+template <class T>
+void stream_init() {
+#define HHG_I(D, V, O) init_stream<D, V, O, T>();
+  HHG_STREAM_CASES(HHG_I)
+#undef HHG_I
+}
+
+template <class T>
+bool stream_image(int disc, int varnu, int op, const std::vector<double>& w, const std::vector<double>& wc,
+                  std::vector<char>& out) {
+#define HHG_M(D, V, O) \
+  if (disc == D && varnu == V && op == O) { make_image<D, V, O, T>(w, wc, out); return true; }
+  HHG_STREAM_CASES(HHG_M)
+#undef HHG_M
+  return false;
+}
+
+#if !defined(HHG_STREAM_ONLY) || HHG_STREAM_ONLY == 64
+bool stream_c_offsets(int disc, int varnu, int op, std::vector<int>& offsets) {
+#define HHG_O(D, V, O) \
+  if (disc == D && varnu == V && op == O) { offsets_of<D, V, O>(offsets); return true; }
+  HHG_STREAM_CASES(HHG_O)
+#undef HHG_O
+  return false;
+}
+template bool stream_rows<double>(int, int, int, int, const Geo&, const void*, const double*, const double*, double*,
+                                  int, cudaStream_t);
+template void stream_init<double>();
+template bool stream_image<double>(int, int, int, const std::vector<double>&, const std::vector<double>&,
+                                   std::vector<char>&);
+#endif
+#if !defined(HHG_STREAM_ONLY) || HHG_STREAM_ONLY == 32
+template bool stream_rows<float>(int, int, int, int, const Geo&, const void*, const float*, const float*, float*, int,
+                                 cudaStream_t);
+template void stream_init<float>();
+template bool stream_image<float>(int, int, int, const std::vector<double>&, const std::vector<double>&,
+                                  std::vector<char>&);
+#endif
+
+}  // namespace hhg

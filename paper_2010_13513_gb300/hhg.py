@@ -106,6 +106,8 @@ def load():
         "hhg_set_launch_shape": [P, I, I, I, I, I, I, I],
         "hhg_get_launch_shape": [P, I, C.POINTER(C.c_int)],
         "hhg_get_level_smoother": [P, I, I, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "hhg_set_level_sweep_order": [P, I, I],
+        "hhg_get_level_sweep_order": [P, I, C.POINTER(C.c_int)],
         "hhg_error_norms": [P, I, VP, DP, DP, DP, DP],
         "hhg_block_norms_noalloc": [VP, I, C.c_int64, C.c_int64, VP, VP],
         "hhg_batch_create": [C.POINTER(P), I, C.POINTER(P)],
@@ -380,20 +382,24 @@ class Problem:
 
     def autotune(self, reps=5):
         """Per-level launch choices; returns {level: (row_threads,
-        row_kplanes, gs_threads, resident_ctas, resident_threads, row_tile,
-        row_sites, gs_lanes, gs_lanes_vertex, bt_threads, bt_kplanes, bt_sites,
-        bc_threads, bc_kplanes, bc_sites, gs_threads_vertex)}."""
+        row_kplanes, gs_threads, resident_ctas, resident_threads,
+        stream_threads, row_sites, gs_lanes, gs_lanes_vertex, bt_threads,
+        bt_kplanes, bt_sites, bc_threads, bc_kplanes, bc_sites,
+        gs_threads_vertex)}; stream_threads is the block size of the
+        streaming kernel of the full operator (0: the plain kernels)."""
         n = self.L - self.lc + 1
         out = (C.c_int * (16 * n))()
         _check(load().hhg_autotune(self.h, reps, out), "hhg_autotune")
         return {self.lc + i: tuple(out[16 * i:16 * i + 16]) for i in range(n)}
 
     def set_launch_shape(self, level, row_threads, row_kplanes, gs_threads, row_tile=0, row_sites=1, gs_lanes=1):
+        """row_tile: 0 = plain row kernels; 64/128/256 = the streaming kernels
+        with that many threads per block (levels with nx >= 64)."""
         _check(load().hhg_set_launch_shape(self.h, level, row_threads, row_kplanes, gs_threads, int(row_tile),
                                            int(row_sites), int(gs_lanes)), "hhg_set_launch_shape")
 
     def launch_shape(self, level):
-        """(row_threads, row_kplanes, gs_threads, row_tile, row_sites, gs_lanes) of a level."""
+        """(row_threads, row_kplanes, gs_threads, stream_threads, row_sites, gs_lanes) of a level."""
         out = (C.c_int * 6)()
         _check(load().hhg_get_launch_shape(self.h, level, out), "hhg_get_launch_shape")
         return tuple(out)
@@ -417,6 +423,16 @@ class Problem:
         c, t = C.c_int(), C.c_int()
         _check(load().hhg_get_level_smoother(self.h, level, p, C.byref(c), C.byref(t)), "hhg_get_level_smoother")
         return c.value, t.value
+
+    def set_sweep_order(self, level, order):
+        """0: every Gauss-Seidel phase on the three components; 1: component
+        by component (same iterates)."""
+        _check(load().hhg_set_level_sweep_order(self.h, level, int(order)), "hhg_set_level_sweep_order")
+
+    def sweep_order(self, level):
+        o = C.c_int()
+        _check(load().hhg_get_level_sweep_order(self.h, level, C.byref(o)), "hhg_get_level_sweep_order")
+        return o.value
 
     def estimate_omega(self, level, v0, iters=100):
         v = np.ascontiguousarray(v0, dtype=np.float64)

@@ -60,7 +60,8 @@ def test_rhs_parity(disc, box, L, lc):
 def test_set_rhs_levels_matches_per_level():
     """hhg_set_rhs_levels (every level queued, one synchronisation) assembles
     the same right-hand sides, bit for bit, as hhg_set_rhs level by level; an
-    empty level range is rejected."""
+    empty level range and a range with an invalid level or pointer are
+    rejected without changing any level."""
     import ctypes as C
     from hhg_inputs import Workload
     from paper_2010_13513_gb300 import hhg
@@ -78,7 +79,20 @@ def test_set_rhs_levels_matches_per_level():
     for l in (1, 2, 3):
         assert np.array_equal(pb.to_host(l, pb.level_vector(l, "rhs")), ref[l]), l
     dp = C.POINTER(C.c_double)
-    assert hhg.load().hhg_set_rhs_levels(pb.h, 3, 2, (dp * 1)(), (dp * 1)()) != 0
+    assert hhg.load().hhg_set_rhs_levels(pb.h, 3, 2, (dp * 1)(), (dp * 1)()) == -1
+    # a range that fails part-way (level 4 is beyond the hierarchy, or one
+    # inner pointer is null) is rejected before anything is queued: no level
+    # changes, although the earlier levels' data are valid
+    zf = [np.zeros_like(f) for f in fs] + [np.zeros_like(fs[-1])]
+    zw = [np.zeros_like(w) for w in ws] + [np.zeros_like(ws[-1])]
+    fp = (dp * 4)(*[hhg._dp(a) for a in zf])
+    wp = (dp * 4)(*[hhg._dp(a) for a in zw])
+    assert hhg.load().hhg_set_rhs_levels(pb.h, 1, 4, fp, wp) == -1
+    wp3 = (dp * 3)(*[hhg._dp(a) for a in zw[:3]])
+    wp3[2] = dp()
+    assert hhg.load().hhg_set_rhs_levels(pb.h, 1, 3, (dp * 3)(*[hhg._dp(a) for a in zf[:3]]), wp3) == -1
+    for l in (1, 2, 3):
+        assert np.array_equal(pb.to_host(l, pb.level_vector(l, "rhs")), ref[l]), l
 
 
 @pytest.mark.parametrize("disc,nu_a", [("P1P1", 0.0), ("P2P1", 0.0), ("P1P1", 1.5)])
@@ -190,36 +204,50 @@ def test_resident_smoother_every_cta_count(disc, L, nu_a, ahat, xi):
         assert rel(v, ref) < 1e-4
 
 
-@pytest.mark.parametrize("disc,box,L,nu_a", [("P2P1", (1, 1, 1), 3, 0.0), ("P2P1", (1, 2, 1), 3, 1.1),
-                                              ("P1P1", (1, 1, 2), 4, 0.0), ("P1P1", (2, 1, 1), 4, 1.4)])
-def test_tiled_rows_match_plain_rows(disc, box, L, nu_a):
-    """The shared-memory-tiled FP32 rows (full operator apply and residual,
-    the smoother's B^T and (B, -C) residual rows) give the plain kernels'
-    results, and the FP64 apply within FP32 rounding; tiles cover partial
-    32 x 4 x 4 blocks at the lattice edges."""
+@pytest.mark.parametrize("disc,box,L,nu_a", [("P2P1", (4, 1, 1), 4, 0.0), ("P2P1", (4, 1, 1), 4, 1.1),
+                                              ("P1P1", (4, 1, 2), 4, 0.0), ("P1P1", (4, 2, 1), 4, 0.9)])
+def test_stream_rows_match_oracle(disc, box, L, nu_a):
+    """The streaming row kernels (planes staged in shared memory, a quad of
+    sites per thread, one or three passes) on levels with nx = 64 (the pitch
+    of such levels is a multiple of four): the full operator and the B^T
+    block against the oracle in FP64 (1e-12), the residual and the per-phase
+    smoother's B^T and (B, -C) residual rows against the plain kernels (FP64
+    1e-14, FP32 1e-6), for 64/128/256 threads per block (FP64 P2-P1 with 256
+    threads exceeds the shared memory and falls back to the plain kernels)
+    and k chunks that do or do not divide the planes (the last chunk is
+    partial); the planes of 17 or 33 rows of 68 positions end in partial
+    tiles."""
     from paper_2010_13513_gb300 import hhg
     pb = lib_problem(box, L, disc, lc=1, nu_a=nu_a, solve="mixed")
     hy = oracle_hierarchy(box, L, disc, lc=1, nu_a=nu_a)
     lev = hy.lv[L]
+    assert pb.layout(L).sx % 4 == 0
     x, b = random_vector(lev, 21), random_vector(lev, 22)
-    x32, b32 = pb.to_device(L, x, prec=hhg.FP32), pb.to_device(L, b, prec=hhg.FP32)
+    ref, ref_bt = lev.apply(x), lev.apply_block("BT", x)
+    prm = hhg.Params.make(ahat="s", xi=1, omega_inv=OMEGA_INV[disc])
+    pb.set_level_smoother(L, 0, prec=hhg.FP64)
+    pb.set_level_smoother(L, 0, prec=hhg.FP32)
     out = {}
-    for tile in (0, 1):
-        pb.set_launch_shape(L, 128, 2, 128, tile)
-        assert pb.launch_shape(L)[3] == tile
-        y = pb.new_vector(L, hhg.FP32)
-        pb.apply(L, "FULL", x32, y)
-        r = pb.new_vector(L, hhg.FP32)
-        pb.residual(L, x32, b32, r)
-        xs = x32.clone()
-        pb.set_level_smoother(L, 0)                      # per-phase smoother: B^T and (B, -C) residual rows
-        pb.smooth(L, hhg.Params.make(ahat="f", xi=1, omega_inv=OMEGA_INV[disc]), 1, xs, b32)
-        out[tile] = [pb.to_host(L, v) for v in (y, r, xs)]
-    for a, c in zip(out[0], out[1]):
-        assert rel(c, a) < 1e-6
-    y64 = pb.new_vector(L)
-    pb.apply(L, "FULL", pb.to_device(L, x), y64)
-    assert rel(out[1][0], pb.to_host(L, y64)) < 1e-5
+    for st, kc in ((0, 2), (64, 3), (128, 16), (256, 5), (128, 1)):
+        pb.set_launch_shape(L, 128, kc, 128, st)
+        assert pb.launch_shape(L)[3] == st
+        res = []
+        for prec in (hhg.FP64, hhg.FP32):
+            xd, bd = pb.to_device(L, x, prec=prec), pb.to_device(L, b, prec=prec)
+            y, ybt, r = pb.new_vector(L, prec), pb.new_vector(L, prec), pb.new_vector(L, prec)
+            pb.apply(L, "FULL", xd, y)
+            pb.apply(L, "BT", xd, ybt)
+            pb.residual(L, xd, bd, r)
+            pb.smooth(L, prm, 1, xd, bd)
+            res += [pb.to_host(L, v) for v in (y, ybt, r, xd)]
+        assert rel(res[0], ref) < 1e-12, (st, kc, rel(res[0], ref))
+        assert rel(res[1], ref_bt) < 1e-12, (st, kc, rel(res[1], ref_bt))
+        assert rel(res[4], ref) < 1e-5
+        out[(st, kc)] = res
+    base = out[(0, 2)]
+    for key, res in out.items():
+        for n, (a, c) in enumerate(zip(res, base)):
+            assert rel(a, c) < (1e-14 if n < 4 else 1e-6), (key, n, rel(a, c))
 
 
 @pytest.mark.parametrize("disc,box,L,nu_a", [("P2P1", (1, 1, 1), 4, 0.0), ("P2P1", (2, 1, 1), 3, 1.1),
@@ -497,7 +525,7 @@ def test_autotune_keeps_results():
     assert set(shapes) == {1, 2, 3, 4}
     for t, kp, gs, rc, rt, tile, sites, lanes, lanes_v, btt, btk, bts, bct, bck, bcs, gsv in shapes.values():
         assert t in (64, 128, 256) and kp in (1, 2, 4, 8, 16) and gs in (64, 128, 256)
-        assert rc in (0, 1, 2, 4, 8, 16) and rt in (256, 512, 1024) and tile in (0, 1) and sites in (1, 4)
+        assert rc in (0, 1, 2, 4, 8, 16) and rt in (256, 512, 1024) and tile in (0, 64, 128, 256) and sites in (1, 4)
         assert lanes in (1, 2, 4) and lanes_v in (1, 2, 4)
         assert btt in (64, 128, 256) and bct in (64, 128, 256) and btk in (1, 2, 4) and bck in (1, 2, 4)
         assert bts in (1, 4) and bcs in (1, 4) and gsv in (64, 128, 256)
