@@ -42,9 +42,12 @@ WORKLOADS = {
     "p2-l6": dict(disc="P2P1", box=(1, 1, 1), L=6, lc=1, kind="paper"),
 }
 WORKLOAD = dict(WORKLOADS["p2-l7"])
-# FMG tuple s = (nu_pre, nu_post, nu_inc, kappa, A_hat, xi); omega^{-1} from 100
-# power iterations on the finest level
-PARAMS = dict(nu_pre=1, nu_post=3, nu_inc=2, kappa=1, ahat="f", xi=3)
+# FMG tuple s = (nu_pre, nu_post, nu_inc, kappa, A_hat, xi): of the tuples of the
+# search space S of Sec. 5.1 that reach (gamma_u, gamma_p) <= (2, 2) on level 7
+# (`--workload tme-disc`), one of the two fastest on the GPU, with the widest
+# accuracy margin (gamma_p ~ 1.03); omega^{-1} from 100 power iterations on
+# the finest level
+PARAMS = dict(nu_pre=1, nu_post=3, nu_inc=1, kappa=1, ahat="f", xi=3)
 # the accuracy bound (gamma_u, gamma_p) of a solve "at discretisation-error
 # accuracy" (Sec. 5.1: both errors within a factor 2 of the discretisation
 # error), and the bound pairs of Table 3 reported beside it
@@ -101,7 +104,8 @@ def make_problem(solve, error_level=False, nn=False):
     from hhg_inputs import Workload
     from paper_2010_13513_gb300 import hhg
     w = WORKLOAD
-    kw = dict(nn_hidden=512, nn_samples=10000, nn_batch=256) if nn else {}
+    # the network's hidden width is well below the coarse system's size (1154)
+    kw = dict(nn_hidden=128, nn_samples=10000, nn_batch=256) if nn else {}
     pb = hhg.Problem(hhg.Mesh.box(*w["box"], 1.0), disc=w["disc"], L=w["L"], coarse_level=w["lc"], solve=solve,
                      error_level=error_level, **kw)
     wl = Workload(w["kind"])
@@ -216,14 +220,23 @@ def measured_traffic(shape):
     return None
 
 
-def profile_apply():
+def profile_apply(workload):
     """Only the roofline apply: set-up, three warm-up launches, then three
-    launches (each after an L2 flush) between cudaProfilerStart/Stop."""
+    launches (each after an L2 flush) between cudaProfilerStart/Stop.  The
+    default workload's level-7 P2-P1 FP32 apply, or (p1-visc) the level-7
+    P1-P1 FP32 apply on the 48-tetrahedron cube with nu = exp(a z)."""
     import torch
+    from hhg_inputs import draw_viscosity_exponent
+    from paper_2010_13513_gb300 import hhg
     torch.cuda.set_stream(torch.cuda.Stream())
-    pb, _ = make_problem("mixed")
+    if workload == "p1-visc":
+        L = 7
+        pb = hhg.Problem(hhg.Mesh.box(2, 2, 2, 0.5), disc="P1P1", L=L, coarse_level=0, solve="mixed",
+                         nu_a=draw_viscosity_exponent(0))
+    else:
+        L = WORKLOAD["L"]
+        pb, _ = make_problem("mixed")
     pb.autotune(reps=3)
-    L = WORKLOAD["L"]
     x = pb.new_vector(L, prec=1)
     x.uniform_(-1, 1)
     y = pb.new_vector(L, prec=1)
@@ -231,6 +244,7 @@ def profile_apply():
     for _ in range(3):
         pb.apply(L, "FULL", x, y)
     torch.cuda.synchronize()
+    print("launch shape", pb.launch_shape(L))
     torch.cuda.profiler.start()
     for _ in range(3):
         flush.fill_(1.0)
@@ -746,13 +760,14 @@ def main():
     ap.add_argument("--profile-region", action="store_true",
                     help="only set-up, warm-up and the timed FMG steps, bracketed by cudaProfilerStart/Stop")
     ap.add_argument("--profile-apply", action="store_true",
-                    help="only the FP32 apply of the roofline line, bracketed by cudaProfilerStart/Stop")
+                    help="only the FP32 apply of the roofline line (or, with --workload p1-visc, the level-7 "
+                         "P1-P1 apply), bracketed by cudaProfilerStart/Stop")
     args = ap.parse_args()
     if args.workload in WORKLOADS:
         WORKLOAD.clear()
         WORKLOAD.update(WORKLOADS[args.workload])
     if args.profile_apply:
-        return profile_apply()
+        return profile_apply(args.workload)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

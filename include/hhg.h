@@ -247,8 +247,8 @@ int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
  * plane, stages the planes of its input arrays in shared memory as it marches
  * along k, and loads each line of a thread's stencil footprint once per
  * plane; the grid is one wave of blocks with equal runs of planes; only on
- * levels with nx >= 64, whose pitch sx is a multiple of four; 0 = the plain
- * kernels), and
+ * levels with nx >= 64, whose pitch sx is a multiple of four; four sites per
+ * thread, or two for FP32 with row_sites = 2; 0 = the plain kernels), and
  * row_sites = 1 or 4 sites per thread of the
  * row kernels (4: each warp evaluates four runs of 32 consecutive
  * positions of the padded (i, j) plane, sharing each term's address

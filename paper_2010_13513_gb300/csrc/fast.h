@@ -33,6 +33,7 @@ struct Shape {
   // and in FP64 (st64_threads; the mixed solve's outer residual)
   int st_threads[3] = {0, 0, 0};
   int st64_threads[3] = {0, 0, 0};
+  int st_sites[3] = {4, 4, 4};   // sites per thread of the FP32 streaming kernels (2 or 4)
   int row_sites = 1;       // sites per thread of the FP32 row kernels (1, or 4: four runs of 32 positions per warp)
   int row_sites64 = 1;     // the same for the FP64 row kernels
   // order of the per-phase Gauss-Seidel launches of a smoothing step: 0 = every

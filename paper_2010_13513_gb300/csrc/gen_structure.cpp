@@ -137,6 +137,16 @@ void print_stream_plan(int disc, int varnu, int op, const HOperator& O) {
   list("PartT", "parts", pl);
   list("LineT", "lines", ll);
   list("TermE", "terms", el);
+  // constant viscosity: the weights at h = 1 (weight index order); a term of
+  // segment s scales as h^2 (s = 0: B, B^T), h (s = 1: A) or h^3 (s = 2: C)
+  if (!varnu) {
+    std::printf("  static constexpr double wref[%d] = {", int(all.size()));
+    int n = 0;
+    for (size_t r = 0; r < O.rows.size(); ++r)
+      for (int sg = 0; sg < 3; ++sg)
+        for (const HTerm& h : O.rows[r].seg[sg]) std::printf("%s%.17g", n++ ? ", " : "", h.w);
+    std::printf("};\n");
+  }
   std::printf("};\n");
 }
 

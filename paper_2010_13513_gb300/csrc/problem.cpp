@@ -611,8 +611,9 @@ bool stream_op(hhg_problem* pb, Level& lv, const Shape& sh, int op, int mode, co
   const int si = op == OP_FULL ? 0 : op == OP_BT ? 1 : op == OP_BC ? 2 : -1;
   if (si < 0 || mode == MODE_ADD || !lv.has_stream[op]) return false;
   const int nt = sizeof(T) == 8 ? sh.st64_threads[si] : sh.st_threads[si];
+  const int ns = sizeof(T) == 8 ? 4 : sh.st_sites[si];
   return nt && stream_rows<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, op, mode, lv.g, stab<T>(lv, op), x, b, y,
-                              nt, pb->stream);
+                              nt, ns, pb->stream);
 }
 
 template <class T>
@@ -1475,7 +1476,8 @@ extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads,
   HHG_TRY(check_level(pb, level));
   auto ok_threads = [](int t) { return t == 64 || t == 128 || t == 256; };
   if (!ok_threads(row_threads) || !ok_threads(gs_threads) || row_kplanes < 1 || row_kplanes > 64 ||
-      (row_tile != 0 && row_tile != 1 && !ok_threads(row_tile)) || (row_sites != 1 && row_sites != 4) ||
+      (row_tile != 0 && row_tile != 1 && !ok_threads(row_tile)) ||
+      (row_sites != 1 && row_sites != 4 && !(row_sites == 2 && row_tile != 0)) ||
       (gs_lanes != 1 && gs_lanes != 2 && gs_lanes != 4))
     return fail(HHG_EINVAL, "invalid launch shape");
   Shape& sh = pb->L(level).shape;
@@ -1483,8 +1485,11 @@ extern "C" int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads,
   sh.row_kplanes = row_kplanes;
   sh.gs_threads = gs_threads;
   const int st = row_tile == 1 ? 128 : row_tile;
-  for (int o = 0; o < 3; ++o) sh.st_threads[o] = sh.st64_threads[o] = st;
-  sh.row_sites = row_sites;
+  for (int o = 0; o < 3; ++o) {
+    sh.st_threads[o] = sh.st64_threads[o] = st;
+    sh.st_sites[o] = row_sites == 2 ? 2 : 4;
+  }
+  sh.row_sites = row_sites == 2 ? 4 : row_sites;
   sh.row_sites64 = row_sites;
   sh.gs_lanes = gs_lanes;
   sh.gs_lanes0 = gs_lanes;
@@ -1849,12 +1854,15 @@ int tune_level(hhg_problem* pb, Level& lv, int reps, T* xa, T* xb) {
         fast_rows<T>(disc, varnu, sops[o], lv.g, lv.op[sops[o]], ftab<T>(lv, sops[o]), MODE_RES, xa, xa, xb, 1.0, sh,
                      pb->stream);
       });
-      for (int t : threads) {
-        sh.st_threads[o] = t;
-        if (!stream_op<T>(pb, lv, sh, sops[o], MODE_RES, xa, xa, xb)) continue;
-        const float ms = time_it([&] { stream_op<T>(pb, lv, sh, sops[o], MODE_RES, xa, xa, xb); });
-        if (ms < bo) { bo = ms; bestS.st_threads[o] = t; }
-      }
+      for (int v : {4, 2})
+        for (int t : threads) {
+          if (v == 2 && sizeof(T) == 8) continue;
+          sh.st_threads[o] = t;
+          sh.st_sites[o] = v;
+          if (!stream_op<T>(pb, lv, sh, sops[o], MODE_RES, xa, xa, xb)) continue;
+          const float ms = time_it([&] { stream_op<T>(pb, lv, sh, sops[o], MODE_RES, xa, xa, xb); });
+          if (ms < bo) { bo = ms; bestS.st_threads[o] = t; bestS.st_sites[o] = v; }
+        }
       if (std::is_same<T, double>::value) bestS.st64_threads[o] = bestS.st_threads[o];
     }
     if (!std::is_same<T, double>::value) {

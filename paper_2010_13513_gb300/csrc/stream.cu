@@ -66,16 +66,32 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// the four values of a quad (16-byte aligned; two 16-byte loads for double)
-template <class T>
-__device__ __forceinline__ void load_quad(const T* p, T (&w)[6]) {
-  if constexpr (sizeof(T) == 4) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    w[1] = v.x; w[2] = v.y; w[3] = v.z; w[4] = v.w;
+// V consecutive values of global memory (V x sizeof(T) bytes, aligned)
+template <int V, class T>
+__device__ __forceinline__ void gload(const T* p, T (&v)[V]) {
+  if constexpr (sizeof(T) == 4 && V == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if constexpr (sizeof(T) == 4) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x; v[1] = q.y;
   } else {
-    const double2 a = *reinterpret_cast<const double2*>(p);
-    const double2 c = *reinterpret_cast<const double2*>(p + 2);
-    w[1] = a.x; w[2] = a.y; w[3] = c.x; w[4] = c.y;
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) {
+      const double2 q = reinterpret_cast<const double2*>(p)[h];
+      v[2 * h] = q.x; v[2 * h + 1] = q.y;
+    }
+  }
+}
+template <int V, class T>
+__device__ __forceinline__ void gstore(T* p, const T (&v)[V]) {
+  if constexpr (sizeof(T) == 4 && V == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) reinterpret_cast<double2*>(p)[h] = make_double2(v[2 * h], v[2 * h + 1]);
   }
 }
 
@@ -108,15 +124,18 @@ template <int OG> struct Par {
   static constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
 };
 
-// accumulators of a pass: row r = 3 * part + segment, four sites each
-template <class T, int NA> struct Acc {
-  T a[NA][4];
+// accumulators of a pass: row r = 3 * part + segment, V sites each
+template <class T, int NA, int V> struct Acc {
+  T a[NA][V];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int r = 0; r < NA; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = T(0);
+    for (int r = 0; r < NA; ++r)
+#pragma unroll
+      for (int s = 0; s < V; ++s) a[r][s] = T(0);
   }
-  __device__ __forceinline__ void get(int r, T (&v)[4]) const {
-    v[0] = a[r][0]; v[1] = a[r][1]; v[2] = a[r][2]; v[3] = a[r][3];
+  __device__ __forceinline__ void get(int r, T (&v)[V]) const {
+#pragma unroll
+    for (int s = 0; s < V; ++s) v[s] = a[r][s];
   }
 };
 
@@ -125,17 +144,26 @@ template <class T, int NA> struct Acc {
 // one accumulator; the C terms (segment 2) keep their own, which the clipped
 // boundary stencil replaces on boundary pressure rows.  Every term is four
 // FMAs with the weight from the constant bank.
-template <class SPT, int E, int VARNU, class T, class Tab, int NA>
-__device__ __forceinline__ void term_fma(const T (&w)[6], Acc<T, NA>& acc, const Tab& tab) {
+// With a constant viscosity the weights are compile-time immediates: those of
+// h = 1 (SPT::wref), the pressure values scaled by h as they are loaded and
+// the rows scaled at the end (B, B^T scale as h^2, A as h, C as h^3).
+template <class SPT, int E, int VARNU, class T, class Tab, int NA, int V>
+__device__ __forceinline__ void term_fma(const T (&w)[V + 2], Acc<T, NA, V>& acc, const Tab& tab) {
   constexpr gen::TermE te = SPT::terms[E];
   constexpr int a = 3 * te.part + (VARNU || te.seg == 2 ? te.seg : 0);
-  const T wt = tab.w[te.t];
+  T wt;
+  if constexpr (VARNU) {
+    wt = tab.w[te.t];
+  } else {
+    constexpr double wd = SPT::wref[te.t];
+    wt = T(wd);
+  }
 #pragma unroll
-  for (int s = 0; s < 4; ++s) acc.a[a][s] = fma(wt, w[te.di + 1 + s], acc.a[a][s]);
+  for (int s = 0; s < V; ++s) acc.a[a][s] = fma(wt, w[te.di + 1 + s], acc.a[a][s]);
 }
 
-template <class SPT, int E0, int VARNU, class T, class Tab, int NA, int... I>
-__device__ __forceinline__ void line_terms(const T (&w)[6], Acc<T, NA>& acc, const Tab& tab,
+template <class SPT, int E0, int VARNU, class T, class Tab, int NA, int V, int... I>
+__device__ __forceinline__ void line_terms(const T (&w)[V + 2], Acc<T, NA, V>& acc, const Tab& tab,
                                            std::integer_sequence<int, I...>) {
   (term_fma<SPT, E0 + I, VARNU>(w, acc, tab), ...);
 }
@@ -143,15 +171,22 @@ __device__ __forceinline__ void line_terms(const T (&w)[6], Acc<T, NA>& acc, con
 // shared-memory buffer of plane kp (ring of four)
 __device__ __forceinline__ int64_t buf_of(int kp, int64_t bufsz) { return ((kp + 1) & 3) * bufsz; }
 
-// shared-memory loads with 32-bit shared addresses: a quad, and one value
-// loaded by one lane only (predicated, no branch)
-__device__ __forceinline__ void lds_quad(uint32_t a, float (&w)[6]) {
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(w[1]), "=f"(w[2]), "=f"(w[3]), "=f"(w[4]) : "r"(a));
+// shared-memory loads with 32-bit shared addresses: the thread's V values
+// (into w[1 .. V]), and one value loaded by one lane only (predicated, no
+// branch)
+template <int V>
+__device__ __forceinline__ void lds_vec(uint32_t a, float (&w)[V + 2]) {
+  if constexpr (V == 4)
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(w[1]), "=f"(w[2]), "=f"(w[3]), "=f"(w[4]) : "r"(a));
+  else
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(w[1]), "=f"(w[2]) : "r"(a));
 }
-__device__ __forceinline__ void lds_quad(uint32_t a, double (&w)[6]) {
-  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(w[1]), "=d"(w[2]) : "r"(a));
-  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(w[3]), "=d"(w[4]) : "r"(a + 16));
+template <int V>
+__device__ __forceinline__ void lds_vec(uint32_t a, double (&w)[V + 2]) {
+#pragma unroll
+  for (int h = 0; h < V / 2; ++h)
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(w[2 * h + 1]), "=d"(w[2 * h + 2]) : "r"(a + 16 * h));
 }
 __device__ __forceinline__ void lds_if(bool on, uint32_t a, float& v) {
   asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f32 %0, [%2];\n}"
@@ -166,31 +201,35 @@ __device__ __forceinline__ void lds_if(bool on, uint32_t a, double& v) {
 // terms need, then every term of the line.  pb[dk + 1] is the shared address
 // of the thread's quad in slot 0 of plane k + dk; lwb, sxb: the slot and row
 // strides in bytes.
-template <class SPT, int L, int VARNU, class T, class Tab, int NA>
-__device__ __forceinline__ void eval_line(const uint32_t (&pb)[3], int lwb, int sxb, int lane, Acc<T, NA>& acc,
-                                          const Tab& tab) {
+template <class SPT, int L, int VARNU, int PSLOT, class T, class Tab, int NA, int V>
+__device__ __forceinline__ void eval_line(const uint32_t (&pb)[3], int lwb, int sxb, int lane, T hs,
+                                          Acc<T, NA, V>& acc, const Tab& tab) {
   constexpr gen::LineT ln = SPT::lines[L];
   constexpr int es = int(sizeof(T));
   const uint32_t a = pb[ln.dk + 1] + uint32_t(ln.slot * lwb + ln.dj * sxb);
-  T w[6];
-  lds_quad(a, w);
+  T w[V + 2];
+  lds_vec<V>(a, w);
   if constexpr (ln.lmin < 0) {
-    T v = __shfl_up_sync(0xffffffffu, w[4], 1);
+    T v = __shfl_up_sync(0xffffffffu, w[V], 1);
     lds_if(lane == 0, a - es, v);
     w[0] = v;
   }
   if constexpr (ln.lmax > 0) {
     T v = __shfl_down_sync(0xffffffffu, w[1], 1);
-    lds_if(lane == 31, a + 4 * es, v);
-    w[5] = v;
+    lds_if(lane == 31, a + V * es, v);
+    w[V + 1] = v;
+  }
+  if constexpr (!VARNU && ln.slot == PSLOT) {
+#pragma unroll
+    for (int s = 0; s < V + 2; ++s) w[s] *= hs;
   }
   line_terms<SPT, ln.e0, VARNU>(w, acc, tab, std::make_integer_sequence<int, ln.ne>{});
 }
 
-template <class SPT, int L0, int VARNU, class T, class Tab, int NA, int... I>
-__device__ __forceinline__ void eval_lines(const uint32_t (&pb)[3], int lwb, int sxb, int lane, Acc<T, NA>& acc,
-                                           const Tab& tab, std::integer_sequence<int, I...>) {
-  (eval_line<SPT, L0 + I, VARNU>(pb, lwb, sxb, lane, acc, tab), ...);
+template <class SPT, int L0, int VARNU, int PSLOT, class T, class Tab, int NA, int V, int... I>
+__device__ __forceinline__ void eval_lines(const uint32_t (&pb)[3], int lwb, int sxb, int lane, T hs,
+                                           Acc<T, NA, V>& acc, const Tab& tab, std::integer_sequence<int, I...>) {
+  (eval_line<SPT, L0 + I, VARNU, PSLOT>(pb, lwb, sxb, lane, hs, acc, tab), ...);
 }
 
 // C terms of a boundary pressure row at site (i, j, k), staged position lf:
@@ -209,32 +248,36 @@ __device__ __forceinline__ T boundary_c(const Geo& g, const T* sm, int64_t bufsz
 }
 
 // --------------------------------------------------------------- outputs
-// the rows of part P at the thread's four sites (positions fk .. fk + 3 of
-// the k plane: coarse indices (i0 .. i0 + 3, j, k)), written to y as one
-// quad.  Positions of the quad outside the group's sites (the halo column,
-// the row padding) and Dirichlet velocity rows are written as 0: halo,
-// padding and Dirichlet entries of every vector are 0, so the quad store
-// never changes them.
-template <class SPT, int Q, int P, int VARNU, int PSLOT, class T, int MODE, class Tab, int NA>
+// the rows of part P at the thread's V sites (positions fk .. fk + V - 1 of
+// the k plane: coarse indices (i0 .. i0 + V - 1, j, k)), written to y as one
+// vector.  Positions outside the group's sites (the halo column, the row
+// padding) and Dirichlet velocity rows are written as 0: halo, padding and
+// Dirichlet entries of every vector are 0, so the vector store never changes
+// them.
+template <class SPT, int Q, int P, int VARNU, int PSLOT, class T, int MODE, class Tab, int NA, int V>
 __device__ __forceinline__ void store_part(const Geo& g, const T* __restrict__ b, T* __restrict__ y, const T* sm,
                                            int64_t bufsz, int lw, int lf, int k, int i0, int j, int64_t fk, T es, T eis,
-                                           const Acc<T, NA>& acc, const Tab& tab) {
+                                           const Acc<T, NA, V>& acc, const Tab& tab) {
   constexpr gen::PartT pt = SPT::parts[SPT::passes[Q].p0 + P];
   constexpr bool HAS_C = part_has_c<SPT, Q, P>();
   using PP = Par<pt.og>;
   if (j < 0 || j > g.ny - PP::oy || k > g.nz - PP::oz) return;
   const bool bjk = 2 * j + PP::oy == 0 || 2 * j + PP::oy == 2 * g.ny || 2 * k + PP::oz == 0 ||
                    2 * k + PP::oz == 2 * g.nz;
-  T a0[4], a1[4], a2[4], v[4];
+  T a0[V], a1[V], a2[V], v[V];
   acc.get(3 * P, a0);
   if (VARNU) acc.get(3 * P + 1, a1);
   if (HAS_C) acc.get(3 * P + 2, a2);
-  bool keep[4];
+  // constant viscosity: the scale of the row (h for velocity rows, h^2 for
+  // pressure rows; the pressure values entered scaled by h)
+  const T hs = pt.all ? T(g.h) * T(g.h) : T(g.h);
+  bool keep[V];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
+  for (int s = 0; s < V; ++s) {
     v[s] = a0[s];
     if (VARNU) v[s] += es * a1[s];
     if (HAS_C) v[s] += VARNU ? eis * a2[s] : a2[s];
+    if (!VARNU) v[s] *= hs;
     const int i = i0 + s;
     const bool bnd = bjk || 2 * i + PP::ox == 0 || 2 * i + PP::ox == 2 * g.nx;
     keep[s] = i >= 0 && i <= g.nx - PP::ox && (pt.all || !bnd);
@@ -243,54 +286,35 @@ __device__ __forceinline__ void store_part(const Geo& g, const T* __restrict__ b
         static_assert(PSLOT >= 0, "the pressure array is staged with the C terms");
         const T c = boundary_c<SPT, PSLOT, T>(g, sm, bufsz, lw, lf + s, i, j, k, tab,
                                               std::make_integer_sequence<int, SPT::NCB>{});
-        v[s] = VARNU ? a0[s] + es * a1[s] + eis * c : a0[s] + c;
+        v[s] = VARNU ? a0[s] + es * a1[s] + eis * c : hs * a0[s] + c;
       }
     }
   }
   const int64_t iy = int64_t(pt.out) * g.arr + fk;
-  T o[4];
+  T o[V];
   if (pt.first) {
     if (MODE == MODE_RES) {
-      T bb[4];
-      if constexpr (sizeof(T) == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(b + iy);
-        bb[0] = q.x; bb[1] = q.y; bb[2] = q.z; bb[3] = q.w;
-      } else {
-        const double2 q0 = *reinterpret_cast<const double2*>(b + iy);
-        const double2 q1 = *reinterpret_cast<const double2*>(b + iy + 2);
-        bb[0] = q0.x; bb[1] = q0.y; bb[2] = q1.x; bb[3] = q1.y;
-      }
+      T bb[V];
+      gload<V>(b + iy, bb);
 #pragma unroll
-      for (int s = 0; s < 4; ++s) o[s] = keep[s] ? bb[s] - v[s] : T(0);
+      for (int s = 0; s < V; ++s) o[s] = keep[s] ? bb[s] - v[s] : T(0);
     } else {
 #pragma unroll
-      for (int s = 0; s < 4; ++s) o[s] = keep[s] ? v[s] : T(0);
+      for (int s = 0; s < V; ++s) o[s] = keep[s] ? v[s] : T(0);
     }
   } else {
-    T c[4];
-    if constexpr (sizeof(T) == 4) {
-      const float4 q = *reinterpret_cast<const float4*>(y + iy);
-      c[0] = q.x; c[1] = q.y; c[2] = q.z; c[3] = q.w;
-    } else {
-      const double2 q0 = *reinterpret_cast<const double2*>(y + iy);
-      const double2 q1 = *reinterpret_cast<const double2*>(y + iy + 2);
-      c[0] = q0.x; c[1] = q0.y; c[2] = q1.x; c[3] = q1.y;
-    }
+    T c[V];
+    gload<V>(y + iy, c);
 #pragma unroll
-    for (int s = 0; s < 4; ++s) o[s] = keep[s] ? (MODE == MODE_RES ? c[s] - v[s] : c[s] + v[s]) : c[s];
+    for (int s = 0; s < V; ++s) o[s] = keep[s] ? (MODE == MODE_RES ? c[s] - v[s] : c[s] + v[s]) : c[s];
   }
-  if constexpr (sizeof(T) == 4) {
-    *reinterpret_cast<float4*>(y + iy) = make_float4(o[0], o[1], o[2], o[3]);
-  } else {
-    reinterpret_cast<double2*>(y + iy)[0] = make_double2(o[0], o[1]);
-    reinterpret_cast<double2*>(y + iy)[1] = make_double2(o[2], o[3]);
-  }
+  gstore<V>(y + iy, o);
 }
 
-template <class SPT, int Q, int VARNU, int PSLOT, class T, int MODE, class Tab, int NA, int... I>
+template <class SPT, int Q, int VARNU, int PSLOT, class T, int MODE, class Tab, int NA, int V, int... I>
 __device__ __forceinline__ void store_parts(const Geo& g, const T* __restrict__ b, T* __restrict__ y, const T* sm,
                                             int64_t bufsz, int lw, int lf, int k, int i0, int j, int64_t fk, T es,
-                                            T eis, const Acc<T, NA>& acc, const Tab& tab,
+                                            T eis, const Acc<T, NA, V>& acc, const Tab& tab,
                                             std::integer_sequence<int, I...>) {
   (store_part<SPT, Q, I, VARNU, PSLOT, T, MODE>(g, b, y, sm, bufsz, lw, lf, k, i0, j, fk, es, eis, acc, tab), ...);
 }
@@ -325,7 +349,7 @@ __device__ __forceinline__ void stage_plane(const T* __restrict__ x, T* buf, int
 // (tile, plane) pairs [b U / grid, (b + 1) U / grid) of the U = tiles x
 // (nz + 1) pairs, tile by tile.  On each tile a block marches through its
 // planes.
-template <int DISC, int VARNU, int OP, int Q, class T, int MODE, class Tab>
+template <int DISC, int VARNU, int OP, int Q, class T, int MODE, int V, class Tab>
 __global__ void __launch_bounds__(256, 2)
     k_stream(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, int lw, int64_t units,
              int64_t tiles, int kc, const __grid_constant__ Tab tab) {
@@ -337,12 +361,12 @@ __global__ void __launch_bounds__(256, 2)
   T* sm = reinterpret_cast<T*>(stream_smem);
   const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(stream_smem));
   const int tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
-  const int M = 4 * nt, sx = g.sx;
+  const int M = V * nt, sx = g.sx;
   const int nk = g.nz + 1;
   const int nch = lw / VE;
   const int64_t vlen = int64_t(3 * g.G + 1) * g.arr;
   const int64_t bufsz = int64_t(SPT::NAMAX) * lw;
-  const int lf = 4 * tid + sx + 4;                   // the thread's quad in a staged line
+  const int lf = V * tid + sx + 4;                   // the thread's sites in a staged line
   int64_t u, uend;
   if (kc > 0) {
     const int64_t t = blockIdx.x % tiles, c = blockIdx.x / tiles;
@@ -360,7 +384,7 @@ __global__ void __launch_bounds__(256, 2)
     u += k1 - k0;
     const int64_t m0 = int64_t(sx) + tile * M;
     const int64_t gbase = m0 - sx - 4;
-    const int64_t f = m0 + 4 * tid;                    // the thread's quad
+    const int64_t f = m0 + V * tid;                    // the thread's first site
     const int j = int(f / sx) - 1;
     const int i0 = int(f - int64_t(j + 1) * sx) - 1;
     auto load = [&](int kp) {
@@ -380,13 +404,13 @@ __global__ void __launch_bounds__(256, 2)
       cp_commit();
       cp_wait1();                                      // planes k-1, k, k+1 are in place (this thread's copies)
       __syncthreads();                                 // ... and every thread's
-      Acc<T, 3 * ps.np> acc;
+      Acc<T, 3 * ps.np, V> acc;
       acc.zero();
       const uint32_t pb[3] = {sbase + uint32_t(buf_of(k - 1, bufsz) + lf) * uint32_t(sizeof(T)),
                               sbase + uint32_t(buf_of(k, bufsz) + lf) * uint32_t(sizeof(T)),
                               sbase + uint32_t(buf_of(k + 1, bufsz) + lf) * uint32_t(sizeof(T))};
-      eval_lines<SPT, ps.l0, VARNU>(pb, lw * int(sizeof(T)), sx * int(sizeof(T)), lane, acc, tab,
-                                    std::make_integer_sequence<int, ps.nl>{});
+      eval_lines<SPT, ps.l0, VARNU, PSLOT>(pb, lw * int(sizeof(T)), sx * int(sizeof(T)), lane, T(g.h), acc, tab,
+                                           std::make_integer_sequence<int, ps.nl>{});
       T es = T(1), eis = T(1);
       if (VARNU) {
         es = T(g.esc[k]);
@@ -410,8 +434,8 @@ template <class T, int N, int NCB> struct STab {
 template <int DISC, int VARNU, int OP, class T>
 using STabOf = STab<T, gen::S<DISC, VARNU, OP>::N, gen::SP<DISC, VARNU, OP>::NCB>;
 
-size_t smem_bytes(int namax, const Geo& g, int threads, size_t es) {
-  return size_t(4) * namax * size_t(4 * threads + 2 * g.sx + 8) * es;
+size_t smem_bytes(int namax, const Geo& g, int threads, int v, size_t es) {
+  return size_t(4) * namax * size_t(v * threads + 2 * g.sx + 8) * es;
 }
 
 // blocks of a kernel that fit on one SM, and the SM count (cached)
@@ -443,16 +467,16 @@ int sm_count() {
   return n;
 }
 
-template <int DISC, int VARNU, int OP, int Q, class T, int MODE>
+template <int DISC, int VARNU, int OP, int Q, class T, int MODE, int V>
 bool launch_pass(const Geo& g, const void* tab, const T* x, const T* b, T* y, int threads, cudaStream_t s) {
   using SPT = gen::SP<DISC, VARNU, OP>;
   using Tab = STabOf<DISC, VARNU, OP, T>;
   const Tab& tb = *static_cast<const Tab*>(tab);
-  const size_t smem = smem_bytes(SPT::NAMAX, g, threads, sizeof(T));
-  auto fn = k_stream<DISC, VARNU, OP, Q, T, MODE, Tab>;
+  const size_t smem = smem_bytes(SPT::NAMAX, g, threads, V, sizeof(T));
+  auto fn = k_stream<DISC, VARNU, OP, Q, T, MODE, V, Tab>;
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(fn), threads, smem);
   if (per_sm < 1) return false;
-  const int M = 4 * threads;
+  const int M = V * threads;
   const int64_t tiles = (int64_t(g.ny + 1) * g.sx + M - 1) / M;
   const int nk = g.nz + 1;
   const int64_t units = tiles * nk;
@@ -470,35 +494,45 @@ bool launch_pass(const Geo& g, const void* tab, const T* x, const T* b, T* y, in
   return true;
 }
 
-template <int DISC, int VARNU, int OP, class T, int MODE, int... Q>
+template <int DISC, int VARNU, int OP, class T, int MODE, int V, int... Q>
 void launch_passes(const Geo& g, const void* tab, const T* x, const T* b, T* y, int threads, cudaStream_t s,
                    std::integer_sequence<int, Q...>) {
-  (launch_pass<DISC, VARNU, OP, Q, T, MODE>(g, tab, x, b, y, threads, s), ...);
+  (launch_pass<DISC, VARNU, OP, Q, T, MODE, V>(g, tab, x, b, y, threads, s), ...);
 }
+
+// sites per thread compiled in this translation unit (FP64: 4; FP32: 4, or
+// 2 in the unit built with HHG_STREAM_V = 2)
+#if defined(HHG_STREAM_V) && HHG_STREAM_V == 2
+constexpr int kV = 2;
+#else
+constexpr int kV = 4;
+#endif
 
 template <int DISC, int VARNU, int OP, class T>
 bool launch_stream(const Geo& g, const void* tab, int mode, const T* x, const T* b, T* y, int threads,
                    cudaStream_t s) {
   using SPT = gen::SP<DISC, VARNU, OP>;
   if ((threads != 64 && threads != 128 && threads != 256) || (g.sx & 3) || (g.arr & 3)) return false;
-  // quads are read and written as 16-byte vectors
+  // the thread's sites are read and written as vectors
   if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(b)) & 15)
     return false;
-  if (smem_bytes(SPT::NAMAX, g, threads, sizeof(T)) > kStreamMaxSmem) return false;
+  if (smem_bytes(SPT::NAMAX, g, threads, kV, sizeof(T)) > kStreamMaxSmem) return false;
   if (mode == MODE_SET)
-    launch_passes<DISC, VARNU, OP, T, MODE_SET>(g, tab, x, b, y, threads, s, std::make_integer_sequence<int, SPT::NP>{});
+    launch_passes<DISC, VARNU, OP, T, MODE_SET, kV>(g, tab, x, b, y, threads, s,
+                                                    std::make_integer_sequence<int, SPT::NP>{});
   else
-    launch_passes<DISC, VARNU, OP, T, MODE_RES>(g, tab, x, b, y, threads, s, std::make_integer_sequence<int, SPT::NP>{});
+    launch_passes<DISC, VARNU, OP, T, MODE_RES, kV>(g, tab, x, b, y, threads, s,
+                                                    std::make_integer_sequence<int, SPT::NP>{});
   return true;
 }
 
 template <int DISC, int VARNU, int OP, class T, int... Q>
 void init_passes(std::integer_sequence<int, Q...>) {
   using Tab = STabOf<DISC, VARNU, OP, T>;
-  ((cudaFuncSetAttribute(k_stream<DISC, VARNU, OP, Q, T, MODE_SET, Tab>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(kStreamMaxSmem)),
-    cudaFuncSetAttribute(k_stream<DISC, VARNU, OP, Q, T, MODE_RES, Tab>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(kStreamMaxSmem))),
+  ((cudaFuncSetAttribute(k_stream<DISC, VARNU, OP, Q, T, MODE_SET, kV, Tab>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStreamMaxSmem)),
+    cudaFuncSetAttribute(k_stream<DISC, VARNU, OP, Q, T, MODE_RES, kV, Tab>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStreamMaxSmem))),
    ...);
 }
 
@@ -538,24 +572,38 @@ void offsets_of(std::vector<int>& o) {
   X(1, 0, OP_FULL) X(1, 0, OP_BT) X(1, 0, OP_BC) X(1, 1, OP_FULL) X(1, 1, OP_BT) X(1, 1, OP_BC) \
   X(2, 0, OP_FULL) X(2, 0, OP_BT) X(2, 0, OP_BC) X(2, 1, OP_FULL) X(2, 1, OP_BT) X(2, 1, OP_BC)
 
-template <class T>
-bool stream_rows(int disc, int varnu, int op, int mode, const Geo& g, const void* tab, const T* x, const T* b, T* y,
-                 int threads, cudaStream_t s) {
+// the kernels of this translation unit (precision HHG_STREAM_ONLY, kV sites
+// per thread)
+template <class T, int V>
+bool stream_rows_v(int disc, int varnu, int op, int mode, const Geo& g, const void* tab, const T* x, const T* b, T* y,
+                   int threads, cudaStream_t s) {
+  static_assert(V == kV, "one site count per translation unit");
   if (mode != MODE_SET && mode != MODE_RES) return false;
-#define HHG_S(D, V, O) \
-  if (disc == D && varnu == V && op == O) return launch_stream<D, V, O, T>(g, tab, mode, x, b, y, threads, s);
+#define HHG_S(D, V_, O) \
+  if (disc == D && varnu == V_ && op == O) return launch_stream<D, V_, O, T>(g, tab, mode, x, b, y, threads, s);
   HHG_STREAM_CASES(HHG_S)
 #undef HHG_S
   return false;
 }
 
-template <class T>
-void stream_init() {
-#define HHG_I(D, V, O) init_stream<D, V, O, T>();
+template <class T, int V>
+void stream_init_v() {
+#define HHG_I(D, V_, O) init_stream<D, V_, O, T>();
   HHG_STREAM_CASES(HHG_I)
 #undef HHG_I
 }
 
+#if defined(HHG_STREAM_ONLY) && HHG_STREAM_ONLY == 32
+template bool stream_rows_v<float, kV>(int, int, int, int, const Geo&, const void*, const float*, const float*, float*,
+                                       int, cudaStream_t);
+template void stream_init_v<float, kV>();
+#else
+template bool stream_rows_v<double, kV>(int, int, int, int, const Geo&, const void*, const double*, const double*,
+                                        double*, int, cudaStream_t);
+template void stream_init_v<double, kV>();
+#endif
+
+#if !defined(HHG_STREAM_V) || HHG_STREAM_V != 2
 template <class T>
 bool stream_image(int disc, int varnu, int op, const std::vector<double>& w, const std::vector<double>& wc,
                   std::vector<char>& out) {
@@ -565,8 +613,13 @@ bool stream_image(int disc, int varnu, int op, const std::vector<double>& w, con
 #undef HHG_M
   return false;
 }
+#if defined(HHG_STREAM_ONLY) && HHG_STREAM_ONLY == 32
+template bool stream_image<float>(int, int, int, const std::vector<double>&, const std::vector<double>&,
+                                  std::vector<char>&);
+#else
+template bool stream_image<double>(int, int, int, const std::vector<double>&, const std::vector<double>&,
+                                   std::vector<char>&);
 
-#if !defined(HHG_STREAM_ONLY) || HHG_STREAM_ONLY == 64
 bool stream_c_offsets(int disc, int varnu, int op, std::vector<int>& offsets) {
 #define HHG_O(D, V, O) \
   if (disc == D && varnu == V && op == O) { offsets_of<D, V, O>(offsets); return true; }
@@ -574,18 +627,36 @@ bool stream_c_offsets(int disc, int varnu, int op, std::vector<int>& offsets) {
 #undef HHG_O
   return false;
 }
+
+// FP32 rows take 2 or 4 sites per thread (two other translation units), FP64
+// four
+extern template bool stream_rows_v<float, 4>(int, int, int, int, const Geo&, const void*, const float*, const float*,
+                                             float*, int, cudaStream_t);
+extern template bool stream_rows_v<float, 2>(int, int, int, int, const Geo&, const void*, const float*, const float*,
+                                             float*, int, cudaStream_t);
+extern template void stream_init_v<float, 4>();
+extern template void stream_init_v<float, 2>();
+
+template <class T>
+bool stream_rows(int disc, int varnu, int op, int mode, const Geo& g, const void* tab, const T* x, const T* b, T* y,
+                 int threads, int sites, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (sites == 2) return stream_rows_v<T, 2>(disc, varnu, op, mode, g, tab, x, b, y, threads, s);
+  }
+  return stream_rows_v<T, 4>(disc, varnu, op, mode, g, tab, x, b, y, threads, s);
+}
+template <class T>
+void stream_init() {
+  stream_init_v<T, 4>();
+  if constexpr (sizeof(T) == 4) stream_init_v<T, 2>();
+}
 template bool stream_rows<double>(int, int, int, int, const Geo&, const void*, const double*, const double*, double*,
-                                  int, cudaStream_t);
-template void stream_init<double>();
-template bool stream_image<double>(int, int, int, const std::vector<double>&, const std::vector<double>&,
-                                   std::vector<char>&);
-#endif
-#if !defined(HHG_STREAM_ONLY) || HHG_STREAM_ONLY == 32
+                                  int, int, cudaStream_t);
 template bool stream_rows<float>(int, int, int, int, const Geo&, const void*, const float*, const float*, float*, int,
-                                 cudaStream_t);
+                                 int, cudaStream_t);
+template void stream_init<double>();
 template void stream_init<float>();
-template bool stream_image<float>(int, int, int, const std::vector<double>&, const std::vector<double>&,
-                                  std::vector<char>&);
+#endif
 #endif
 
 }  // namespace hhg

@@ -20,15 +20,23 @@ void stream_init();
 
 // rows of op (OP_FULL, OP_BT or OP_BC) in MODE_SET / MODE_RES by the
 // streaming kernels (one launch per pass): blocks of `threads` (64 / 128 /
-// 256) threads, each owning 4 x threads positions of the (i, j) plane and a
-// run of k planes.  `tab` is the level's parameter image of op from
+// 256) threads of `sites` (FP32: 2 or 4; FP64: 4) consecutive sites each,
+// owning sites x threads positions of the (i, j) plane and a run of k
+// planes.  `tab` is the level's parameter image of op from
 // stream_image<T>.  Returns false (nothing launched) if the combination is
 // not supported, the level's pitch is not a multiple of four, the shared
 // memory of a block would exceed kStreamMaxSmem, or a vector is not 16-byte
 // aligned.
 template <class T>
 bool stream_rows(int disc, int varnu, int op, int mode, const Geo& g, const void* tab, const T* x, const T* b, T* y,
-                 int threads, cudaStream_t s);
+                 int threads, int sites, cudaStream_t s);
+
+// the kernels of one translation unit: V = 2 or 4 sites per thread (FP64: 4)
+template <class T, int V>
+bool stream_rows_v(int disc, int varnu, int op, int mode, const Geo& g, const void* tab, const T* x, const T* b, T* y,
+                   int threads, cudaStream_t s);
+template <class T, int V>
+void stream_init_v();
 
 // the parameter image of op: weights w in the order of the FastTab images,
 // and wc = 27 x NCB class sums of the boundary C stencil (class index

@@ -394,7 +394,8 @@ class Problem:
 
     def set_launch_shape(self, level, row_threads, row_kplanes, gs_threads, row_tile=0, row_sites=1, gs_lanes=1):
         """row_tile: 0 = plain row kernels; 64/128/256 = the streaming kernels
-        with that many threads per block (levels with nx >= 64)."""
+        with that many threads per block (levels with nx >= 64), of 4 sites
+        per thread, or 2 (FP32) with row_sites = 2."""
         _check(load().hhg_set_launch_shape(self.h, level, row_threads, row_kplanes, gs_threads, int(row_tile),
                                            int(row_sites), int(gs_lanes)), "hhg_set_launch_shape")
 

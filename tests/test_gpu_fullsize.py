@@ -176,7 +176,7 @@ def test_fullsize_rows_match_oracle(disc, box, H, L, lc, nu_a):
 
 def test_fmg_headline_tuple_parity():
     """The benchmark's FMG (P2-P1, the paper's cube solution, coarse level 2,
-    s = (1, 3, 2, 1, A_f, 3)) in FP64 at level 4 under autotuned launch
+    s = (1, 3, 1, 1, A_f, 3)) in FP64 at level 4 under autotuned launch
     shapes against the oracle's Algorithm 1: 1e-10 relative."""
     from hhg_inputs import Workload
     from oracle.stokes import Params, StokesHierarchy
@@ -184,7 +184,7 @@ def test_fmg_headline_tuple_parity():
     torch.cuda.set_stream(torch.cuda.Stream())
     wl = Workload("paper")
     L, lc = 4, 2
-    s = dict(nu_pre=1, nu_post=3, nu_inc=2, kappa=1, ahat="f", xi=3, omega_inv=0.32)
+    s = dict(nu_pre=1, nu_post=3, nu_inc=1, kappa=1, ahat="f", xi=3, omega_inv=0.32)
     pb = hhg.Problem(hhg.Mesh.box(1, 1, 1, 1.0), disc="P2P1", L=L, coarse_level=lc, solve="fp64")
     hhg.set_workload_rhs(pb, wl)
     pb.autotune(reps=2)

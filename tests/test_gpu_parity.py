@@ -212,11 +212,10 @@ def test_stream_rows_match_oracle(disc, box, L, nu_a):
     of such levels is a multiple of four): the full operator and the B^T
     block against the oracle in FP64 (1e-12), the residual and the per-phase
     smoother's B^T and (B, -C) residual rows against the plain kernels (FP64
-    1e-14, FP32 1e-6), for 64/128/256 threads per block (FP64 P2-P1 with 256
-    threads exceeds the shared memory and falls back to the plain kernels)
-    and k chunks that do or do not divide the planes (the last chunk is
-    partial); the planes of 17 or 33 rows of 68 positions end in partial
-    tiles."""
+    1e-14, FP32 1e-6), for 64/128/256 threads per block of 4 sites per
+    thread, or (FP32; FP64 keeps 4) 2 sites per thread (FP64 P2-P1 with 256
+    threads exceeds the shared memory and falls back to the plain kernels);
+    the planes of 17 or 33 rows of 68 positions end in partial tiles."""
     from paper_2010_13513_gb300 import hhg
     pb = lib_problem(box, L, disc, lc=1, nu_a=nu_a, solve="mixed")
     hy = oracle_hierarchy(box, L, disc, lc=1, nu_a=nu_a)
@@ -228,8 +227,8 @@ def test_stream_rows_match_oracle(disc, box, L, nu_a):
     pb.set_level_smoother(L, 0, prec=hhg.FP64)
     pb.set_level_smoother(L, 0, prec=hhg.FP32)
     out = {}
-    for st, kc in ((0, 2), (64, 3), (128, 16), (256, 5), (128, 1)):
-        pb.set_launch_shape(L, 128, kc, 128, st)
+    for st, kc, v in ((0, 2, 1), (64, 3, 1), (128, 16, 2), (256, 5, 1), (128, 1, 1), (256, 4, 2), (64, 8, 2)):
+        pb.set_launch_shape(L, 128, kc, 128, st, v)
         assert pb.launch_shape(L)[3] == st
         res = []
         for prec in (hhg.FP64, hhg.FP32):
@@ -243,8 +242,8 @@ def test_stream_rows_match_oracle(disc, box, L, nu_a):
         assert rel(res[0], ref) < 1e-12, (st, kc, rel(res[0], ref))
         assert rel(res[1], ref_bt) < 1e-12, (st, kc, rel(res[1], ref_bt))
         assert rel(res[4], ref) < 1e-5
-        out[(st, kc)] = res
-    base = out[(0, 2)]
+        out[(st, kc, v)] = res
+    base = out[(0, 2, 1)]
     for key, res in out.items():
         for n, (a, c) in enumerate(zip(res, base)):
             assert rel(a, c) < (1e-14 if n < 4 else 1e-6), (key, n, rel(a, c))
