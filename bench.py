@@ -208,12 +208,14 @@ def kernel_source_hash():
 def measured_traffic(shape):
     """DRAM bytes per launch of the roofline apply from the committed ncu
     summary of that kernel and workload, if it was taken on the current
-    kernel sources with the same launch shape (else None)."""
+    kernel sources with the same apply launch shape -- streaming-row threads
+    per CTA and sites per thread, slots 3 and 4 of the level's launch shape --
+    (else None)."""
     path = os.path.join(ROOT, "profiles", f"apply_{WORKLOAD['disc'].lower()}_l{WORKLOAD['L']}_fp32.md")
     try:
         fields = dict(l.strip("- \n").split(": ", 1) for l in open(path) if l.startswith("- ") and ": " in l)
         if fields.get("kernel_source_sha256") == kernel_source_hash() and \
-                fields.get("launch_shape") == json.dumps(list(shape)):
+                fields.get("apply_shape") == json.dumps([shape[3], shape[4]]):
             return int(fields["dram_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
         pass
@@ -253,7 +255,7 @@ def profile_apply(workload):
     torch.cuda.profiler.stop()
 
 
-def e2e_steps(pb, wl, prm, steps):
+def e2e_steps(pb, wl, prm, steps, profile=False):
     """Through the public API with host data: nodal forcing/Dirichlet data from
     host memory (hhg_set_rhs_levels: every level, assembled on the GPU, one
     synchronisation), the FMG solve, and the solution copied back to the host."""
@@ -272,13 +274,25 @@ def e2e_steps(pb, wl, prm, steps):
     x = pb.new_vector(L)
     d2h = pb.layout(L).n_dofs * 8
     out = torch.empty(pb.layout(L).n_dofs, dtype=torch.float64).pin_memory()
+
+    def step():
+        pb.set_rhs_levels(WORKLOAD["lc"], [host[l][0] for l in sorted(host)], [host[l][1] for l in sorted(host)])
+        pb.fmg_solve(prm, x, stats=False)
+        pb.to_host(L, x, out=out)
+
+    step()                                       # warm-up (not timed)
+    if profile:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return [], h2d, d2h
     ts = []
     for _ in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pb.set_rhs_levels(WORKLOAD["lc"], [host[l][0] for l in sorted(host)], [host[l][1] for l in sorted(host)])
-        pb.fmg_solve(prm, x, stats=False)
-        pb.to_host(L, x, out=out)
+        step()
         ts.append(time.perf_counter() - t0)
     assert torch.isfinite(out).all()
     return ts, h2d, d2h
@@ -759,6 +773,9 @@ def main():
     ap.add_argument("--rows-out", default="", help="tme-disc: write every tuple's row to <prefix>_L<level>.json")
     ap.add_argument("--profile-region", action="store_true",
                     help="only set-up, warm-up and the timed FMG steps, bracketed by cudaProfilerStart/Stop")
+    ap.add_argument("--profile-e2e", action="store_true",
+                    help="only set-up and one end-to-end step (host data in, FMG, solution out), bracketed by "
+                         "cudaProfilerStart/Stop")
     ap.add_argument("--profile-apply", action="store_true",
                     help="only the FP32 apply of the roofline line (or, with --workload p1-visc, the level-7 "
                          "P1-P1 apply), bracketed by cudaProfilerStart/Stop")
@@ -793,11 +810,14 @@ def main():
         dist.init_process_group("nccl")
     hhg.load()
     L = WORKLOAD["L"]
-    learned = rank == 0 and not args.no_learned and not args.profile_region
+    learned = rank == 0 and not args.no_learned and not args.profile_region and not args.profile_e2e
 
     # ---------------- set-up (not timed): hierarchy, rhs on all levels, omega
-    pb, wl = make_problem("mixed", error_level=(rank == 0 and not args.profile_region), nn=learned)
+    pb, wl = make_problem("mixed", error_level=(rank == 0 and not args.profile_region and not args.profile_e2e), nn=learned)
     shapes = pb.autotune(reps=5)
+    if args.profile_e2e:
+        e2e_steps(pb, wl, hhg.Params.make(**PARAMS, omega_inv=0.32), 1, profile=True)
+        return
     if args.profile_region:
         prm = hhg.Params.make(**PARAMS, omega_inv=0.32)
         x = pb.new_vector(L)

@@ -259,7 +259,8 @@ int hhg_autotune(hhg_problem* pb, int reps, int* shapes_out);
  * and the edge groups, which hhg_autotune chooses apart; the B^T and
  * (B, -C) rows take this shape too until hhg_autotune gives them their own).  Results agree up to
  * rounding.  Drops cached graphs.  hhg_get_launch_shape writes the six
- * values to shape6. */
+ * values to shape6 in the same order; its row_sites slot reads 2 when the
+ * level's streaming rows (first velocity pass) take 2 sites per thread. */
 int hhg_set_launch_shape(hhg_problem* pb, int level, int row_threads, int row_kplanes, int gs_threads, int row_tile,
                          int row_sites, int gs_lanes);
 int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape6);

@@ -39,14 +39,11 @@ __device__ __forceinline__ bool dof_boundary(const Geo& g, int i, int j, int k, 
 __constant__ int c_goff[8][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
 
 // ------------------------------------------------------------------ apply
+// row r of op at coarse index (i, j, k)
 template <class T, int MODE>
-__global__ void __launch_bounds__(128) k_apply(Geo g, OpDev op, const T* __restrict__ x, const T* __restrict__ b,
-                                               T* __restrict__ y, T alpha) {
-  const int nzp = g.nz + 1;
-  const int r = blockIdx.z / nzp;
-  const int k = blockIdx.z - r * nzp;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void apply_site(const Geo& g, const OpDev& op, int r, int i, int j, int k,
+                                           const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y,
+                                           T alpha) {
   const DRow row = op.rows[r];
   const int ox = c_goff[row.og][0], oy = c_goff[row.og][1], oz = c_goff[row.og][2];
   if (!dof_valid(g, i, j, k, ox, oy, oz)) return;
@@ -93,6 +90,52 @@ __global__ void __launch_bounds__(128) k_apply(Geo g, OpDev op, const T* __restr
   if (MODE == MODE_SET) *yo = v;
   else if (MODE == MODE_RES) *yo = b[int64_t(row.out_arr) * g.arr + idx] - v;
   else *yo += alpha * v;
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(128) k_apply(Geo g, OpDev op, const T* __restrict__ x, const T* __restrict__ b,
+                                               T* __restrict__ y, T alpha) {
+  const int nzp = g.nz + 1;
+  const int r = blockIdx.z / nzp;
+  const int k = blockIdx.z - r * nzp;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  apply_site<T, MODE>(g, op, r, i, j, k, x, b, y, alpha);
+}
+
+// the rows within one site of the box's faces (the shell, where an input that
+// is non-zero only on boundary nodes gives non-zero rows): blockIdx.y = row x
+// plane (planes k of `ks`: the first two and last two planes, all of each;
+// or the inner planes, their ring of sites with i or j within one site of a
+// face)
+template <class T, int MODE>
+__global__ void __launch_bounds__(128) k_apply_shell(Geo g, OpDev op, int inner, const T* __restrict__ x,
+                                                     const T* __restrict__ b, T* __restrict__ y, T alpha) {
+  const int np = inner ? g.nz - 3 : 4;
+  const int r = blockIdx.y / np, kk = blockIdx.y - r * np;
+  const int k = inner ? 2 + kk : (kk < 2 ? kk : g.nz - 3 + kk);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nxp = g.nx + 1;
+  int i, j;
+  if (!inner) {
+    if (q >= nxp * (g.ny + 1)) return;
+    j = q / nxp;
+    i = q - j * nxp;
+  } else {
+    const int nfull = 4 * nxp;                       // rows j = 0, 1, ny - 1, ny
+    if (q < nfull) {
+      const int jj = q / nxp;
+      i = q - jj * nxp;
+      j = jj < 2 ? jj : g.ny - 3 + jj;
+    } else {
+      const int q2 = q - nfull;                     // rows 2 .. ny - 2: i = 0, 1, nx - 1, nx
+      j = 2 + q2 / 4;
+      if (j > g.ny - 2) return;
+      const int c = q2 - (j - 2) * 4;
+      i = c < 2 ? c : g.nx - 3 + c;
+    }
+  }
+  apply_site<T, MODE>(g, op, r, i, j, k, x, b, y, alpha);
 }
 
 // ------------------------------------------------------- Gauss-Seidel phase
@@ -376,6 +419,24 @@ void launch_apply(const Geo& g, const OpDev& op, int mode, const T* x, const T* 
 }
 
 template <class T>
+void launch_apply_shell(const Geo& g, const OpDev& op, int mode, const T* x, const T* b, T* y, double alpha,
+                        cudaStream_t s) {
+  if (op.nrows == 0) return;
+  if (g.nx < 4 || g.ny < 4 || g.nz < 4) return launch_apply<T>(g, op, mode, x, b, y, alpha, s);
+  auto go = [&](int inner) {
+    const int64_t n = inner ? 4 * int64_t(g.nx + 1) + 4 * int64_t(g.ny - 3) : int64_t(g.nx + 1) * (g.ny + 1);
+    const int np = inner ? g.nz - 3 : 4;
+    dim3 grd(unsigned((n + 127) / 128), unsigned(np * op.nrows), 1);
+    ++g_launches;
+    if (mode == MODE_SET) k_apply_shell<T, MODE_SET><<<grd, 128, 0, s>>>(g, op, inner, x, b, y, T(alpha));
+    else if (mode == MODE_RES) k_apply_shell<T, MODE_RES><<<grd, 128, 0, s>>>(g, op, inner, x, b, y, T(alpha));
+    else k_apply_shell<T, MODE_ADD><<<grd, 128, 0, s>>>(g, op, inner, x, b, y, T(alpha));
+  };
+  go(0);
+  go(1);
+}
+
+template <class T>
 void launch_gs(const Geo& g, const OpDev& A, int grp, int colour, double inv_diag, T* u, const T* rhs,
                cudaStream_t s) {
   dim3 blk(32, 4, 1);
@@ -493,6 +554,8 @@ template void launch_canon_gather<float>(const Geo&, const float*, double*, int6
 
 #define HHG_INST(T)                                                                                              \
   template void launch_apply<T>(const Geo&, const OpDev&, int, const T*, const T*, T*, double, cudaStream_t);     \
+  template void launch_apply_shell<T>(const Geo&, const OpDev&, int, const T*, const T*, T*, double,              \
+                                      cudaStream_t);                                                              \
   template void launch_gs<T>(const Geo&, const OpDev&, int, int, double, T*, const T*, cudaStream_t);              \
   template void launch_pupdate<T>(const Geo&, T*, const T*, const double*, double, cudaStream_t);                 \
   template void launch_sub_scalar_p<T>(const Geo&, T*, const double*, double, cudaStream_t);                      \

@@ -15,6 +15,13 @@ template <class T>
 void launch_apply(const Geo& g, const OpDev& op, int mode, const T* x, const T* b, T* y, double alpha,
                   cudaStream_t s);
 
+// the same on the rows within one site of the box's faces only: exact when x
+// is non-zero only on boundary nodes (the Dirichlet lifting), since the rows
+// farther inside read no boundary node
+template <class T>
+void launch_apply_shell(const Geo& g, const OpDev& op, int mode, const T* x, const T* b, T* y, double alpha,
+                        cudaStream_t s);
+
 // one multicolour Gauss-Seidel phase on the three velocity components:
 // group `grp`, colour `colour` (0..3 for the vertex group, -1 = whole group)
 template <class T>

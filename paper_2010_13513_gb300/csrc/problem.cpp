@@ -1246,11 +1246,14 @@ int enqueue_rhs(hhg_problem* pb, int level, const double* f_nodal, const double*
   launch_canon_scatter<double>(g, lv.bw64, lv.W, nvn, npn, false, true, pb->stream);
   HHG_CHECK_LAUNCH();
   HHG_CUDA(cudaMemsetAsync(lv.rhs, 0, size_t(lv.nvec()) * 8, pb->stream));
-  // f = M f_h - A w_h (interior velocity rows)
+  // f = M f_h - A w_h (interior velocity rows); w_h is non-zero only on
+  // boundary nodes, so A w_h and B w_h are evaluated on the shell of rows
+  // within one site of the box's faces (the others read no boundary node)
   HHG_TRY(apply_op<double>(pb, lv, OP_MVINT, MODE_SET, lv.tmp64, nullptr, lv.rhs));
-  HHG_TRY(apply_op<double>(pb, lv, OP_A, MODE_ADD, lv.W, nullptr, lv.rhs, -1.0));
+  launch_apply_shell<double>(lv.g, lv.op[OP_A], MODE_ADD, lv.W, nullptr, lv.rhs, -1.0, pb->stream);
   // g = -B w_h (+ PSPG load), projected to sum zero
-  HHG_TRY(apply_op<double>(pb, lv, OP_B, MODE_ADD, lv.W, nullptr, lv.rhs, -1.0));
+  launch_apply_shell<double>(lv.g, lv.op[OP_B], MODE_ADD, lv.W, nullptr, lv.rhs, -1.0, pb->stream);
+  HHG_CHECK_LAUNCH();
   if (pb->ov == 1 && pb->desc.pspg_rhs) HHG_TRY(apply_op<double>(pb, lv, OP_LOAD, MODE_ADD, lv.tmp64, nullptr, lv.rhs, 1.0));
   const int64_t po = p_offset(lv);
   launch_reduce<double>(RED_SUM, lv.rhs + po, nullptr, nullptr, g.arr, pb->partials, pb->max_blocks, pb->scal, pb->stream);
@@ -1522,7 +1525,7 @@ extern "C" int hhg_get_launch_shape(hhg_problem* pb, int level, int* shape6) {
   if (!shape6) return fail(HHG_EINVAL, "null argument");
   const Shape& sh = pb->L(level).shape;
   shape6[0] = sh.row_threads; shape6[1] = sh.row_kplanes; shape6[2] = sh.gs_threads; shape6[3] = sh.st_threads[0];
-  shape6[4] = sh.row_sites; shape6[5] = sh.gs_lanes;
+  shape6[4] = sh.st_threads[0] && sh.st_sites[0] == 2 ? 2 : sh.row_sites; shape6[5] = sh.gs_lanes;
   return HHG_OK;
 }
 

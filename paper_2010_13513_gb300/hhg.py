@@ -400,7 +400,8 @@ class Problem:
                                            int(row_sites), int(gs_lanes)), "hhg_set_launch_shape")
 
     def launch_shape(self, level):
-        """(row_threads, row_kplanes, gs_threads, stream_threads, row_sites, gs_lanes) of a level."""
+        """(row_threads, row_kplanes, gs_threads, stream_threads, row_sites, gs_lanes) of a level;
+        row_sites reads 2 when the streaming rows take 2 sites per thread."""
         out = (C.c_int * 6)()
         _check(load().hhg_get_launch_shape(self.h, level, out), "hhg_get_launch_shape")
         return tuple(out)
