@@ -193,11 +193,12 @@ def apply_roofline(pb, steps=20):
 
 
 def kernel_source_hash():
-    """sha256 of the sources of the stencil-row kernels (the apply kernel of
-    the roofline line)."""
+    """sha256 of the sources of the streaming stencil-row kernel (the apply
+    kernel of the roofline line): its source and header, and the generator
+    and stencil builder that produce its compile-time row structure."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("fast.cu", "fast.h", "stream.cu", "gen_structure.cpp", "stencils.cpp"):
+    for f in ("stream.cu", "stream.h", "gen_structure.cpp", "stencils.cpp"):
         path = os.path.join(ROOT, "paper_2010_13513_gb300", "csrc", f)
         if os.path.exists(path):
             with open(path, "rb") as fh:
@@ -376,7 +377,8 @@ def cpu_baseline(prm_dict, level=CPU_SAMPLE_LEVEL, seconds=10.0):
 def run_batched(args):
     """The batched workload: 64 independent problems (Kuhn boxes {1,2}^3,
     levels 3..6, P1-P1 / P2-P1, random smooth forcing, zero Dirichlet data)
-    solved by one CUDA graph with one branch per problem, against the same
+    solved by one CUDA graph of merged launches (each launch runs one kernel
+    over the work items of all problems that reach it), against the same
     problems solved one after another (each with its own graph)."""
     import torch
     from hhg_inputs import Workload, batched_problem_list
@@ -419,6 +421,7 @@ def run_batched(args):
         return s.elapsed_time(e) / reps * 1e-3
 
     sampler = ClockSampler(0)
+    graph_kernels, problem_kernels = batch.launch_counts()
     t_batch = timed(lambda: batch.fmg_solve(prms, stream), args.steps)
     t_seq = timed(lambda: [pb.fmg_solve(prm, None, stats=False) for pb, prm in zip(pbs, prms)], max(1, args.steps // 2))
     clocks = sampler.stop()
@@ -446,7 +449,8 @@ def run_batched(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "64 independent Stokes problems: Kuhn boxes {1,2}^3, levels 3..6, P1-P1 and P2-P1, "
                                    "random smooth forcing (8 sine modes per component), zero Dirichlet data",
-                       "dofs": dofs, "problems": len(pbs), "graph_kernels": kernels, "setup_s": t_setup,
+                       "dofs": dofs, "problems": len(pbs), "graph_kernels": graph_kernels,
+                       "problem_kernels": problem_kernels, "setup_s": t_setup,
                        "sequential_ms": t_seq * 1e3, "batch_speedup_vs_sequential": t_seq / t_batch,
                        "accuracy": deltas},
             "clocks": clocks}

@@ -330,19 +330,34 @@ int hhg_coarse_nn_enable(hhg_problem* pb, int mode, double theta);
 int hhg_coarse_nn_counts(hhg_problem* pb, int64_t* accepted, int64_t* rejected);
 
 /* ------------------------------------------------------------------ batches */
-/* A batch of n independent problems (each bound, with its rhs set on every
- * level; a problem may belong to one batch at a time).  The handles are
- * borrowed: the problems must outlive the batch.  The batch owns n CUDA
- * streams and events (no device memory). */
+/* Not in the paper (many independent problems on one GPU; the paper's
+ * ownership of work by primitives, Sec. 2.1, taken across problems).  A batch
+ * of n independent problems (each bound, with its rhs set on every level; a
+ * problem may belong to one batch at a time).  The handles are borrowed: the
+ * problems must outlive the batch.  The batch owns n CUDA streams and
+ * events, and (after the first solve) the device copies of the stencil
+ * tables and the work-item lists of its merged launches. */
 int hhg_batch_create(hhg_problem* const* problems, int n, hhg_batch** out);
 int hhg_batch_destroy(hhg_batch* batch);
 /* FMG (Algorithm 1) of every problem of the batch, params[i] for problem i.
- * The first call (and every call with different parameters) records one CUDA
- * graph in which every problem's FMG is an independent branch; the graph is
- * launched on `stream` (cudaStream_t, must not be the legacy default stream).
- * Each problem's solution ends in its workspace (hhg_level_vector(.., L, 2)).
- * *kernels (optional) receives the kernel count of the graph.  Asynchronous. */
+ * The first call (and every call with different parameters) records every
+ * problem's kernel sequence without running it, then merges the sequences:
+ * the next kernels of all problems that run the same kernel with the same
+ * block shape become ONE launch over the flat list of (problem, block) work
+ * items, each item with its own problem's arguments; each problem's own
+ * order is kept, and the problems share no data, so every problem gets
+ * exactly its individual hhg_fmg_solve result.  The merged launches are
+ * captured as one CUDA graph (the streaming row passes of large levels stay
+ * launches of their own).  Batches with a problem that uses the learned
+ * coarse correction record one graph branch per problem instead.  The graph
+ * is launched on `stream` (cudaStream_t, must not be the legacy default
+ * stream).  Each problem's solution ends in its workspace
+ * (hhg_level_vector(.., L, 2)).  *kernels (optional) receives the kernel
+ * count of the graph.  Asynchronous. */
 int hhg_batch_fmg_solve(hhg_batch* batch, const hhg_params* params, void* stream, int64_t* kernels);
+/* after a solve: *launches = kernels of the batch graph, *problem_kernels =
+ * the kernels of the problems' own sequences (their sum over the problems) */
+int hhg_batch_launch_counts(const hhg_batch* batch, int64_t* launches, int64_t* problem_kernels);
 
 /* Whether hhg_fmg_solve records its kernel sequence once per parameter tuple
  * as a CUDA graph and replays it (default on).  Graphs are used only when the

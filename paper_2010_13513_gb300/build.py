@@ -22,11 +22,13 @@ LIB = os.path.join(HERE, "libhhg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, object, extra flags): fast.cu and stream.cu are compiled once per precision
 SOURCES = [("kernels.cu", "kernels", []), ("fast.cu", "fast64", ["-DHHG_FAST_ONLY=64"]),
-           ("fast.cu", "fast32", ["-DHHG_FAST_ONLY=32"]), ("stream.cu", "stream64", ["-DHHG_STREAM_ONLY=64"]),
+           ("fast.cu", "fast32", ["-DHHG_FAST_ONLY=32"]),
+           ("fast.cu", "fast64b", ["-DHHG_FAST_ONLY=64", "-DHHG_FAST_BATCHED"]),
+           ("fast.cu", "fast32b", ["-DHHG_FAST_ONLY=32", "-DHHG_FAST_BATCHED"]), ("stream.cu", "stream64", ["-DHHG_STREAM_ONLY=64"]),
            ("stream.cu", "stream32", ["-DHHG_STREAM_ONLY=32"]),
            ("stream.cu", "stream32v2", ["-DHHG_STREAM_ONLY=32", "-DHHG_STREAM_V=2"]), ("small.cu", "small", []),
            ("nn.cu", "nn", []), ("noalloc.cu", "noalloc", []), ("stencils.cpp", "stencils", []),
-           ("problem.cpp", "problem", [])]
+           ("batch.cpp", "batch", []), ("problem.cpp", "problem", [])]
 
 
 def _nvcc():

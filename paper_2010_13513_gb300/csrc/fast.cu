@@ -18,6 +18,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "batch.h"
 #include "fast.h"
 #include "kernels.h"
 #include "structure.inc"
@@ -150,17 +151,18 @@ __device__ __forceinline__ void row_site(const Geo& g, int R, int i, int j, int 
 // blocks resident at the same time run the same (fully unrolled) row code.
 template <int DISC, int VARNU, int OP, class T, int MODE, int OUT, int OG, int ALL, int T0, int N0, int N1, int N2,
           class Tab>
-__device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restrict__ x, const T* __restrict__ b,
-                                         T* __restrict__ y, T alpha, const OpDev& op, const Tab& tab, int kp) {
+__device__ __forceinline__ void eval_row(const uint3 bid, const Geo& g, int R, const T* __restrict__ x,
+                                         const T* __restrict__ b, T* __restrict__ y, T alpha, const OpDev& op,
+                                         const Tab& tab, int kp) {
   constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
   constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
   constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
   const int w = g.nx + 1 - ox;                       // sites per i row of this group
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = bid.x * blockDim.x + threadIdx.x;
   const int j = q / w;
   const int i = q - j * w;
   if (j > g.ny - oy) return;
-  const int k0 = blockIdx.y * kp;
+  const int k0 = bid.y * kp;
   const bool bij = 2 * i + ox == 0 || 2 * i + ox == 2 * g.nx || 2 * j + oy == 0 || 2 * j + oy == 2 * g.ny;
 #pragma unroll 1
   for (int k = k0; k < k0 + kp && k <= g.nz - oz; ++k)
@@ -176,16 +178,17 @@ __device__ __forceinline__ void eval_row(const Geo& g, int R, const T* __restric
 // evaluates its sites one by one (its runs would read past the plane).
 template <int DISC, int VARNU, int OP, class T, int MODE, int V, int OUT, int OG, int ALL, int T0, int N0, int N1,
           int N2, class Tab>
-__device__ __forceinline__ void eval_row_vec(const Geo& g, int R, const T* __restrict__ x, const T* __restrict__ b,
-                                             T* __restrict__ y, T alpha, const OpDev& op, const Tab& tab, int kp) {
+__device__ __forceinline__ void eval_row_vec(const uint3 bid, const Geo& g, int R, const T* __restrict__ x,
+                                             const T* __restrict__ b, T* __restrict__ y, T alpha, const OpDev& op,
+                                             const Tab& tab, int kp) {
   constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
   constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
   constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
-  const int m0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * V);
+  const int m0 = ((bid.x * blockDim.x + threadIdx.x) >> 5) * (32 * V);
   const int lane = int(threadIdx.x & 31);
   const int mlast = (g.ny - oy) * g.sx + (g.nx - ox);   // position of the group's last site in the plane
   if (m0 > mlast) return;
-  const int k0 = blockIdx.y * kp, k1 = min(k0 + kp, g.nz - oz + 1);
+  const int k0 = bid.y * kp, k1 = min(k0 + kp, g.nz - oz + 1);
   if (m0 + 32 * V - 1 > mlast) {                     // warp-uniform: the plane's last warp
 #pragma unroll 1
     for (int k = k0; k < k1; ++k)
@@ -259,30 +262,63 @@ __device__ __forceinline__ void pdl_trigger() { cudaTriggerProgrammaticLaunchCom
 
 // FP32 P2-P1 rows: at most 80 registers (three 256-thread blocks per SM);
 // the shorter P1-P1 rows, and FP64 (bound by its arithmetic), uncapped
+// arguments of the row kernels as a work item of a merged launch (the table
+// as a device copy)
+template <class T, class Tab>
+struct RowsA { Geo g; const T* x; const T* b; T* y; T alpha; OpDev op; int kp; const Tab* tab; };
+
+template <int DISC, int VARNU, int OP, class T, int MODE, int V, class Tab>
+__device__ __forceinline__ void rows_vec_body(const uint3 bid, const Geo& g, const T* __restrict__ x,
+                                              const T* __restrict__ b, T* __restrict__ y, T alpha, const OpDev& op,
+                                              int kp, const Tab& tab) {
+  using S = gen::S<DISC, VARNU, OP>;
+  dispatch<S, 0>(int(bid.z), [&](auto rc) {
+    constexpr int R = decltype(rc)::value;
+    constexpr gen::RowS rw = S::rows[R];
+    eval_row_vec<DISC, VARNU, OP, T, MODE, V, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(bid, g, R, x, b, y,
+                                                                                                alpha, op, tab, kp);
+  });
+}
 template <int DISC, int VARNU, int OP, class T, int MODE, int V>
 __global__ void __launch_bounds__(256, DISC == 2 && sizeof(T) == 4 ? 3 : 1)
     k_rows_vec(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, T alpha, OpDev op, int kp,
                const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP>::N> tab) {
-  using S = gen::S<DISC, VARNU, OP>;
-  dispatch<S, 0>(int(blockIdx.z), [&](auto rc) {
-    constexpr int R = decltype(rc)::value;
-    constexpr gen::RowS rw = S::rows[R];
-    eval_row_vec<DISC, VARNU, OP, T, MODE, V, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, x, b, y, alpha,
-                                                                                                op, tab, kp);
-  });
+  rows_vec_body<DISC, VARNU, OP, T, MODE, V>(blockIdx, g, x, b, y, alpha, op, kp, tab);
+}
+template <int DISC, int VARNU, int OP, class T, int MODE, int V>
+__global__ void __launch_bounds__(256, DISC == 2 && sizeof(T) == 4 ? 3 : 1) kb_rows_vec(const void* items, int n) {
+  using Tab = FastTab<T, gen::S<DISC, VARNU, OP>::N>;
+  uint3 bid, gd;
+  const auto& it = batch_item<RowsA<T, Tab>>(items, n, bid, gd);
+  const RowsA<T, Tab>& a = it.a;
+  rows_vec_body<DISC, VARNU, OP, T, MODE, V>(bid, a.g, a.x, a.b, a.y, a.alpha, a.op, a.kp, *a.tab);
 }
 
+template <int DISC, int VARNU, int OP, class T, int MODE, class Tab>
+__device__ __forceinline__ void rows_fast_body(const uint3 bid, const Geo& g, const T* __restrict__ x,
+                                               const T* __restrict__ b, T* __restrict__ y, T alpha, const OpDev& op,
+                                               int kp, const Tab& tab) {
+  using S = gen::S<DISC, VARNU, OP>;
+  dispatch<S, 0>(int(bid.z), [&](auto rc) {
+    constexpr int R = decltype(rc)::value;
+    constexpr gen::RowS rw = S::rows[R];
+    eval_row<DISC, VARNU, OP, T, MODE, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(bid, g, R, x, b, y, alpha,
+                                                                                          op, tab, kp);
+  });
+}
 template <int DISC, int VARNU, int OP, class T, int MODE>
 __global__ void __launch_bounds__(256)
     k_rows_fast(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, T alpha, OpDev op, int kp,
                 const __grid_constant__ FastTab<T, gen::S<DISC, VARNU, OP>::N> tab) {
-  using S = gen::S<DISC, VARNU, OP>;
-  dispatch<S, 0>(int(blockIdx.z), [&](auto rc) {
-    constexpr int R = decltype(rc)::value;
-    constexpr gen::RowS rw = S::rows[R];
-    eval_row<DISC, VARNU, OP, T, MODE, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, x, b, y, alpha, op,
-                                                                                          tab, kp);
-  });
+  rows_fast_body<DISC, VARNU, OP, T, MODE>(blockIdx, g, x, b, y, alpha, op, kp, tab);
+}
+template <int DISC, int VARNU, int OP, class T, int MODE>
+__global__ void __launch_bounds__(256) kb_rows_fast(const void* items, int n) {
+  using Tab = FastTab<T, gen::S<DISC, VARNU, OP>::N>;
+  uint3 bid, gd;
+  const auto& it = batch_item<RowsA<T, Tab>>(items, n, bid, gd);
+  const RowsA<T, Tab>& a = it.a;
+  rows_fast_body<DISC, VARNU, OP, T, MODE>(bid, a.g, a.x, a.b, a.y, a.alpha, a.op, a.kp, *a.tab);
 }
 
 // -------------------------------------------------- Gauss-Seidel phase kernel
@@ -302,15 +338,15 @@ __device__ __forceinline__ T lane_sum(T v) {
 // NC = 3: the three velocity components at once (u, rhs: block vectors);
 // NC = 1: one component (u, rhs point to that component's first group array)
 template <int DISC, int VARNU, int GRP, class T, int LP, int NC, int T0, int N1, class Tab>
-__device__ __forceinline__ void gs_site(const Geo& g, T* __restrict__ u, const T* __restrict__ rhs, T inv_diag,
-                                        int colour, const Tab& tab) {
+__device__ __forceinline__ void gs_site(const uint3 bid, const Geo& g, T* __restrict__ u, const T* __restrict__ rhs,
+                                        T inv_diag, int colour, const Tab& tab) {
   constexpr int ox = GRP == 1 || GRP == 4 || GRP == 5 || GRP == 7;
   constexpr int oy = GRP == 2 || GRP == 4 || GRP == 6 || GRP == 7;
   constexpr int oz = GRP == 3 || GRP == 5 || GRP == 6 || GRP == 7;
   constexpr int P = 1 << LP;
-  const int k = blockIdx.z;
+  const int k = bid.z;
   const int w = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1 - ox;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = bid.x * blockDim.x + threadIdx.x;
   const int site = q >> LP, p = q & (P - 1);
   const int j = site / w;
   int i = site - j * w;
@@ -374,8 +410,20 @@ __global__ void __launch_bounds__(256)
   constexpr gen::RowS rw = S::rows[GRP];       // component-0 row of the group; all terms in segment 1
   static_assert(rw.n0 == 0 && rw.n2 == 0, "A rows carry only nu-scaled terms");
   pdl_wait();
-  gs_site<DISC, VARNU, GRP, T, LP, NC, rw.t0, rw.n1>(g, u, rhs, inv_diag, colour, tab);
+  gs_site<DISC, VARNU, GRP, T, LP, NC, rw.t0, rw.n1>(blockIdx, g, u, rhs, inv_diag, colour, tab);
   pdl_trigger();
+}
+template <class T, class Tab>
+struct GsA { Geo g; T* u; const T* rhs; T inv_diag; int colour; const Tab* tab; };
+template <int DISC, int VARNU, int GRP, class T, int LP, int NC>
+__global__ void __launch_bounds__(256) kb_gs_fast(const void* items, int n) {
+  using S = gen::S<DISC, VARNU, OP_A>;
+  using Tab = FastTab<T, S::N>;
+  constexpr gen::RowS rw = S::rows[GRP];
+  uint3 bid, gd;
+  const auto& it = batch_item<GsA<T, Tab>>(items, n, bid, gd);
+  const GsA<T, Tab>& a = it.a;
+  gs_site<DISC, VARNU, GRP, T, LP, NC, rw.t0, rw.n1>(bid, a.g, a.u, a.rhs, a.inv_diag, a.colour, *a.tab);
 }
 
 }  // namespace
@@ -401,68 +449,60 @@ void launch_pdl(K kernel, dim3 grd, dim3 blk, cudaStream_t s, A... args) {
   cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// launch geometry of the row kernels (plain launch and batch recording)
+struct RowsGeo {
+  dim3 grd, blk;
+  int kp;
+  bool vec;          // four sites per thread (k_rows_vec)
+};
 template <int DISC, int VARNU, int OP, class T>
-void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, const T* x, const T* b, T* y,
-                      double alpha, const Shape& sh, cudaStream_t s) {
+RowsGeo rows_geo(const Geo& g, int mode, const Shape& sh) {
   using S = gen::S<DISC, VARNU, OP>;
-  using Tab = FastTab<T, S::N>;
-  const Tab& tb = *static_cast<const Tab*>(tab);
   int nt = sh.row_threads, kp = sh.row_kplanes, sites = sizeof(T) == 8 ? sh.row_sites64 : sh.row_sites;
   if (OP == OP_BT && sh.bt_threads) {
     nt = sh.bt_threads; kp = sh.bt_kplanes; sites = sh.bt_sites;
   } else if (OP == OP_BC && sh.bc_threads) {
     nt = sh.bc_threads; kp = sh.bc_kplanes; sites = sh.bc_sites;
   }
-  dim3 blk(nt, 1, 1);
-  ++g_launches;
-  if (sites == 4 && mode != MODE_ADD) {
+  RowsGeo r;
+  r.blk = dim3(nt, 1, 1);
+  r.kp = kp;
+  r.vec = sites == 4 && mode != MODE_ADD;
+  if (r.vec) {
     // warps of 4 x 32 positions over the padded plane up to the last site
     const int64_t warps = ((int64_t(g.ny) * g.sx + g.nx + 1) + 127) / 128;
-    dim3 grd(unsigned((warps * 32 + nt - 1) / nt), (g.nz + 1 + kp - 1) / kp, S::R);
-    auto go = [&](auto vc) {
-      constexpr int V = decltype(vc)::value;
-      if (mode == MODE_SET) k_rows_vec<DISC, VARNU, OP, T, MODE_SET, V><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
-      else k_rows_vec<DISC, VARNU, OP, T, MODE_RES, V><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
-    };
-    go(std::integral_constant<int, 4>{});
-    return;
+    r.grd = dim3(unsigned((warps * 32 + nt - 1) / nt), (g.nz + 1 + kp - 1) / kp, S::R);
+  } else {
+    const int plane = (g.nx + 1) * (g.ny + 1);
+    r.grd = dim3((plane + nt - 1) / nt, (g.nz + 1 + kp - 1) / kp, S::R);
   }
-  const int plane = (g.nx + 1) * (g.ny + 1);
-  dim3 grd((plane + nt - 1) / nt, (g.nz + 1 + kp - 1) / kp, S::R);
-  if (mode == MODE_SET) k_rows_fast<DISC, VARNU, OP, T, MODE_SET><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
-  else if (mode == MODE_RES) k_rows_fast<DISC, VARNU, OP, T, MODE_RES><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
-  else k_rows_fast<DISC, VARNU, OP, T, MODE_ADD><<<grd, blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+  return r;
 }
 
-template <int DISC, int VARNU, class T>
-void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u, const T* rhs,
-                    const Shape& sh, int comp, cudaStream_t s) {
-  using S = gen::S<DISC, VARNU, OP_A>;
-  using Tab = FastTab<T, S::N>;
-  const Tab& tb = *static_cast<const Tab*>(tab);
+// launch geometry of a Gauss-Seidel phase
+struct GsGeo {
+  dim3 grd, blk;
+  int lp;            // log2 of the lanes per site
+};
+inline GsGeo gs_geo(const Geo& g, int grp, int colour, const Shape& sh) {
   const int nt = grp == 0 && sh.gs_threads0 ? sh.gs_threads0 : sh.gs_threads;
   const int nl = grp == 0 ? sh.gs_lanes0 : sh.gs_lanes;
-  const int lp = nl == 4 ? 2 : nl == 2 ? 1 : 0;
-  dim3 blk(nt, 1, 1);
+  GsGeo r;
+  r.lp = nl == 4 ? 2 : nl == 2 ? 1 : 0;
+  r.blk = dim3(nt, 1, 1);
   const int ni = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1;
-  const int64_t plane = int64_t(ni) * (g.ny + 1) << lp;
-  dim3 grd(unsigned((plane + nt - 1) / nt), 1, g.nz + 1);
-  ++g_launches;
-  auto go = [&](auto gc, auto lc) {
-    constexpr int GRP = decltype(gc)::value, LP = decltype(lc)::value;
-    if constexpr (DISC == 2 || GRP == 0) {
-      if (comp < 0) {
-        launch_pdl(k_gs_fast<DISC, VARNU, GRP, T, LP, 3>, grd, blk, s, g, u, rhs, T(inv_diag), colour, tb);
-      } else {
-        const int64_t cs = int64_t(comp) * g.G * g.arr;   // the component's first group array
-        launch_pdl(k_gs_fast<DISC, VARNU, GRP, T, LP, 1>, grd, blk, s, g, u + cs, rhs + cs, T(inv_diag), colour, tb);
-      }
-    }
-  };
+  const int64_t plane = int64_t(ni) * (g.ny + 1) << r.lp;
+  r.grd = dim3(unsigned((plane + nt - 1) / nt), 1, g.nz + 1);
+  return r;
+}
+
+// the group and lane count of a phase as compile-time constants
+template <class F>
+void by_group_lanes(int grp, int lp, F&& f) {
   auto by_lanes = [&](auto gc) {
-    if (lp == 2) go(gc, std::integral_constant<int, 2>{});
-    else if (lp == 1) go(gc, std::integral_constant<int, 1>{});
-    else go(gc, std::integral_constant<int, 0>{});
+    if (lp == 2) f(gc, std::integral_constant<int, 2>{});
+    else if (lp == 1) f(gc, std::integral_constant<int, 1>{});
+    else f(gc, std::integral_constant<int, 0>{});
   };
   switch (grp) {
     case 0: by_lanes(std::integral_constant<int, 0>{}); break;
@@ -477,7 +517,89 @@ void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double i
   }
 }
 
-#if !defined(HHG_FAST_ONLY) || HHG_FAST_ONLY == 64
+#if defined(HHG_FAST_BATCHED)
+// ------------------------------------------------ batch recording (kb_*)
+template <int DISC, int VARNU, int OP, class T>
+void record_rows(const Geo& g, const OpDev& op, const void* tab, int mode, const T* x, const T* b, T* y,
+                 double alpha, const Shape& sh) {
+  using Tab = FastTab<T, gen::S<DISC, VARNU, OP>::N>;
+  const RowsGeo rg = rows_geo<DISC, VARNU, OP, T>(g, mode, sh);
+  const Tab* dtab = static_cast<const Tab*>(g_rec->table(tab, sizeof(Tab)));
+  const RowsA<T, Tab> ra{g, x, b, y, T(alpha), op, rg.kp, dtab};
+  const void* fn;
+  if (rg.vec)
+    fn = mode == MODE_SET ? reinterpret_cast<const void*>(kb_rows_vec<DISC, VARNU, OP, T, MODE_SET, 4>)
+                          : reinterpret_cast<const void*>(kb_rows_vec<DISC, VARNU, OP, T, MODE_RES, 4>);
+  else
+    fn = mode == MODE_SET   ? reinterpret_cast<const void*>(kb_rows_fast<DISC, VARNU, OP, T, MODE_SET>)
+         : mode == MODE_RES ? reinterpret_cast<const void*>(kb_rows_fast<DISC, VARNU, OP, T, MODE_RES>)
+                            : reinterpret_cast<const void*>(kb_rows_fast<DISC, VARNU, OP, T, MODE_ADD>);
+  g_rec->add(fn, rg.grd, rg.blk, 0, 1, ra);
+}
+
+template <int DISC, int VARNU, class T>
+void record_gs(const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u, const T* rhs,
+               const Shape& sh, int comp) {
+  using Tab = FastTab<T, gen::S<DISC, VARNU, OP_A>::N>;
+  const GsGeo gg = gs_geo(g, grp, colour, sh);
+  const Tab* dtab = static_cast<const Tab*>(g_rec->table(tab, sizeof(Tab)));
+  const int64_t cs = comp < 0 ? 0 : int64_t(comp) * g.G * g.arr;   // the component's first group array
+  by_group_lanes(grp, gg.lp, [&](auto gc, auto lc) {
+    constexpr int GRP = decltype(gc)::value, LP = decltype(lc)::value;
+    if constexpr (DISC == 2 || GRP == 0) {
+      const void* fn = comp < 0 ? reinterpret_cast<const void*>(kb_gs_fast<DISC, VARNU, GRP, T, LP, 3>)
+                                : reinterpret_cast<const void*>(kb_gs_fast<DISC, VARNU, GRP, T, LP, 1>);
+      g_rec->add(fn, gg.grd, gg.blk, 0, 1, GsA<T, Tab>{g, u + cs, rhs + cs, T(inv_diag), colour, dtab});
+    }
+  });
+}
+#else
+// ------------------------------------------------------- plain launches
+template <int DISC, int VARNU, int OP, class T>
+void launch_rows_fast(const Geo& g, const OpDev& op, const void* tab, int mode, const T* x, const T* b, T* y,
+                      double alpha, const Shape& sh, cudaStream_t s) {
+  using Tab = FastTab<T, gen::S<DISC, VARNU, OP>::N>;
+  const Tab& tb = *static_cast<const Tab*>(tab);
+  const RowsGeo rg = rows_geo<DISC, VARNU, OP, T>(g, mode, sh);
+  const int kp = rg.kp;
+  ++g_launches;
+  if (rg.vec) {
+    if (mode == MODE_SET)
+      k_rows_vec<DISC, VARNU, OP, T, MODE_SET, 4><<<rg.grd, rg.blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+    else
+      k_rows_vec<DISC, VARNU, OP, T, MODE_RES, 4><<<rg.grd, rg.blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+    return;
+  }
+  if (mode == MODE_SET)
+    k_rows_fast<DISC, VARNU, OP, T, MODE_SET><<<rg.grd, rg.blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+  else if (mode == MODE_RES)
+    k_rows_fast<DISC, VARNU, OP, T, MODE_RES><<<rg.grd, rg.blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+  else
+    k_rows_fast<DISC, VARNU, OP, T, MODE_ADD><<<rg.grd, rg.blk, 0, s>>>(g, x, b, y, T(alpha), op, kp, tb);
+}
+
+template <int DISC, int VARNU, class T>
+void launch_gs_fast(const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u, const T* rhs,
+                    const Shape& sh, int comp, cudaStream_t s) {
+  using Tab = FastTab<T, gen::S<DISC, VARNU, OP_A>::N>;
+  const Tab& tb = *static_cast<const Tab*>(tab);
+  const GsGeo gg = gs_geo(g, grp, colour, sh);
+  ++g_launches;
+  const int64_t cs = comp < 0 ? 0 : int64_t(comp) * g.G * g.arr;   // the component's first group array
+  by_group_lanes(grp, gg.lp, [&](auto gc, auto lc) {
+    constexpr int GRP = decltype(gc)::value, LP = decltype(lc)::value;
+    if constexpr (DISC == 2 || GRP == 0) {
+      if (comp < 0)
+        launch_pdl(k_gs_fast<DISC, VARNU, GRP, T, LP, 3>, gg.grd, gg.blk, s, g, u, rhs, T(inv_diag), colour, tb);
+      else
+        launch_pdl(k_gs_fast<DISC, VARNU, GRP, T, LP, 1>, gg.grd, gg.blk, s, g, u + cs, rhs + cs, T(inv_diag),
+                   colour, tb);
+    }
+  });
+}
+#endif
+
+#if (!defined(HHG_FAST_ONLY) || HHG_FAST_ONLY == 64) && !defined(HHG_FAST_BATCHED)
 int fast_terms(int disc, int varnu, int op) {
 #define HHG_N(D, V, O) if (disc == D && varnu == V && op == O) return gen::S<D, V, O>::N;
   HHG_N(1, 0, OP_FULL) HHG_N(1, 0, OP_A) HHG_N(1, 0, OP_BT) HHG_N(1, 0, OP_BC)
@@ -490,10 +612,47 @@ int fast_terms(int disc, int varnu, int op) {
 
 #endif
 
-// run-time dispatch over (disc, varnu, op)
+#if defined(HHG_FAST_BATCHED)
+// run-time dispatch over (disc, varnu, op) of the recorders
+template <class T>
+void fast_rows_record(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode,
+                      const T* x, const T* b, T* y, double alpha, const Shape& sh) {
+#define HHG_R(D, V, O) \
+  if (disc == D && varnu == V && op == O) return record_rows<D, V, O, T>(g, od, tab, mode, x, b, y, alpha, sh);
+  HHG_R(1, 0, OP_FULL) HHG_R(1, 0, OP_BT) HHG_R(1, 0, OP_BC)
+  HHG_R(1, 1, OP_FULL) HHG_R(1, 1, OP_BT) HHG_R(1, 1, OP_BC)
+  HHG_R(2, 0, OP_FULL) HHG_R(2, 0, OP_BT) HHG_R(2, 0, OP_BC)
+  HHG_R(2, 1, OP_FULL) HHG_R(2, 1, OP_BT) HHG_R(2, 1, OP_BC)
+#undef HHG_R
+}
+
+template <class T>
+void fast_gs_record(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
+                    const T* rhs, const Shape& sh, int comp) {
+  if (disc == 1 && !varnu) record_gs<1, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp);
+  else if (disc == 1) record_gs<1, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp);
+  else if (!varnu) record_gs<2, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp);
+  else record_gs<2, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp);
+}
+
+#if HHG_FAST_ONLY == 64
+template void fast_rows_record<double>(int, int, int, const Geo&, const OpDev&, const void*, int, const double*,
+                                       const double*, double*, double, const Shape&);
+template void fast_gs_record<double>(int, int, const Geo&, const void*, int, int, double, double*, const double*,
+                                     const Shape&, int);
+#else
+template void fast_rows_record<float>(int, int, int, const Geo&, const OpDev&, const void*, int, const float*,
+                                      const float*, float*, double, const Shape&);
+template void fast_gs_record<float>(int, int, const Geo&, const void*, int, int, double, float*, const float*,
+                                    const Shape&, int);
+#endif
+#else
+// run-time dispatch over (disc, varnu, op); while a batch records, the
+// recorders (the batched translation units) take the launch
 template <class T>
 void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode, const T* x,
                const T* b, T* y, double alpha, const Shape& sh, cudaStream_t s) {
+  if (g_rec) return fast_rows_record<T>(disc, varnu, op, g, od, tab, mode, x, b, y, alpha, sh);
 #define HHG_R(D, V, O) \
   if (disc == D && varnu == V && op == O) return launch_rows_fast<D, V, O, T>(g, od, tab, mode, x, b, y, alpha, sh, s);
   HHG_R(1, 0, OP_FULL) HHG_R(1, 0, OP_BT) HHG_R(1, 0, OP_BC)
@@ -506,6 +665,7 @@ void fast_rows(int disc, int varnu, int op, const Geo& g, const OpDev& od, const
 template <class T>
 void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
              const T* rhs, const Shape& sh, cudaStream_t s, int comp) {
+  if (g_rec) return fast_gs_record<T>(disc, varnu, g, tab, grp, colour, inv_diag, u, rhs, sh, comp);
   if (disc == 1 && !varnu) launch_gs_fast<1, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp, s);
   else if (disc == 1) launch_gs_fast<1, 1, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp, s);
   else if (!varnu) launch_gs_fast<2, 0, T>(g, tab, grp, colour, inv_diag, u, rhs, sh, comp, s);
@@ -525,6 +685,7 @@ template void fast_rows<float>(int, int, int, const Geo&, const OpDev&, const vo
                                float*, double, const Shape&, cudaStream_t);
 template void fast_gs<float>(int, int, const Geo&, const void*, int, int, double, float*, const float*, const Shape&,
                              cudaStream_t, int);
+#endif
 #endif
 
 }  // namespace hhg

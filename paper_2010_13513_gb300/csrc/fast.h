@@ -60,4 +60,13 @@ template <class T>
 void fast_gs(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
              const T* rhs, const Shape& sh, cudaStream_t s, int comp = -1);
 
+// the same two calls as work items of a batch being recorded (batch.h): the
+// batched kernels live in their own translation units
+template <class T>
+void fast_rows_record(int disc, int varnu, int op, const Geo& g, const OpDev& od, const void* tab, int mode,
+                      const T* x, const T* b, T* y, double alpha, const Shape& sh);
+template <class T>
+void fast_gs_record(int disc, int varnu, const Geo& g, const void* tab, int grp, int colour, double inv_diag, T* u,
+                    const T* rhs, const Shape& sh, int comp);
+
 }  // namespace hhg

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "batch.h"
 #include "kernels.h"
 
 namespace hhg {
@@ -169,35 +170,67 @@ __global__ void __launch_bounds__(128) k_gs(Geo g, OpDev A, int grp, int colour,
 }
 
 // --------------------------------------------------------- pressure update
+// Every kernel below is a device body that takes its block index (and grid
+// size) as arguments, a plain kernel that passes blockIdx, and a batched
+// kernel (kb_*) that runs the body for one work item of a merged launch.
 template <class T>
-__global__ void k_pupdate(Geo g, T* __restrict__ p, const T* __restrict__ r, const double* __restrict__ inv_ml,
-                          double s) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
+struct PUpdateA { Geo g; T* p; const T* r; const double* inv_ml; double s; };
+template <class T>
+__device__ __forceinline__ void pupdate_body(const uint3 bid, const Geo& g, T* __restrict__ p, const T* __restrict__ r,
+                                             const double* __restrict__ inv_ml, double s) {
+  const int i = bid.x * blockDim.x + threadIdx.x;
+  const int j = bid.y * blockDim.y + threadIdx.y;
+  const int k = bid.z;
   if (i > g.nx || j > g.ny) return;
   const int64_t idx = site_index(g, i, j, k);
   p[idx] -= T(s * inv_ml[idx]) * r[idx];
 }
+template <class T>
+__global__ void k_pupdate(Geo g, T* __restrict__ p, const T* __restrict__ r, const double* __restrict__ inv_ml,
+                          double s) {
+  pupdate_body<T>(blockIdx, g, p, r, inv_ml, s);
+}
+template <class T>
+__global__ void kb_pupdate(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<PUpdateA<T>>(items, n, bid, gd);
+  pupdate_body<T>(bid, it.a.g, it.a.p, it.a.r, it.a.inv_ml, it.a.s);
+}
 
 template <class T>
-__global__ void k_sub_scalar_p(Geo g, T* __restrict__ p, const double* __restrict__ sum, double scale) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
+struct SubScalarA { Geo g; T* p; const double* sum; double scale; };
+template <class T>
+__device__ __forceinline__ void sub_scalar_body(const uint3 bid, const Geo& g, T* __restrict__ p,
+                                                const double* __restrict__ sum, double scale) {
+  const int i = bid.x * blockDim.x + threadIdx.x;
+  const int j = bid.y * blockDim.y + threadIdx.y;
+  const int k = bid.z;
   if (i > g.nx || j > g.ny) return;
   p[site_index(g, i, j, k)] -= T(sum[0] * scale);
+}
+template <class T>
+__global__ void k_sub_scalar_p(Geo g, T* __restrict__ p, const double* __restrict__ sum, double scale) {
+  sub_scalar_body<T>(blockIdx, g, p, sum, scale);
+}
+template <class T>
+__global__ void kb_sub_scalar_p(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<SubScalarA<T>>(items, n, bid, gd);
+  sub_scalar_body<T>(bid, it.a.g, it.a.p, it.a.sum, it.a.scale);
 }
 
 // ---------------------------------------------------------------- transfers
 template <class T>
-__global__ void __launch_bounds__(128) k_prolong(Geo gf, Geo gc, XferDev X, int base_f, int base_c, int ncomp, int G,
-                                                 int interior_only, const T* __restrict__ xc, T* __restrict__ xf) {
+struct XferA { Geo gf, gc; XferDev X; int base_f, base_c, ncomp, G, interior_only; const T* in; T* out; };
+template <class T>
+__device__ __forceinline__ void prolong_body(const uint3 bid, const Geo& gf, const Geo& gc, const XferDev& X,
+                                             int base_f, int base_c, int ncomp, int G, int interior_only,
+                                             const T* __restrict__ xc, T* __restrict__ xf) {
   const int nzp = gf.nz + 1;
-  const int gfi = blockIdx.z / nzp;
-  const int k = blockIdx.z - gfi * nzp;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int gfi = bid.z / nzp;
+  const int k = bid.z - gfi * nzp;
+  const int i = bid.x * blockDim.x + threadIdx.x;
+  const int j = bid.y * blockDim.y + threadIdx.y;
   const int ox = G == 1 ? 0 : c_goff[gfi][0], oy = G == 1 ? 0 : c_goff[gfi][1], oz = G == 1 ? 0 : c_goff[gfi][2];
   if (!dof_valid(gf, i, j, k, ox, oy, oz)) return;
   if (interior_only && dof_boundary(gf, i, j, k, ox, oy, oz)) return;
@@ -224,19 +257,32 @@ __global__ void __launch_bounds__(128) k_prolong(Geo gf, Geo gc, XferDev X, int 
     xf[int64_t(base_f + gfi) * gf.arr + c * cstride_f + fidx] += a;
   }
 }
+template <class T>
+__global__ void __launch_bounds__(128) k_prolong(Geo gf, Geo gc, XferDev X, int base_f, int base_c, int ncomp, int G,
+                                                 int interior_only, const T* __restrict__ xc, T* __restrict__ xf) {
+  prolong_body<T>(blockIdx, gf, gc, X, base_f, base_c, ncomp, G, interior_only, xc, xf);
+}
+template <class T>
+__global__ void __launch_bounds__(128) kb_prolong(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<XferA<T>>(items, n, bid, gd);
+  const XferA<T>& a = it.a;
+  prolong_body<T>(bid, a.gf, a.gc, a.X, a.base_f, a.base_c, a.ncomp, a.G, a.interior_only, a.in, a.out);
+}
 
 // r_c = I^T r_f per coarse DoF: its restriction terms (up to 125 for the P2
 // vertex group) are shared by P lanes, lane p taking terms p, p+P, ..., and
 // the partial sums are added by shuffles.  Block: 128 threads = 128/P coarse
 // sites along i; grid: (i blocks, j, (k, group)).
 template <class T, int P>
-__global__ void __launch_bounds__(128) k_restrict(Geo gf, Geo gc, XferDev X, int base_f, int base_c, int ncomp, int G,
-                                                  int interior_only, const T* __restrict__ rf, T* __restrict__ rc) {
+__device__ __forceinline__ void restrict_body(const uint3 bid, const Geo& gf, const Geo& gc, const XferDev& X,
+                                              int base_f, int base_c, int ncomp, int G, int interior_only,
+                                              const T* __restrict__ rf, T* __restrict__ rc) {
   const int nzp = gc.nz + 1;
-  const int gci = blockIdx.z / nzp;
-  const int k = blockIdx.z - gci * nzp;
-  const int i = blockIdx.x * (128 / P) + int(threadIdx.x) / P, p = int(threadIdx.x) % P;
-  const int j = blockIdx.y;
+  const int gci = bid.z / nzp;
+  const int k = bid.z - gci * nzp;
+  const int i = bid.x * (128 / P) + int(threadIdx.x) / P, p = int(threadIdx.x) % P;
+  const int j = bid.y;
   const int ox = G == 1 ? 0 : c_goff[gci][0], oy = G == 1 ? 0 : c_goff[gci][1], oz = G == 1 ? 0 : c_goff[gci][2];
   const bool valid = dof_valid(gc, i, j, k, ox, oy, oz);
   const bool zero = valid && interior_only && dof_boundary(gc, i, j, k, ox, oy, oz);
@@ -272,6 +318,18 @@ __global__ void __launch_bounds__(128) k_restrict(Geo gf, Geo gc, XferDev X, int
     o[cstride_c] = zero ? T(0) : a1;
     o[2 * cstride_c] = zero ? T(0) : a2;
   }
+}
+template <class T, int P>
+__global__ void __launch_bounds__(128) k_restrict(Geo gf, Geo gc, XferDev X, int base_f, int base_c, int ncomp, int G,
+                                                  int interior_only, const T* __restrict__ rf, T* __restrict__ rc) {
+  restrict_body<T, P>(blockIdx, gf, gc, X, base_f, base_c, ncomp, G, interior_only, rf, rc);
+}
+template <class T, int P>
+__global__ void __launch_bounds__(128) kb_restrict(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<XferA<T>>(items, n, bid, gd);
+  const XferA<T>& a = it.a;
+  restrict_body<T, P>(bid, a.gf, a.gc, a.X, a.base_f, a.base_c, a.ncomp, a.G, a.interior_only, a.in, a.out);
 }
 
 // ------------------------------------------ canonical order <-> padded layout
@@ -325,12 +383,14 @@ __global__ void k_canon_gather(Geo g, const T* __restrict__ src, double* __restr
 }
 
 // ---------------------------------------------------------------- reductions
+template <class T>
+struct ReduceA { const T* a; const T* b; const double* w; int64_t n; double* partials; };
 template <class T, int MODE>
-__global__ void __launch_bounds__(256) k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b,
-                                                        const double* __restrict__ w, int64_t n,
-                                                        double* __restrict__ partials) {
+__device__ __forceinline__ void reduce_partial_body(const uint3 bid, const uint3 gd, const T* __restrict__ a,
+                                                    const T* __restrict__ b, const double* __restrict__ w, int64_t n,
+                                                    double* __restrict__ partials) {
   double s = 0.0;
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t q = bid.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gd.x) * blockDim.x) {
     const double va = double(a[q]);
     if (MODE == RED_SQ) s += va * va;
     else if (MODE == RED_DOT) s += va * double(b[q]);
@@ -344,12 +404,25 @@ __global__ void __launch_bounds__(256) k_reduce_partial(const T* __restrict__ a,
   if (threadIdx.x < 32) {
     s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    if (threadIdx.x == 0) partials[bid.x] = s;
   }
 }
+template <class T, int MODE>
+__global__ void __launch_bounds__(256) k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b,
+                                                        const double* __restrict__ w, int64_t n,
+                                                        double* __restrict__ partials) {
+  reduce_partial_body<T, MODE>(blockIdx, gridDim, a, b, w, n, partials);
+}
+template <class T, int MODE>
+__global__ void __launch_bounds__(256) kb_reduce_partial(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<ReduceA<T>>(items, n, bid, gd);
+  reduce_partial_body<T, MODE>(bid, gd, it.a.a, it.a.b, it.a.w, it.a.n, it.a.partials);
+}
 
-__global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__ partials, int n,
-                                                      double* __restrict__ out) {
+struct FinalA { const double* partials; int n; double* out; };
+__device__ __forceinline__ void reduce_final_body(const double* __restrict__ partials, int n,
+                                                  double* __restrict__ out) {
   double s = 0.0;
   for (int q = threadIdx.x; q < n; q += blockDim.x) s += partials[q];
   __shared__ double sh[32];
@@ -362,12 +435,24 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__
     if (threadIdx.x == 0) out[0] = s;
   }
 }
+__global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__ partials, int n,
+                                                      double* __restrict__ out) {
+  reduce_final_body(partials, n, out);
+}
+__global__ void __launch_bounds__(256) kb_reduce_final(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<FinalA>(items, n, bid, gd);
+  reduce_final_body(it.a.partials, it.a.n, it.a.out);
+}
 
 // --------------------------------------------------------------- coarse solve
 template <class T>
-__global__ void __launch_bounds__(128) k_coarse(const double* __restrict__ Z, int n, const int64_t* __restrict__ idx,
-                                                const T* __restrict__ b, T* __restrict__ x) {
-  const int r = blockIdx.x;
+struct CoarseA { const double* Z; int n; const int64_t* idx; const T* b; T* x; };
+template <class T>
+__device__ __forceinline__ void coarse_body(const uint3 bid, const double* __restrict__ Z, int n,
+                                            const int64_t* __restrict__ idx, const T* __restrict__ b,
+                                            T* __restrict__ x) {
+  const int r = bid.x;
   double s = 0.0;
   for (int q = threadIdx.x; q < n; q += blockDim.x) s += Z[int64_t(r) * n + q] * double(b[idx[q]]);
   __shared__ double sh[4];
@@ -376,15 +461,59 @@ __global__ void __launch_bounds__(128) k_coarse(const double* __restrict__ Z, in
   __syncthreads();
   if (threadIdx.x == 0) x[idx[r]] = T(sh[0] + sh[1] + sh[2] + sh[3]);
 }
+template <class T>
+__global__ void __launch_bounds__(128) k_coarse(const double* __restrict__ Z, int n, const int64_t* __restrict__ idx,
+                                                const T* __restrict__ b, T* __restrict__ x) {
+  coarse_body<T>(blockIdx, Z, n, idx, b, x);
+}
+template <class T>
+__global__ void __launch_bounds__(128) kb_coarse(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<CoarseA<T>>(items, n, bid, gd);
+  coarse_body<T>(bid, it.a.Z, it.a.n, it.a.idx, it.a.b, it.a.x);
+}
 
 // ------------------------------------------------------------ element-wise
+// grid-stride loops of the element-wise kernels: q runs over
+// bid.x * blockDim.x + threadIdx.x, stepping by the item's grid
+#define HHG_GRID_LOOP(q, n) \
+  for (int64_t q = bid.x * int64_t(blockDim.x) + threadIdx.x; q < (n); q += int64_t(gd.x) * blockDim.x)
+
+struct CastA { const double* a; float* b; int64_t n; };
+__device__ __forceinline__ void cast_d2f_body(const uint3 bid, const uint3 gd, const double* __restrict__ a,
+                                              float* __restrict__ b, int64_t n) {
+  HHG_GRID_LOOP(q, n) b[q] = float(a[q]);
+}
 __global__ void k_cast_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
-    b[q] = float(a[q]);
+  cast_d2f_body(blockIdx, gridDim, a, b, n);
+}
+__global__ void kb_cast_d2f(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<CastA>(items, n, bid, gd);
+  cast_d2f_body(bid, gd, it.a.a, it.a.b, it.a.n);
+}
+struct AddF2dA { const float* a; double* b; int64_t n; };
+__device__ __forceinline__ void add_f2d_body(const uint3 bid, const uint3 gd, const float* __restrict__ a,
+                                             double* __restrict__ b, int64_t n) {
+  HHG_GRID_LOOP(q, n) b[q] += double(a[q]);
 }
 __global__ void k_add_f2d(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
-    b[q] += double(a[q]);
+  add_f2d_body(blockIdx, gridDim, a, b, n);
+}
+__global__ void kb_add_f2d(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<AddF2dA>(items, n, bid, gd);
+  add_f2d_body(bid, gd, it.a.a, it.a.b, it.a.n);
+}
+// zero n 4-byte words
+struct ZeroA { unsigned* p; int64_t n; };
+__device__ __forceinline__ void zero_body(const uint3 bid, const uint3 gd, unsigned* __restrict__ p, int64_t n) {
+  HHG_GRID_LOOP(q, n) p[q] = 0u;
+}
+__global__ void kb_zero(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<ZeroA>(items, n, bid, gd);
+  zero_body(bid, gd, it.a.p, it.a.n);
 }
 template <class T>
 __global__ void k_axpy(T alpha, const T* __restrict__ x, T* __restrict__ y, int64_t n) {
@@ -392,9 +521,21 @@ __global__ void k_axpy(T alpha, const T* __restrict__ x, T* __restrict__ y, int6
     y[q] += alpha * x[q];
 }
 template <class T>
+struct XpbyA { const T* x; T beta; const T* y; T* z; int64_t n; };
+template <class T>
+__device__ __forceinline__ void xpby_body(const uint3 bid, const uint3 gd, const T* __restrict__ x, T beta,
+                                          const T* __restrict__ y, T* __restrict__ z, int64_t n) {
+  HHG_GRID_LOOP(q, n) z[q] = x[q] + beta * y[q];
+}
+template <class T>
 __global__ void k_xpby(const T* __restrict__ x, T beta, const T* __restrict__ y, T* __restrict__ z, int64_t n) {
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
-    z[q] = x[q] + beta * y[q];
+  xpby_body<T>(blockIdx, gridDim, x, beta, y, z, n);
+}
+template <class T>
+__global__ void kb_xpby(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<XpbyA<T>>(items, n, bid, gd);
+  xpby_body<T>(bid, gd, it.a.x, it.a.beta, it.a.y, it.a.z, it.a.n);
 }
 __global__ void k_inv(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
   for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x)
@@ -406,9 +547,23 @@ inline int lin_blocks(int64_t n) { return int(std::min<int64_t>((n + 255) / 256,
 }  // namespace
 
 // ============================================================ host wrappers
+// While a batch records (g_rec set), each wrapper records its launch instead:
+// a work item of the batched kernel, or (kernels without one) the launch itself.
+#define HHG_NATIVE(...)                                                   \
+  if (g_rec) {                                                            \
+    g_rec->native([=](cudaStream_t s_) { __VA_ARGS__; });                 \
+    return;                                                               \
+  }
+#define HHG_BATCHED(fn, grd, blk, A, ...)                                                                   \
+  if (g_rec) {                                                                                             \
+    g_rec->add(reinterpret_cast<const void*>(fn), grd, blk, 0, 1, A{__VA_ARGS__});                        \
+    return;                                                                                                \
+  }
+
 template <class T>
 void launch_apply(const Geo& g, const OpDev& op, int mode, const T* x, const T* b, T* y, double alpha,
                   cudaStream_t s) {
+  HHG_NATIVE(launch_apply<T>(g, op, mode, x, b, y, alpha, s_))
   dim3 blk(32, 4, 1);
   if (op.nrows == 0) return;
   dim3 grd((g.nx + 1 + 31) / 32, (g.ny + 1 + 3) / 4, (g.nz + 1) * op.nrows);
@@ -421,6 +576,7 @@ void launch_apply(const Geo& g, const OpDev& op, int mode, const T* x, const T* 
 template <class T>
 void launch_apply_shell(const Geo& g, const OpDev& op, int mode, const T* x, const T* b, T* y, double alpha,
                         cudaStream_t s) {
+  HHG_NATIVE(launch_apply_shell<T>(g, op, mode, x, b, y, alpha, s_))
   if (op.nrows == 0) return;
   if (g.nx < 4 || g.ny < 4 || g.nz < 4) return launch_apply<T>(g, op, mode, x, b, y, alpha, s);
   auto go = [&](int inner) {
@@ -439,6 +595,7 @@ void launch_apply_shell(const Geo& g, const OpDev& op, int mode, const T* x, con
 template <class T>
 void launch_gs(const Geo& g, const OpDev& A, int grp, int colour, double inv_diag, T* u, const T* rhs,
                cudaStream_t s) {
+  HHG_NATIVE(launch_gs<T>(g, A, grp, colour, inv_diag, u, rhs, s_))
   dim3 blk(32, 4, 1);
   const int ni = colour >= 0 ? (g.nx + 1 + 3) / 4 : g.nx + 1;
   dim3 grd((ni + 31) / 32, (g.ny + 1 + 3) / 4, g.nz + 1);
@@ -450,6 +607,7 @@ template <class T>
 void launch_pupdate(const Geo& g, T* p, const T* r, const double* inv_mlhat, double inv_omega_inv, cudaStream_t s) {
   dim3 blk(32, 4, 1);
   dim3 grd((g.nx + 1 + 31) / 32, (g.ny + 1 + 3) / 4, g.nz + 1);
+  HHG_BATCHED(kb_pupdate<T>, grd, blk, PUpdateA<T>, g, p, r, inv_mlhat, inv_omega_inv)
   ++g_launches;
   k_pupdate<T><<<grd, blk, 0, s>>>(g, p, r, inv_mlhat, inv_omega_inv);
 }
@@ -458,6 +616,7 @@ template <class T>
 void launch_sub_scalar_p(const Geo& g, T* p, const double* sum, double scale, cudaStream_t s) {
   dim3 blk(32, 4, 1);
   dim3 grd((g.nx + 1 + 31) / 32, (g.ny + 1 + 3) / 4, g.nz + 1);
+  HHG_BATCHED(kb_sub_scalar_p<T>, grd, blk, SubScalarA<T>, g, p, sum, scale)
   ++g_launches;
   k_sub_scalar_p<T><<<grd, blk, 0, s>>>(g, p, sum, scale);
 }
@@ -467,6 +626,7 @@ void launch_prolong(const Geo& gf, const Geo& gc, const XferDev& X, int base_f, 
                     bool interior_only, const T* xc, T* xf, cudaStream_t s) {
   dim3 blk(32, 4, 1);
   dim3 grd((gf.nx + 1 + 31) / 32, (gf.ny + 1 + 3) / 4, (gf.nz + 1) * G);
+  HHG_BATCHED(kb_prolong<T>, grd, blk, XferA<T>, gf, gc, X, base_f, base_c, ncomp, G, interior_only ? 1 : 0, xc, xf)
   ++g_launches;
   k_prolong<T><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, interior_only ? 1 : 0, xc, xf);
 }
@@ -478,8 +638,16 @@ void launch_restrict(const Geo& gf, const Geo& gc, const XferDev& X, int base_f,
   const int P = X.rmax > 32 ? 8 : X.rmax > 16 ? 4 : X.rmax > 8 ? 2 : 1;
   dim3 blk(128, 1, 1);
   dim3 grd((gc.nx + 1 + 128 / P - 1) / (128 / P), gc.ny + 1, (gc.nz + 1) * G);
-  ++g_launches;
   const int io = interior_only ? 1 : 0;
+  if (g_rec) {
+    const void* fn = P == 8   ? reinterpret_cast<const void*>(kb_restrict<T, 8>)
+                     : P == 4 ? reinterpret_cast<const void*>(kb_restrict<T, 4>)
+                     : P == 2 ? reinterpret_cast<const void*>(kb_restrict<T, 2>)
+                              : reinterpret_cast<const void*>(kb_restrict<T, 1>);
+    g_rec->add(fn, grd, blk, 0, 1, XferA<T>{gf, gc, X, base_f, base_c, ncomp, G, io, rf, rc});
+    return;
+  }
+  ++g_launches;
   switch (P) {
     case 8: k_restrict<T, 8><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, io, rf, rc); break;
     case 4: k_restrict<T, 4><<<grd, blk, 0, s>>>(gf, gc, X, base_f, base_c, ncomp, G, io, rf, rc); break;
@@ -493,6 +661,15 @@ void launch_reduce(int mode, const T* a, const T* b, const double* w, int64_t n,
                    double* out, cudaStream_t s) {
   int nb = int(std::min<int64_t>((n + 255) / 256, max_blocks));
   if (nb < 1) nb = 1;
+  if (g_rec) {
+    const void* fn = mode == RED_SQ     ? reinterpret_cast<const void*>(kb_reduce_partial<T, RED_SQ>)
+                     : mode == RED_DOT  ? reinterpret_cast<const void*>(kb_reduce_partial<T, RED_DOT>)
+                     : mode == RED_WSUM ? reinterpret_cast<const void*>(kb_reduce_partial<T, RED_WSUM>)
+                                        : reinterpret_cast<const void*>(kb_reduce_partial<T, RED_SUM>);
+    g_rec->add(fn, dim3(nb), dim3(256), 0, 1, ReduceA<T>{a, b, w, n, partials});
+    g_rec->add(reinterpret_cast<const void*>(kb_reduce_final), dim3(1), dim3(256), 0, 1, FinalA{partials, nb, out});
+    return;
+  }
   g_launches += 2;
   switch (mode) {
     case RED_SQ: k_reduce_partial<T, RED_SQ><<<nb, 256, 0, s>>>(a, b, w, n, partials); break;
@@ -506,6 +683,7 @@ void launch_reduce(int mode, const T* a, const T* b, const double* w, int64_t n,
 template <class T>
 void launch_canon_scatter(const Geo& g, const double* src, T* dst, int64_t nvn, int64_t npn, bool with_pressure,
                           bool boundary_only, cudaStream_t s) {
+  HHG_NATIVE(launch_canon_scatter<T>(g, src, dst, nvn, npn, with_pressure, boundary_only, s_))
   ++g_launches;
   dim3 grd(unsigned(std::min<int64_t>((nvn + 255) / 256, 152 * 8)), with_pressure ? 4 : 3);
   k_canon_scatter<T><<<grd, 256, 0, s>>>(g, src, dst, nvn, npn, boundary_only ? 1 : 0);
@@ -513,6 +691,7 @@ void launch_canon_scatter(const Geo& g, const double* src, T* dst, int64_t nvn, 
 
 template <class T>
 void launch_canon_gather(const Geo& g, const T* src, double* dst, int64_t nvn, int64_t npn, cudaStream_t s) {
+  HHG_NATIVE(launch_canon_gather<T>(g, src, dst, nvn, npn, s_))
   ++g_launches;
   dim3 grd(unsigned(std::min<int64_t>((nvn + 255) / 256, 152 * 8)), 4);
   k_canon_gather<T><<<grd, 256, 0, s>>>(g, src, dst, nvn, npn);
@@ -520,31 +699,47 @@ void launch_canon_gather(const Geo& g, const T* src, double* dst, int64_t nvn, i
 
 template <class T>
 void launch_coarse(const double* Z, int n, const int64_t* idx, const T* b, T* x, cudaStream_t s) {
+  HHG_BATCHED(kb_coarse<T>, dim3(n), dim3(128), CoarseA<T>, Z, n, idx, b, x)
   ++g_launches;
   k_coarse<T><<<n, 128, 0, s>>>(Z, n, idx, b, x);
 }
 
 void launch_cast_d2f(const double* a, float* b, int64_t n, cudaStream_t s) {
+  HHG_BATCHED(kb_cast_d2f, dim3(lin_blocks(n)), dim3(256), CastA, a, b, n)
   ++g_launches;
   k_cast_d2f<<<lin_blocks(n), 256, 0, s>>>(a, b, n);
 }
 void launch_add_f2d(const float* a, double* b, int64_t n, cudaStream_t s) {
+  HHG_BATCHED(kb_add_f2d, dim3(lin_blocks(n)), dim3(256), AddF2dA, a, b, n)
   ++g_launches;
   k_add_f2d<<<lin_blocks(n), 256, 0, s>>>(a, b, n);
 }
 template <class T>
 void launch_axpy(double alpha, const T* x, T* y, int64_t n, cudaStream_t s) {
+  HHG_NATIVE(launch_axpy<T>(alpha, x, y, n, s_))
   ++g_launches;
   k_axpy<T><<<lin_blocks(n), 256, 0, s>>>(T(alpha), x, y, n);
 }
 template <class T>
 void launch_xpby(const T* x, double beta, const T* y, T* z, int64_t n, cudaStream_t s) {
+  HHG_BATCHED(kb_xpby<T>, dim3(lin_blocks(n)), dim3(256), XpbyA<T>, x, T(beta), y, z, n)
   ++g_launches;
   k_xpby<T><<<lin_blocks(n), 256, 0, s>>>(x, T(beta), y, z, n);
 }
 void launch_inv(const double* a, double* b, int64_t n, cudaStream_t s) {
+  HHG_NATIVE(launch_inv(a, b, n, s_))
   ++g_launches;
   k_inv<<<lin_blocks(n), 256, 0, s>>>(a, b, n);
+}
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) {
+  if (g_rec) {
+    const int64_t words = int64_t(bytes / 4);
+    g_rec->add(reinterpret_cast<const void*>(kb_zero), dim3(lin_blocks(words)), dim3(256), 0, 1,
+               ZeroA{static_cast<unsigned*>(p), words}, 0);
+    return cudaSuccess;
+  }
+  return cudaMemsetAsync(p, 0, bytes, s);
 }
 
 template void launch_canon_scatter<double>(const Geo&, const double*, double*, int64_t, int64_t, bool, bool, cudaStream_t);

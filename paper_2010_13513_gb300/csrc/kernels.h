@@ -71,6 +71,8 @@ void launch_axpy(double alpha, const T* x, T* y, int64_t n, cudaStream_t s);   /
 template <class T>
 void launch_xpby(const T* x, double beta, const T* y, T* z, int64_t n, cudaStream_t s);  // z = x + beta y
 void launch_inv(const double* a, double* b, int64_t n, cudaStream_t s);        // b = 1/a where a != 0
+// bytes (a multiple of 4) of zeros at p (cudaMemsetAsync; a merged op while a batch records)
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
 
 extern thread_local int64_t g_launches;   // kernels issued by this thread
 

@@ -13,6 +13,7 @@
 #include <tuple>
 #include <vector>
 
+#include "batch.h"
 #include "fast.h"
 #include "internal.h"
 #include "kernels.h"
@@ -612,8 +613,15 @@ bool stream_op(hhg_problem* pb, Level& lv, const Shape& sh, int op, int mode, co
   if (si < 0 || mode == MODE_ADD || !lv.has_stream[op]) return false;
   const int nt = sizeof(T) == 8 ? sh.st64_threads[si] : sh.st_threads[si];
   const int ns = sizeof(T) == 8 ? 4 : sh.st_sites[si];
-  return nt && stream_rows<T>(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, op, mode, lv.g, stab<T>(lv, op), x, b, y,
-                              nt, ns, pb->stream);
+  if (!nt) return false;
+  const int disc = pb->desc.disc, varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
+  if (g_rec) {                  // a batch records: the streaming passes stay separate launches
+    const Geo g = lv.g;
+    const void* tab = stab<T>(lv, op);
+    g_rec->native([=](cudaStream_t s_) { stream_rows<T>(disc, varnu, op, mode, g, tab, x, b, y, nt, ns, s_); });
+    return true;
+  }
+  return stream_rows<T>(disc, varnu, op, mode, lv.g, stab<T>(lv, op), x, b, y, nt, ns, pb->stream);
 }
 
 template <class T>
@@ -818,7 +826,7 @@ template <class T> int coarse_nn(hhg_problem* pb, const T* b, T* x);
 template <class T>
 int coarse_solve(hhg_problem* pb, const T* b, T* x) {
   Level& lv = pb->lv[0];
-  HHG_CUDA(cudaMemsetAsync(x, 0, size_t(lv.nvec()) * sizeof(T), pb->stream));
+  HHG_CUDA(launch_zero(x, size_t(lv.nvec()) * sizeof(T), pb->stream));
   if (pb->nn_recording) {
     nn_gather<T>(b, pb->cidx, pb->nn_n, pb->nn_xin, pb->nn_scal, pb->stream);
     nn_record(pb->nn_xin, pb->nn_X, pb->nn_n, pb->nn_S, pb->nn_counts + 2, pb->stream);
@@ -849,7 +857,7 @@ int vcycle(hhg_problem* pb, int lf, int l, const hhg_params& prm, T* x, const T*
   HHG_TRY(restrict_to<T>(pb, l, vt<T>(lv), vb<T>(lc)));
   // the coarse correction starts from a zero guess (Algorithm 1)
   if (l - 1 > pb->desc.coarse_level)
-    HHG_CUDA(cudaMemsetAsync(vx<T>(lc), 0, size_t(lc.nvec()) * sizeof(T), pb->stream));
+    HHG_CUDA(launch_zero(vx<T>(lc), size_t(lc.nvec()) * sizeof(T), pb->stream));
   HHG_TRY(vcycle<T>(pb, lf, l - 1, prm, vx<T>(lc), vb<T>(lc)));
   HHG_TRY(prolong_add<T>(pb, l, vx<T>(lc), x));
   HHG_TRY(uzawa<T>(pb, lv, prm, prm.nu_post + extra, x, b, vt<T>(lv)));
@@ -869,7 +877,7 @@ int fmg_interpolate(hhg_problem* pb, int l) {
   Level& f = pb->L(l);
   Level& c = pb->L(l - 1);
   launch_xpby<double>(c.x64, 1.0, c.W, c.tmp64, c.nvec(), pb->stream);
-  HHG_CUDA(cudaMemsetAsync(f.x64, 0, size_t(f.nvec()) * 8, pb->stream));
+  HHG_CUDA(launch_zero(f.x64, size_t(f.nvec()) * 8, pb->stream));
   HHG_TRY(prolong_add<double>(pb, l, c.tmp64, f.x64, true));
   return HHG_OK;
 }
@@ -1434,7 +1442,7 @@ int fmg_core(hhg_problem* pb, const hhg_params* prm) {
         // iterative refinement: FP64 residual, FP32 V-cycle on the defect, FP64 update
         HHG_TRY(residual<double>(pb, lv, lv.x64, lv.rhs, lv.tmp64));
         launch_cast_d2f(lv.tmp64, lv.b32, lv.nvec(), pb->stream);
-        HHG_CUDA(cudaMemsetAsync(lv.x32, 0, size_t(lv.nvec()) * 4, pb->stream));
+        HHG_CUDA(launch_zero(lv.x32, size_t(lv.nvec()) * 4, pb->stream));
         HHG_TRY(vcycle<float>(pb, l, l, *prm, lv.x32, lv.b32));
         launch_add_f2d(lv.x32, lv.x64, lv.nvec(), pb->stream);
         HHG_CHECK_LAUNCH();
@@ -2026,6 +2034,8 @@ struct hhg_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<hhg_params> key;            // parameters the graph was recorded with
   int64_t kernels = 0;
+  int64_t ops = 0;                        // kernels of the problems' own sequences
+  std::unique_ptr<Recorder> rec;          // device tables and work items of the merged launches
   ~hhg_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     for (auto e : events) cudaEventDestroy(e);
@@ -2072,6 +2082,84 @@ bool same_params(const std::vector<hhg_params>& a, const hhg_params* b) {
 }
 }  // namespace
 
+namespace {
+// every problem's FMG on its own branch of one graph (batches whose problems
+// use the learned coarse correction, whose kernels are not recorded)
+int capture_branches(hhg_batch* bt, const hhg_params* params, cudaGraph_t* graph) {
+  const int n = int(bt->pbs.size());
+  cudaStream_t cap = bt->streams[0];
+  const int64_t l0 = g_launches;
+  HHG_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  int rc = HHG_OK;
+  cudaError_t ce = cudaEventRecord(bt->fork, cap);
+  for (int i = 0; i < n && rc == HHG_OK && ce == cudaSuccess; ++i) {
+    hhg_problem* pb = bt->pbs[i];
+    if (i > 0) ce = cudaStreamWaitEvent(bt->streams[i], bt->fork, 0);
+    if (ce != cudaSuccess) break;
+    cudaStream_t keep = pb->stream;
+    pb->stream = bt->streams[i];
+    rc = fmg_core(pb, &params[i]);
+    pb->stream = keep;
+    if (i > 0 && rc == HHG_OK) {
+      ce = cudaEventRecord(bt->events[i], bt->streams[i]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, bt->events[i], 0);
+    }
+  }
+  cudaError_t ee = cudaStreamEndCapture(cap, graph);
+  if (rc != HHG_OK) return rc;
+  if (ce != cudaSuccess || ee != cudaSuccess)
+    return fail(HHG_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+  bt->kernels = bt->ops = g_launches - l0;
+  return HHG_OK;
+}
+
+struct RecordScope {
+  explicit RecordScope(Recorder* r) { g_rec = r; }
+  ~RecordScope() { g_rec = nullptr; }
+};
+
+// record every problem's FMG, merge the sequences into shared launches over
+// all problems (batch.h) and capture those launches as one chain
+int capture_merged(hhg_batch* bt, const hhg_params* params, cudaGraph_t* graph) {
+  const int n = int(bt->pbs.size());
+  auto rec = std::make_unique<Recorder>();
+  {
+    RecordScope scope(rec.get());
+    for (int i = 0; i < n; ++i) {
+      rec->begin(i);
+      HHG_TRY(fmg_core(bt->pbs[i], &params[i]));
+    }
+  }
+  std::vector<BatchLaunch> launches;
+  const int me = rec->merge(launches);
+  if (me != 0) return fail(HHG_ECUDA, std::string("batch merge: ") + cudaGetErrorString(cudaError_t(me)));
+  for (const BatchLaunch& l : launches) {
+    if (l.native) continue;
+    if (l.smem > 48 * 1024)
+      HHG_CUDA(cudaFuncSetAttribute(l.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(l.smem)));
+    if (l.cluster > 8) HHG_CUDA(cudaFuncSetAttribute(l.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  }
+  cudaStream_t cap = bt->streams[0];
+  int64_t natives = 0, merged = 0;
+  const int64_t l0 = g_launches;
+  HHG_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = cudaSuccess;
+  for (const BatchLaunch& l : launches) {
+    ce = launch_merged(l, rec->items(), cap);
+    if (ce != cudaSuccess) break;
+    if (l.native) ++natives;
+    else ++merged;
+  }
+  cudaError_t ee = cudaStreamEndCapture(cap, graph);
+  if (ce != cudaSuccess || ee != cudaSuccess)
+    return fail(HHG_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+  bt->kernels = merged + (g_launches - l0);
+  bt->ops = rec->batched_kernels() + (g_launches - l0);
+  bt->rec = std::move(rec);
+  return HHG_OK;
+}
+}  // namespace
+
 extern "C" int hhg_batch_fmg_solve(hhg_batch* bt, const hhg_params* params, void* stream, int64_t* kernels) {
   if (!bt || !params) return fail(HHG_EINVAL, "hhg_batch_fmg_solve: null argument");
   const int n = int(bt->pbs.size());
@@ -2079,40 +2167,28 @@ extern "C" int hhg_batch_fmg_solve(hhg_batch* bt, const hhg_params* params, void
   cudaStream_t s0 = static_cast<cudaStream_t>(stream);
   if (!bt->exec || !same_params(bt->key, params)) {
     if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
-    // record every problem's FMG on its own branch of one graph
-    cudaStream_t cap = bt->streams[0];
-    const int64_t l0 = g_launches;
-    HHG_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    int rc = HHG_OK;
-    cudaError_t ce = cudaEventRecord(bt->fork, cap);
-    for (int i = 0; i < n && rc == HHG_OK && ce == cudaSuccess; ++i) {
-      hhg_problem* pb = bt->pbs[i];
-      if (i > 0) ce = cudaStreamWaitEvent(bt->streams[i], bt->fork, 0);
-      if (ce != cudaSuccess) break;
-      cudaStream_t keep = pb->stream;
-      pb->stream = bt->streams[i];
-      rc = fmg_core(pb, &params[i]);
-      pb->stream = keep;
-      if (i > 0 && rc == HHG_OK) {
-        ce = cudaEventRecord(bt->events[i], bt->streams[i]);
-        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, bt->events[i], 0);
-      }
-    }
+    bool plain = true;
+    for (hhg_problem* pb : bt->pbs) plain = plain && pb->nn_mode == 0 && !pb->nn_recording;
     cudaGraph_t graph = nullptr;
-    cudaError_t ee = cudaStreamEndCapture(cap, &graph);
-    if (rc != HHG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
-    if (ce != cudaSuccess || ee != cudaSuccess) {
+    const int rc = plain ? capture_merged(bt, params, &graph) : capture_branches(bt, params, &graph);
+    if (rc != HHG_OK) {
       if (graph) cudaGraphDestroy(graph);
-      return fail(HHG_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+      return rc;
     }
     cudaError_t ei = cudaGraphInstantiate(&bt->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) return fail(HHG_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(ei));
     bt->key.assign(params, params + n);
-    bt->kernels = g_launches - l0;
   }
   HHG_CUDA(cudaGraphLaunch(bt->exec, s0));
   if (kernels) *kernels = bt->kernels;
+  return HHG_OK;
+}
+
+extern "C" int hhg_batch_launch_counts(const hhg_batch* bt, int64_t* launches, int64_t* problem_kernels) {
+  if (!bt || !launches || !problem_kernels) return fail(HHG_EINVAL, "hhg_batch_launch_counts: null argument");
+  *launches = bt->kernels;
+  *problem_kernels = bt->ops;
   return HHG_OK;
 }
 

@@ -38,6 +38,7 @@
 
 #include <type_traits>
 
+#include "batch.h"
 #include "kernels.h"
 #include "small.h"
 
@@ -123,10 +124,12 @@ __device__ __forceinline__ void set_desc(PhaseDesc& d, int ninst, int terms, int
 // lanes that may share the rows of a Gauss-Seidel phase
 constexpr int kPhaseLanes = 256;
 
+// the smoother of one cluster (the kernel below, or one work item of a
+// merged launch over several problems' clusters)
 template <class T>
-__global__ void __launch_bounds__(kResidentThreads)
-    k_uzawa_resident(Geo g, int arr_l, int arr_t, T* xg, const T* __restrict__ b, const double* __restrict__ inv_ml,
-                     const __grid_constant__ SmallArgs a, OpDev bc_op, const __grid_constant__ ResTabs<T> tb) {
+__device__ __forceinline__ void uzawa_resident_body(const Geo& g, int arr_l, int arr_t, T* xg,
+                                                    const T* __restrict__ b, const double* __restrict__ inv_ml,
+                                                    const SmallArgs& a, const OpDev& bc_op, const ResTabs<T>& tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PhaseDesc sd[13];                     // GS phases 0..nph-1, then B^T, then (B, -C)
   __shared__ T sdiag[8];
@@ -384,6 +387,26 @@ __global__ void __launch_bounds__(kResidentThreads)
   }
 }
 
+template <class T>
+__global__ void __launch_bounds__(kResidentThreads)
+    k_uzawa_resident(Geo g, int arr_l, int arr_t, T* xg, const T* __restrict__ b, const double* __restrict__ inv_ml,
+                     const __grid_constant__ SmallArgs a, OpDev bc_op, const __grid_constant__ ResTabs<T> tb) {
+  uzawa_resident_body<T>(g, arr_l, arr_t, xg, b, inv_ml, a, bc_op, tb);
+}
+
+template <class T>
+struct ResA { Geo g; int arr_l, arr_t; T* xg; const T* b; const double* inv_ml; SmallArgs a; OpDev bc_op;
+              const ResTabs<T>* tb; };
+// every cluster of the merged grid belongs to one item (items start at
+// multiples of the cluster size)
+template <class T>
+__global__ void __launch_bounds__(kResidentThreads) kb_uzawa_resident(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<ResA<T>>(items, n, bid, gd);
+  const ResA<T>& r = it.a;
+  uzawa_resident_body<T>(r.g, r.arr_l, r.arr_t, r.xg, r.b, r.inv_ml, r.a, r.bc_op, *r.tb);
+}
+
 template <class T> constexpr int prec_of() { return sizeof(T) == 8 ? HHG_FP64 : HHG_FP32; }
 
 void fill_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int C, int threads, size_t smem,
@@ -457,8 +480,14 @@ int uzawa_resident(const Geo& g, int ctas, int threads, T* x, const T* b, const 
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   fill_config(cfg, attr, ctas, threads, resident_smem(g, ctas, prec_of<T>()), s);
-  ++g_launches;
   const int arr_l = int(resident_arr(g, ctas)), arr_t = int(resident_arr_t(g, ctas));
+  if (g_rec) {
+    const ResTabs<T>* dt = static_cast<const ResTabs<T>*>(g_rec->table(&tabs, sizeof(ResTabs<T>)));
+    g_rec->add(reinterpret_cast<const void*>(kb_uzawa_resident<T>), dim3(ctas), dim3(threads), cfg.dynamicSmemBytes,
+               ctas, ResA<T>{g, arr_l, arr_t, x, b, inv_ml, a, bc_op, dt});
+    return dt ? 0 : -1;
+  }
+  ++g_launches;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_uzawa_resident<T>, g, arr_l, arr_t, x, b, inv_ml, a, bc_op, tabs);
   return e == cudaSuccess ? 0 : -1;
 }

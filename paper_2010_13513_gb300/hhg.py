@@ -122,6 +122,7 @@ def load():
         "hhg_coarse_nn_counts": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
         "hhg_batch_destroy": [P],
         "hhg_batch_fmg_solve": [P, C.POINTER(Params), VP, C.POINTER(C.c_int64)],
+        "hhg_batch_launch_counts": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -452,7 +453,9 @@ class Problem:
 
 
 class Batch:
-    """Independent problems solved by one CUDA graph with one branch per problem."""
+    """Independent problems solved by one CUDA graph of merged launches: each
+    launch runs the same kernel for all problems whose sequences reach it,
+    over the flat list of their work items."""
 
     def __init__(self, problems):
         lib = load()
@@ -469,6 +472,12 @@ class Batch:
         _check(load().hhg_batch_fmg_solve(self.h, prm, C.c_void_p(stream.cuda_stream), C.byref(k)),
                "hhg_batch_fmg_solve")
         return k.value
+
+    def launch_counts(self):
+        """(kernels of the batch graph, kernels of the problems' own sequences)."""
+        a, b = C.c_int64(), C.c_int64()
+        _check(load().hhg_batch_launch_counts(self.h, C.byref(a), C.byref(b)), "hhg_batch_launch_counts")
+        return a.value, b.value
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -485,9 +485,10 @@ def test_cluster_smoother_matches_per_phase_launches(disc, L, lc, solve, ahat):
 
 
 def test_batch_graph_matches_individual_solves():
-    """A batch of uneven problems (P1-P1 / P2-P1, different boxes and
-    levels) solved by one graph with one branch per problem gives exactly the
-    individual FMG results."""
+    """A batch of uneven problems (P1-P1 / P2-P1, different boxes, levels and
+    precisions) solved by one graph of merged launches gives exactly the
+    individual FMG results, in fewer launches than the problems' own
+    sequences."""
     from hhg_inputs import Workload
     from paper_2010_13513_gb300 import hhg
     stream = torch.cuda.Stream()
@@ -508,10 +509,50 @@ def test_batch_graph_matches_individual_solves():
         for rep in range(2):
             k = batch.fmg_solve(prms, stream)
         stream.synchronize()
-    assert k > 0
+    launches, own = batch.launch_counts()
+    assert launches == k and 0 < k < own
     for pb, ref in zip(pbs, refs):
         got = pb.level_vector(pb.L, "x")
         assert torch.equal(got, ref)
+
+
+def test_batch_merges_aligned_problems():
+    """Problems whose kernel sequences align (same discretisation, level and
+    parameters; boxes of different shape) share every launch: the batch graph
+    has about one problem's launches, and every problem still gets exactly its
+    individual FMG result (the resident cluster smoother, the row and
+    Gauss-Seidel kernels, transfers, reductions and the coarse solve all run
+    as merged work-item lists)."""
+    from hhg_inputs import Workload
+    from paper_2010_13513_gb300 import hhg
+    stream = torch.cuda.Stream()
+    specs = [("P2P1", (1, 1, 1)), ("P2P1", (2, 1, 1)), ("P2P1", (1, 2, 1)), ("P2P1", (1, 1, 2)),
+             ("P1P1", (1, 1, 1)), ("P1P1", (2, 2, 1)), ("P1P1", (1, 2, 2))]
+    pbs, prms, refs = [], [], []
+    own_each = []
+    with torch.cuda.stream(stream):
+        for i, (disc, box) in enumerate(specs):
+            wl = Workload("modes", seed=200 + i, box=box, H=1.0 / max(box))
+            lc = 1 if disc == "P2P1" else 0
+            pb = lib_problem(box, 4, disc, lc=lc, solve="mixed", workload=wl)
+            prm = hhg.Params.make(1, 2, 1, 1, "f", 2, OMEGA_INV[disc])
+            x = pb.new_vector(4)
+            st = pb.fmg_solve(prm, x)
+            own_each.append(st.kernel_launches)
+            pbs.append(pb)
+            prms.append(prm)
+            refs.append(x.clone())
+        batch = hhg.Batch(pbs)
+        k = batch.fmg_solve(prms, stream)
+        k = batch.fmg_solve(prms, stream)
+        stream.synchronize()
+    launches, own = batch.launch_counts()
+    assert own == sum(own_each)
+    # one P2-P1 and one P1-P1 sequence, give or take the few kernels the two
+    # discretisations share
+    assert launches <= max(own_each[:4]) + max(own_each[4:]), (launches, own_each)
+    for pb, ref in zip(pbs, refs):
+        assert torch.equal(pb.level_vector(pb.L, "x"), ref)
 
 
 def test_autotune_keeps_results():
