@@ -424,6 +424,14 @@ def run_batched(args):
     graph_kernels, problem_kernels = batch.launch_counts()
     t_batch = timed(lambda: batch.fmg_solve(prms, stream), args.steps)
     t_seq = timed(lambda: [pb.fmg_solve(prm, None, stats=False) for pb, prm in zip(pbs, prms)], max(1, args.steps // 2))
+    # the other groupings of the batch's sequences (hhg_batch_set_grouping)
+    groupings = {0: {"ms": t_batch * 1e3, "graph_kernels": graph_kernels}}
+    for grouping in (1, 2):
+        batch.set_grouping(grouping)
+        batch.fmg_solve(prms, stream)
+        groupings[grouping] = {"ms": timed(lambda: batch.fmg_solve(prms, stream), args.steps) * 1e3,
+                               "graph_kernels": batch.launch_counts()[0]}
+    batch.set_grouping(0)
     clocks = sampler.stop()
     # accuracy of a few problems: delta against the discrete solution (Eq. relative-error)
     deltas = []
@@ -451,6 +459,9 @@ def run_batched(args):
                                    "random smooth forcing (8 sine modes per component), zero Dirichlet data",
                        "dofs": dofs, "problems": len(pbs), "graph_kernels": graph_kernels,
                        "problem_kernels": problem_kernels, "setup_s": t_setup,
+                       "groupings": {"0 (cohorts of identical sequences)": groupings[0],
+                                     "1 (cohorts by structure)": groupings[1],
+                                     "2 (one branch per problem, no merging)": groupings[2]},
                        "sequential_ms": t_seq * 1e3, "batch_speedup_vs_sequential": t_seq / t_batch,
                        "accuracy": deltas},
             "clocks": clocks}
@@ -731,6 +742,7 @@ def learned_coarse(pb, wl, prm, steps, warmup, stream):
     plain dense coarse solve; training on the GPU by the library's own
     forward/backward kernels.  Then the gated FMG (network accepted only if
     its coarse residual passes the gate) and the network alone."""
+    import torch
     from hhg_inputs import Workload
     from paper_2010_13513_gb300 import hhg
     L, lc = WORKLOAD["L"], WORKLOAD["lc"]
@@ -753,9 +765,14 @@ def learned_coarse(pb, wl, prm, steps, warmup, stream):
         pb.nn_counts()
         tt = statistics.mean(time_steps(pb, prm, x, steps, warmup, stream)) * 1e-3
         acc, rej = pb.nn_counts()
-        gg = accuracy(pb, wl, prm, x)
-        out[name] = {"ms_per_step": tt * 1e3, "gamma_u": gg[0], "gamma_p": gg[1], "accepted": acc, "rejected": rej}
+        # gamma of this FMG's solution x against the discrete solution, which
+        # the plain coarse solve computes
         pb.nn_enable(0)
+        if bool(torch.isfinite(x).all()):
+            gg = accuracy(pb, wl, prm, x)
+        else:
+            gg = (None, None)           # the FMG diverged
+        out[name] = {"ms_per_step": tt * 1e3, "gamma_u": gg[0], "gamma_p": gg[1], "accepted": acc, "rejected": rej}
     return out
 
 

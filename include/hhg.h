@@ -336,7 +336,14 @@ int hhg_coarse_nn_counts(hhg_problem* pb, int64_t* accepted, int64_t* rejected);
  * problem may belong to one batch at a time).  The handles are borrowed: the
  * problems must outlive the batch.  The batch owns n CUDA streams and
  * events, and (after the first solve) the device copies of the stencil
- * tables and the work-item lists of its merged launches. */
+ * tables and the work-item lists of its merged launches.  Creating the batch
+ * gives its problems common launch shapes, so that their kernels can share
+ * launches: on each level, every problem of a discretisation takes the
+ * launch shape of the one with the most DoFs there; the resident smoother
+ * keeps each problem's CTA count and
+ * takes the CTA size of the largest problem with that count.  Later
+ * hhg_fmg_solve calls of the problems use these shapes too (hhg_autotune or
+ * hhg_set_launch_shape change them again). */
 int hhg_batch_create(hhg_problem* const* problems, int n, hhg_batch** out);
 int hhg_batch_destroy(hhg_batch* batch);
 /* FMG (Algorithm 1) of every problem of the batch, params[i] for problem i.
@@ -346,9 +353,10 @@ int hhg_batch_destroy(hhg_batch* batch);
  * block shape become ONE launch over the flat list of (problem, block) work
  * items, each item with its own problem's arguments; each problem's own
  * order is kept, and the problems share no data, so every problem gets
- * exactly its individual hhg_fmg_solve result.  The merged launches are
- * captured as one CUDA graph (the streaming row passes of large levels stay
- * launches of their own).  Batches with a problem that uses the learned
+ * exactly its individual hhg_fmg_solve result.  The problems form cohorts
+ * (hhg_batch_set_grouping) whose sequences are merged; each cohort's merged
+ * launches form one chain of a CUDA graph, and the cohorts run as parallel
+ * branches.  Batches with a problem that uses the learned
  * coarse correction record one graph branch per problem instead.  The graph
  * is launched on `stream` (cudaStream_t, must not be the legacy default
  * stream).  Each problem's solution ends in its workspace
@@ -358,6 +366,16 @@ int hhg_batch_fmg_solve(hhg_batch* batch, const hhg_params* params, void* stream
 /* after a solve: *launches = kernels of the batch graph, *problem_kernels =
  * the kernels of the problems' own sequences (their sum over the problems) */
 int hhg_batch_launch_counts(const hhg_batch* batch, int64_t* launches, int64_t* problem_kernels);
+/* How the batch's sequences are grouped (next solve; drops the cached graph).
+ * 0 (default): cohorts of problems whose kernel sequences are the same op
+ * for op (discretisation, precision, coarse and finest level, viscosity
+ * model, smoothing tuple, resident-smoother CTA counts per level) -- many
+ * short chains side by side.  1: cohorts by discretisation, precision,
+ * coarse level, viscosity model and smoothing tuple only, whatever the
+ * problems' sizes -- fewer, longer chains and fewer launches; the merge
+ * aligns the sequences as far as they agree.  2: no merging, one graph
+ * branch per problem.  HHG_EINVAL otherwise. */
+int hhg_batch_set_grouping(hhg_batch* batch, int grouping);
 
 /* Whether hhg_fmg_solve records its kernel sequence once per parameter tuple
  * as a CUDA graph and replays it (default on).  Graphs are used only when the

@@ -26,7 +26,11 @@ SOURCES = [("kernels.cu", "kernels", []), ("fast.cu", "fast64", ["-DHHG_FAST_ONL
            ("fast.cu", "fast64b", ["-DHHG_FAST_ONLY=64", "-DHHG_FAST_BATCHED"]),
            ("fast.cu", "fast32b", ["-DHHG_FAST_ONLY=32", "-DHHG_FAST_BATCHED"]), ("stream.cu", "stream64", ["-DHHG_STREAM_ONLY=64"]),
            ("stream.cu", "stream32", ["-DHHG_STREAM_ONLY=32"]),
-           ("stream.cu", "stream32v2", ["-DHHG_STREAM_ONLY=32", "-DHHG_STREAM_V=2"]), ("small.cu", "small", []),
+           ("stream.cu", "stream32v2", ["-DHHG_STREAM_ONLY=32", "-DHHG_STREAM_V=2"]),
+           ("stream.cu", "stream64b", ["-DHHG_STREAM_ONLY=64", "-DHHG_STREAM_BATCHED"]),
+           ("stream.cu", "stream32b", ["-DHHG_STREAM_ONLY=32", "-DHHG_STREAM_BATCHED"]),
+           ("stream.cu", "stream32v2b", ["-DHHG_STREAM_ONLY=32", "-DHHG_STREAM_V=2", "-DHHG_STREAM_BATCHED"]),
+           ("small.cu", "small", []),
            ("nn.cu", "nn", []), ("noalloc.cu", "noalloc", []), ("stencils.cpp", "stencils", []),
            ("batch.cpp", "batch", []), ("problem.cpp", "problem", [])]
 

@@ -53,15 +53,21 @@ int Recorder::merge(std::vector<BatchLaunch>& out) {
   std::vector<unsigned char> host;
   std::vector<const BatchOp*> heads(np);
   for (;;) {
-    // the kind with the most problems at their next op (ties: the earliest problem)
-    int best = -1, best_count = 0;
-    for (size_t p = 0; p < np; ++p) heads[p] = cur[p] < lists_[p].size() ? &lists_[p][cur[p]] : nullptr;
+    // among the problems that are furthest behind (fewest ops taken), the
+    // kind that most of them run next (ties: the earliest problem); every
+    // problem whose next op is of that kind joins the launch
+    size_t behind = ~size_t(0);
     for (size_t p = 0; p < np; ++p) {
-      if (!heads[p]) continue;
+      heads[p] = cur[p] < lists_[p].size() ? &lists_[p][cur[p]] : nullptr;
+      if (heads[p]) behind = std::min(behind, cur[p]);
+    }
+    int best = -1, best_count = 0;
+    for (size_t p = 0; p < np; ++p) {
+      if (!heads[p] || cur[p] != behind) continue;
       int count = 1;
       if (!heads[p]->native)
         for (size_t q = p + 1; q < np; ++q)
-          if (heads[q] && same_kind(*heads[p], *heads[q])) ++count;
+          if (heads[q] && cur[q] == behind && same_kind(*heads[p], *heads[q])) ++count;
       if (count > best_count) {
         best = int(p);
         best_count = count;
@@ -82,7 +88,7 @@ int Recorder::merge(std::vector<BatchLaunch>& out) {
     l.items = (host.size() + 15) / 16 * 16;
     host.resize(l.items);
     int64_t blocks = 0;
-    for (size_t p = best; p < np; ++p) {
+    for (size_t p = 0; p < np; ++p) {
       if (!heads[p] || !same_kind(k, *heads[p])) continue;
       const BatchOp& op = *heads[p];
       const int64_t nb = int64_t(op.grid.x) * op.grid.y * op.grid.z;

@@ -615,12 +615,6 @@ bool stream_op(hhg_problem* pb, Level& lv, const Shape& sh, int op, int mode, co
   const int ns = sizeof(T) == 8 ? 4 : sh.st_sites[si];
   if (!nt) return false;
   const int disc = pb->desc.disc, varnu = pb->desc.nu_a != 0.0 ? 1 : 0;
-  if (g_rec) {                  // a batch records: the streaming passes stay separate launches
-    const Geo g = lv.g;
-    const void* tab = stab<T>(lv, op);
-    g_rec->native([=](cudaStream_t s_) { stream_rows<T>(disc, varnu, op, mode, g, tab, x, b, y, nt, ns, s_); });
-    return true;
-  }
   return stream_rows<T>(disc, varnu, op, mode, lv.g, stab<T>(lv, op), x, b, y, nt, ns, pb->stream);
 }
 
@@ -2035,7 +2029,8 @@ struct hhg_batch {
   std::vector<hhg_params> key;            // parameters the graph was recorded with
   int64_t kernels = 0;
   int64_t ops = 0;                        // kernels of the problems' own sequences
-  std::unique_ptr<Recorder> rec;          // device tables and work items of the merged launches
+  int grouping = 0;                       // hhg_batch_set_grouping
+  std::vector<std::unique_ptr<Recorder>> recs;   // per cohort: device tables and work items of the merged launches
   ~hhg_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     for (auto e : events) cudaEventDestroy(e);
@@ -2063,6 +2058,33 @@ extern "C" int hhg_batch_create(hhg_problem* const* problems, int n, hhg_batch**
     bt->events.push_back(e);
   }
   HHG_CUDA(cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming));
+  // one launch shape per (discretisation, level) across the batch, so that the
+  // problems' kernels can share launches: that of the problem with the most
+  // DoFs on the level; the resident smoother keeps each problem's CTA count
+  // (it depends on the level's size) and takes, per CTA count, the largest
+  // problem's CTA size
+  for (hhg_problem* pb : bt->pbs) {
+    for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l) {
+      const hhg_problem* big = pb;
+      for (const hhg_problem* q : bt->pbs)
+        if (q->desc.disc == pb->desc.disc && l >= q->desc.coarse_level && l <= q->desc.L &&
+            const_cast<hhg_problem*>(q)->L(l).n_dofs() > const_cast<hhg_problem*>(big)->L(l).n_dofs())
+          big = q;
+      Level& lv = pb->L(l);
+      lv.shape = const_cast<hhg_problem*>(big)->L(l).shape;
+      for (int pr = 0; pr < 2; ++pr) {
+        const hhg_problem* bc = pb;
+        for (const hhg_problem* q : bt->pbs)
+          if (q->desc.disc == pb->desc.disc && l >= q->desc.coarse_level && l <= q->desc.L &&
+              const_cast<hhg_problem*>(q)->L(l).rctas[pr] == lv.rctas[pr] &&
+              const_cast<hhg_problem*>(q)->L(l).n_dofs() > const_cast<hhg_problem*>(bc)->L(l).n_dofs())
+            bc = q;
+        lv.rthreads[pr] = const_cast<hhg_problem*>(bc)->L(l).rthreads[pr];
+      }
+    }
+    for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
+    pb->graphs.clear();
+  }
   *out = bt.release();
   return HHG_OK;
 }
@@ -2119,43 +2141,89 @@ struct RecordScope {
 };
 
 // record every problem's FMG, merge the sequences into shared launches over
-// all problems (batch.h) and capture those launches as one chain
+// all problems (batch.h) and capture those launches.  The problems form
+// cohorts; each cohort's merged launches are one chain on its own branch of
+// the graph, and the cohorts run side by side.  Grouping 0: a cohort is the
+// problems whose kernel sequences are the same op for op (discretisation,
+// precision, coarse and finest level, viscosity model, smoothing tuple, and
+// which levels smooth in one resident launch with how many CTAs).  Grouping
+// 1: the problems with the same discretisation, precision, coarse level,
+// viscosity model and smoothing tuple, whatever their size (fewer, longer
+// chains; the merge aligns their sequences as far as they agree)
 int capture_merged(hhg_batch* bt, const hhg_params* params, cudaGraph_t* graph) {
   const int n = int(bt->pbs.size());
-  auto rec = std::make_unique<Recorder>();
-  {
-    RecordScope scope(rec.get());
-    for (int i = 0; i < n; ++i) {
-      rec->begin(i);
-      HHG_TRY(fmg_core(bt->pbs[i], &params[i]));
+  std::vector<std::vector<int>> keys;
+  std::vector<int> cohort(n);
+  for (int i = 0; i < n; ++i) {
+    hhg_problem* pb = bt->pbs[i];
+    const hhg_params& p = params[i];
+    const int prec = pb->desc.solve == HHG_SOLVE_FP64 ? HHG_FP64 : HHG_FP32;
+    std::vector<int> key = {pb->desc.disc, pb->desc.solve, pb->desc.coarse_level, pb->desc.nu_a != 0.0 ? 1 : 0,
+                            p.nu_pre, p.nu_post, p.nu_inc, p.kappa, p.ahat, p.xi};
+    if (bt->grouping == 0) {
+      key.push_back(pb->desc.L);
+      for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l) key.push_back(pb->L(l).rctas[prec]);
     }
+    auto it = std::find(keys.begin(), keys.end(), key);
+    cohort[i] = int(it - keys.begin());
+    if (it == keys.end()) keys.push_back(key);
   }
-  std::vector<BatchLaunch> launches;
-  const int me = rec->merge(launches);
-  if (me != 0) return fail(HHG_ECUDA, std::string("batch merge: ") + cudaGetErrorString(cudaError_t(me)));
-  for (const BatchLaunch& l : launches) {
-    if (l.native) continue;
-    if (l.smem > 48 * 1024)
-      HHG_CUDA(cudaFuncSetAttribute(l.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(l.smem)));
-    if (l.cluster > 8) HHG_CUDA(cudaFuncSetAttribute(l.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  const int nc = int(keys.size());
+  std::vector<std::unique_ptr<Recorder>> recs(nc);
+  std::vector<std::vector<BatchLaunch>> launches(nc);
+  int64_t batched = 0;
+  for (int c = 0; c < nc; ++c) {
+    recs[c] = std::make_unique<Recorder>();
+    {
+      RecordScope scope(recs[c].get());
+      int slot = 0;
+      for (int i = 0; i < n; ++i) {
+        if (cohort[i] != c) continue;
+        recs[c]->begin(slot++);
+        HHG_TRY(fmg_core(bt->pbs[i], &params[i]));
+      }
+    }
+    const int me = recs[c]->merge(launches[c]);
+    if (me != 0) return fail(HHG_ECUDA, std::string("batch merge: ") + cudaGetErrorString(cudaError_t(me)));
+    batched += recs[c]->batched_kernels();
   }
+  // function attributes before the capture: per kernel the largest dynamic
+  // shared memory of its launches, and non-portable cluster sizes
+  std::map<const void*, size_t> smem_of;
+  std::set<const void*> big_cluster;
+  for (const auto& ls : launches)
+    for (const BatchLaunch& l : ls) {
+      if (l.native) continue;
+      smem_of[l.fn] = std::max(smem_of[l.fn], l.smem);
+      if (l.cluster > 8) big_cluster.insert(l.fn);
+    }
+  for (const auto& kv : smem_of)
+    if (kv.second > 48 * 1024)
+      HHG_CUDA(cudaFuncSetAttribute(kv.first, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kv.second)));
+  for (const void* fn : big_cluster) HHG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaStream_t cap = bt->streams[0];
-  int64_t natives = 0, merged = 0;
+  int64_t merged = 0;
   const int64_t l0 = g_launches;
   HHG_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t ce = cudaSuccess;
-  for (const BatchLaunch& l : launches) {
-    ce = launch_merged(l, rec->items(), cap);
-    if (ce != cudaSuccess) break;
-    if (l.native) ++natives;
-    else ++merged;
+  cudaError_t ce = cudaEventRecord(bt->fork, cap);
+  for (int c = 0; c < nc && ce == cudaSuccess; ++c) {
+    cudaStream_t sc = bt->streams[c];
+    if (c > 0) ce = cudaStreamWaitEvent(sc, bt->fork, 0);
+    for (size_t q = 0; q < launches[c].size() && ce == cudaSuccess; ++q) {
+      ce = launch_merged(launches[c][q], recs[c]->items(), sc);
+      if (!launches[c][q].native) ++merged;
+    }
+    if (c > 0 && ce == cudaSuccess) {
+      ce = cudaEventRecord(bt->events[c], sc);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, bt->events[c], 0);
+    }
   }
   cudaError_t ee = cudaStreamEndCapture(cap, graph);
   if (ce != cudaSuccess || ee != cudaSuccess)
     return fail(HHG_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
   bt->kernels = merged + (g_launches - l0);
-  bt->ops = rec->batched_kernels() + (g_launches - l0);
-  bt->rec = std::move(rec);
+  bt->ops = batched + (g_launches - l0);
+  bt->recs = std::move(recs);
   return HHG_OK;
 }
 }  // namespace
@@ -2167,7 +2235,7 @@ extern "C" int hhg_batch_fmg_solve(hhg_batch* bt, const hhg_params* params, void
   cudaStream_t s0 = static_cast<cudaStream_t>(stream);
   if (!bt->exec || !same_params(bt->key, params)) {
     if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
-    bool plain = true;
+    bool plain = bt->grouping != 2;
     for (hhg_problem* pb : bt->pbs) plain = plain && pb->nn_mode == 0 && !pb->nn_recording;
     cudaGraph_t graph = nullptr;
     const int rc = plain ? capture_merged(bt, params, &graph) : capture_branches(bt, params, &graph);
@@ -2182,6 +2250,16 @@ extern "C" int hhg_batch_fmg_solve(hhg_batch* bt, const hhg_params* params, void
   }
   HHG_CUDA(cudaGraphLaunch(bt->exec, s0));
   if (kernels) *kernels = bt->kernels;
+  return HHG_OK;
+}
+
+extern "C" int hhg_batch_set_grouping(hhg_batch* bt, int grouping) {
+  if (!bt || grouping < 0 || grouping > 2) return fail(HHG_EINVAL, "hhg_batch_set_grouping: bad arguments");
+  if (grouping != bt->grouping && bt->exec) {
+    cudaGraphExecDestroy(bt->exec);
+    bt->exec = nullptr;
+  }
+  bt->grouping = grouping;
   return HHG_OK;
 }
 

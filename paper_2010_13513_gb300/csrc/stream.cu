@@ -48,6 +48,7 @@
 #include <type_traits>
 #include <utility>
 
+#include "batch.h"
 #include "fast.h"
 #include "internal.h"
 #include "kernels.h"
@@ -349,10 +350,12 @@ __device__ __forceinline__ void stage_plane(const T* __restrict__ x, T* buf, int
 // (tile, plane) pairs [b U / grid, (b + 1) U / grid) of the U = tiles x
 // (nz + 1) pairs, tile by tile.  On each tile a block marches through its
 // planes.
+// (bx, gx: the block's index and the grid size; the plain kernel passes
+// blockIdx.x and gridDim.x, the batched one the values of its work item)
 template <int DISC, int VARNU, int OP, int Q, class T, int MODE, int V, class Tab>
-__global__ void __launch_bounds__(256, 2)
-    k_stream(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, int lw, int64_t units,
-             int64_t tiles, int kc, const __grid_constant__ Tab tab) {
+__device__ __forceinline__ void stream_body(const unsigned bx, const unsigned gx, const Geo& g,
+                                            const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y,
+                                            int lw, int64_t units, int64_t tiles, int kc, const Tab& tab) {
   using SPT = gen::SP<DISC, VARNU, OP>;
   constexpr gen::PassT ps = SPT::passes[Q];
   constexpr int PSLOT = slot_of<SPT, Q, (DISC == 2 ? 24 : 3)>();
@@ -369,12 +372,12 @@ __global__ void __launch_bounds__(256, 2)
   const int lf = V * tid + sx + 4;                   // the thread's sites in a staged line
   int64_t u, uend;
   if (kc > 0) {
-    const int64_t t = blockIdx.x % tiles, c = blockIdx.x / tiles;
+    const int64_t t = bx % tiles, c = bx / tiles;
     u = t * nk + min(int64_t(nk), c * kc);
     uend = t * nk + min(int64_t(nk), (c + 1) * kc);
   } else {
-    u = int64_t(blockIdx.x) * units / gridDim.x;
-    uend = int64_t(blockIdx.x + 1) * units / gridDim.x;
+    u = int64_t(bx) * units / gx;
+    uend = int64_t(bx + 1) * units / gx;
   }
 #pragma unroll 1
   while (u < uend) {
@@ -424,6 +427,24 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
+template <int DISC, int VARNU, int OP, int Q, class T, int MODE, int V, class Tab>
+__global__ void __launch_bounds__(256, 2)
+    k_stream(Geo g, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y, int lw, int64_t units,
+             int64_t tiles, int kc, const __grid_constant__ Tab tab) {
+  stream_body<DISC, VARNU, OP, Q, T, MODE, V>(blockIdx.x, gridDim.x, g, x, b, y, lw, units, tiles, kc, tab);
+}
+
+// one pass as a work item of a merged batch launch (the table as a device copy)
+template <class T, class Tab>
+struct StreamA { Geo g; const T* x; const T* b; T* y; int lw; int64_t units, tiles; int kc; const Tab* tab; };
+template <int DISC, int VARNU, int OP, int Q, class T, int MODE, int V, class Tab>
+__global__ void __launch_bounds__(256, 2) kb_stream(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<StreamA<T, Tab>>(items, n, bid, gd);
+  const StreamA<T, Tab>& a = it.a;
+  stream_body<DISC, VARNU, OP, Q, T, MODE, V>(bid.x, gd.x, a.g, a.x, a.b, a.y, a.lw, a.units, a.tiles, a.kc, *a.tab);
+}
+
 // --------------------------------------------------------- launch support
 // parameter block of the streaming kernels of one operator
 template <class T, int N, int NCB> struct STab {
@@ -467,6 +488,29 @@ int sm_count() {
   return n;
 }
 
+// grid of a pass: one wave of blocks (per_sm resident blocks per SM)
+struct PassGrid {
+  int64_t grid, units, tiles;
+  int kc;
+};
+inline PassGrid pass_grid(const Geo& g, int per_sm, int M) {
+  PassGrid p;
+  p.tiles = (int64_t(g.ny + 1) * g.sx + M - 1) / M;
+  const int nk = g.nz + 1;
+  p.units = p.tiles * nk;
+  const int64_t resident = int64_t(per_sm) * sm_count();
+  p.grid = std::min<int64_t>(p.units, resident);
+  p.kc = 0;
+  // lockstep chunks if they fill at least 85 % of the resident blocks
+  const int64_t chunks = resident / p.tiles;
+  if (chunks >= 1 && p.tiles * chunks * 100 >= 85 * resident) {
+    p.kc = int((nk + chunks - 1) / chunks);
+    p.grid = p.tiles * ((nk + p.kc - 1) / p.kc);
+  }
+  return p;
+}
+
+#if !defined(HHG_STREAM_BATCHED)
 template <int DISC, int VARNU, int OP, int Q, class T, int MODE, int V>
 bool launch_pass(const Geo& g, const void* tab, const T* x, const T* b, T* y, int threads, cudaStream_t s) {
   using SPT = gen::SP<DISC, VARNU, OP>;
@@ -477,22 +521,34 @@ bool launch_pass(const Geo& g, const void* tab, const T* x, const T* b, T* y, in
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(fn), threads, smem);
   if (per_sm < 1) return false;
   const int M = V * threads;
-  const int64_t tiles = (int64_t(g.ny + 1) * g.sx + M - 1) / M;
-  const int nk = g.nz + 1;
-  const int64_t units = tiles * nk;
-  const int64_t resident = int64_t(per_sm) * sm_count();
-  int64_t grid = std::min<int64_t>(units, resident);
-  int kc = 0;
-  // lockstep chunks if they fill at least 85 % of the resident blocks
-  const int64_t chunks = resident / tiles;
-  if (chunks >= 1 && tiles * chunks * 100 >= 85 * resident) {
-    kc = int((nk + chunks - 1) / chunks);
-    grid = tiles * ((nk + kc - 1) / kc);
-  }
+  const PassGrid pg = pass_grid(g, per_sm, M);
   ++g_launches;
-  fn<<<unsigned(grid), threads, smem, s>>>(g, x, b, y, int(M + 2 * g.sx + 8), units, tiles, kc, tb);
+  fn<<<unsigned(pg.grid), threads, smem, s>>>(g, x, b, y, int(M + 2 * g.sx + 8), pg.units, pg.tiles, pg.kc, tb);
   return true;
 }
+#else
+// the same pass as a work item of the batch being recorded (batch.h); the
+// stream argument is unused
+template <int DISC, int VARNU, int OP, int Q, class T, int MODE, int V>
+bool launch_pass(const Geo& g, const void* tab, const T* x, const T* b, T* y, int threads, cudaStream_t) {
+  using SPT = gen::SP<DISC, VARNU, OP>;
+  using Tab = STabOf<DISC, VARNU, OP, T>;
+  const size_t smem = smem_bytes(SPT::NAMAX, g, threads, V, sizeof(T));
+  auto fn = kb_stream<DISC, VARNU, OP, Q, T, MODE, V, Tab>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStreamMaxSmem)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(fn), threads, smem);
+  if (per_sm < 1) return false;
+  const int M = V * threads;
+  const PassGrid pg = pass_grid(g, per_sm, M);
+  const Tab* dt = static_cast<const Tab*>(g_rec->table(tab, sizeof(Tab)));
+  g_rec->add(reinterpret_cast<const void*>(fn), dim3(unsigned(pg.grid)), dim3(threads), smem, 1,
+             StreamA<T, Tab>{g, x, b, y, int(M + 2 * g.sx + 8), pg.units, pg.tiles, pg.kc, dt});
+  return true;
+}
+#endif
 
 template <int DISC, int VARNU, int OP, class T, int MODE, int V, int... Q>
 void launch_passes(const Geo& g, const void* tab, const T* x, const T* b, T* y, int threads, cudaStream_t s,
@@ -526,6 +582,7 @@ bool launch_stream(const Geo& g, const void* tab, int mode, const T* x, const T*
   return true;
 }
 
+#if !defined(HHG_STREAM_BATCHED)
 template <int DISC, int VARNU, int OP, class T, int... Q>
 void init_passes(std::integer_sequence<int, Q...>) {
   using Tab = STabOf<DISC, VARNU, OP, T>;
@@ -540,6 +597,7 @@ template <int DISC, int VARNU, int OP, class T>
 void init_stream() {
   init_passes<DISC, VARNU, OP, T>(std::make_integer_sequence<int, gen::SP<DISC, VARNU, OP>::NP>{});
 }
+#endif
 
 // the parameter block from the weights (FastTab order) and the class sums of
 // the boundary C stencils (27 x NCB, offsets in the order of cbo)
@@ -572,12 +630,36 @@ void offsets_of(std::vector<int>& o) {
   X(1, 0, OP_FULL) X(1, 0, OP_BT) X(1, 0, OP_BC) X(1, 1, OP_FULL) X(1, 1, OP_BT) X(1, 1, OP_BC) \
   X(2, 0, OP_FULL) X(2, 0, OP_BT) X(2, 0, OP_BC) X(2, 1, OP_FULL) X(2, 1, OP_BT) X(2, 1, OP_BC)
 
+#if defined(HHG_STREAM_BATCHED)
+// the recorder of this translation unit's kernels (precision HHG_STREAM_ONLY,
+// kV sites per thread): the passes become work items of the batch being
+// recorded
+template <class T, int V>
+bool stream_rows_record_v(int disc, int varnu, int op, int mode, const Geo& g, const void* tab, const T* x,
+                          const T* b, T* y, int threads) {
+  static_assert(V == kV, "one site count per translation unit");
+  if (mode != MODE_SET && mode != MODE_RES) return false;
+#define HHG_S(D, V_, O) \
+  if (disc == D && varnu == V_ && op == O) return launch_stream<D, V_, O, T>(g, tab, mode, x, b, y, threads, nullptr);
+  HHG_STREAM_CASES(HHG_S)
+#undef HHG_S
+  return false;
+}
+#if defined(HHG_STREAM_ONLY) && HHG_STREAM_ONLY == 32
+template bool stream_rows_record_v<float, kV>(int, int, int, int, const Geo&, const void*, const float*, const float*,
+                                              float*, int);
+#else
+template bool stream_rows_record_v<double, kV>(int, int, int, int, const Geo&, const void*, const double*,
+                                               const double*, double*, int);
+#endif
+#else
 // the kernels of this translation unit (precision HHG_STREAM_ONLY, kV sites
-// per thread)
+// per thread); while a batch records, the batched units take the call
 template <class T, int V>
 bool stream_rows_v(int disc, int varnu, int op, int mode, const Geo& g, const void* tab, const T* x, const T* b, T* y,
                    int threads, cudaStream_t s) {
   static_assert(V == kV, "one site count per translation unit");
+  if (g_rec) return stream_rows_record_v<T, V>(disc, varnu, op, mode, g, tab, x, b, y, threads);
   if (mode != MODE_SET && mode != MODE_RES) return false;
 #define HHG_S(D, V_, O) \
   if (disc == D && varnu == V_ && op == O) return launch_stream<D, V_, O, T>(g, tab, mode, x, b, y, threads, s);
@@ -658,5 +740,7 @@ template void stream_init<double>();
 template void stream_init<float>();
 #endif
 #endif
+
+#endif  // HHG_STREAM_BATCHED
 
 }  // namespace hhg

@@ -37,6 +37,11 @@ bool stream_rows_v(int disc, int varnu, int op, int mode, const Geo& g, const vo
                    int threads, cudaStream_t s);
 template <class T, int V>
 void stream_init_v();
+// the same passes as work items of the batch being recorded (batch.h; the
+// batched translation units)
+template <class T, int V>
+bool stream_rows_record_v(int disc, int varnu, int op, int mode, const Geo& g, const void* tab, const T* x,
+                          const T* b, T* y, int threads);
 
 // the parameter image of op: weights w in the order of the FastTab images,
 // and wc = 27 x NCB class sums of the boundary C stencil (class index

@@ -123,6 +123,7 @@ def load():
         "hhg_batch_destroy": [P],
         "hhg_batch_fmg_solve": [P, C.POINTER(Params), VP, C.POINTER(C.c_int64)],
         "hhg_batch_launch_counts": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+        "hhg_batch_set_grouping": [P, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -472,6 +473,11 @@ class Batch:
         _check(load().hhg_batch_fmg_solve(self.h, prm, C.c_void_p(stream.cuda_stream), C.byref(k)),
                "hhg_batch_fmg_solve")
         return k.value
+
+    def set_grouping(self, grouping):
+        """0: cohorts of identical kernel sequences (default); 1: cohorts by
+        structure only, whatever the sizes; 2: one graph branch per problem."""
+        _check(load().hhg_batch_set_grouping(self.h, int(grouping)), "hhg_batch_set_grouping")
 
     def launch_counts(self):
         """(kernels of the batch graph, kernels of the problems' own sequences)."""
