@@ -257,9 +257,10 @@ def profile_apply(workload):
 
 
 def e2e_steps(pb, wl, prm, steps, profile=False):
-    """Through the public API with host data: nodal forcing/Dirichlet data from
-    host memory (hhg_set_rhs_levels: every level, assembled on the GPU, one
-    synchronisation), the FMG solve, and the solution copied back to the host."""
+    """Through the public API with host data (hhg_fmg_solve_host): nodal
+    forcing/Dirichlet data of every level from pinned host memory, assembled
+    on the GPU (the finest level beside the FMG stages below it), the FMG
+    solve, and the solution copied back to the host."""
     import torch
     from paper_2010_13513_gb300 import hhg
     L = WORKLOAD["L"]
@@ -272,14 +273,14 @@ def e2e_steps(pb, wl, prm, steps, profile=False):
         w = torch.from_numpy(np.ascontiguousarray(wl.dirichlet(X).T.ravel())).pin_memory()
         host[l] = (f, w)
         h2d += 8 * (f.numel() + w.numel())
-    x = pb.new_vector(L)
     d2h = pb.layout(L).n_dofs * 8
     out = torch.empty(pb.layout(L).n_dofs, dtype=torch.float64).pin_memory()
 
+    fl = [host[l][0] for l in sorted(host)]
+    wl_ = [host[l][1] for l in sorted(host)]
+
     def step():
-        pb.set_rhs_levels(WORKLOAD["lc"], [host[l][0] for l in sorted(host)], [host[l][1] for l in sorted(host)])
-        pb.fmg_solve(prm, x, stats=False)
-        pb.to_host(L, x, out=out)
+        pb.fmg_solve_host(prm, fl, wl_, out=out, stats=False)
 
     step()                                       # warm-up (not timed)
     if profile:
@@ -374,6 +375,33 @@ def cpu_baseline(prm_dict, level=CPU_SAMPLE_LEVEL, seconds=10.0):
             "single_core": {"value": out[1][0], "unit": "DoF/s", "cores": 1, "solves": out[1][1]}}
 
 
+def aligned_batch(timed, n=48, L=4):
+    """A batch whose kernel sequences align op for op: n P2-P1 problems on the
+    unit cube at level L (random smooth forcing, one seed each), merged
+    (grouping 0) against one graph branch per problem (grouping 2) and the
+    same solves one after another."""
+    from hhg_inputs import Workload
+    from paper_2010_13513_gb300 import hhg
+    pbs, prms = [], []
+    for i in range(n):
+        pb = hhg.Problem(hhg.Mesh.box(1, 1, 1, 1.0), disc="P2P1", L=L, coarse_level=1, solve="mixed")
+        hhg.set_workload_rhs(pb, Workload("modes", seed=9000 + i, box=(1, 1, 1), H=1.0))
+        pbs.append(pb)
+        prms.append(hhg.Params.make(**dict(PARAMS, omega_inv=0.32)))
+    pbs[0].autotune(reps=2)
+    batch = hhg.Batch(pbs)
+    out = {"problems": n, "workload": f"P2-P1 unit cube level {L}", "dofs": pbs[0].layout(L).n_dofs * n}
+    batch.fmg_solve(prms)
+    out["grouping_used"] = batch.grouping()
+    for grouping in (0, 2):
+        batch.set_grouping(grouping)
+        batch.fmg_solve(prms)
+        out[f"grouping_{grouping}"] = {"ms": timed(lambda: batch.fmg_solve(prms), 10) * 1e3,
+                                      "graph_kernels": batch.launch_counts()[0]}
+    out["sequential_ms"] = timed(lambda: [pb.fmg_solve(prm, None, stats=False) for pb, prm in zip(pbs, prms)], 3) * 1e3
+    return out
+
+
 def run_batched(args):
     """The batched workload: 64 independent problems (Kuhn boxes {1,2}^3,
     levels 3..6, P1-P1 / P2-P1, random smooth forcing, zero Dirichlet data)
@@ -425,13 +453,17 @@ def run_batched(args):
     t_batch = timed(lambda: batch.fmg_solve(prms, stream), args.steps)
     t_seq = timed(lambda: [pb.fmg_solve(prm, None, stats=False) for pb, prm in zip(pbs, prms)], max(1, args.steps // 2))
     # the other groupings of the batch's sequences (hhg_batch_set_grouping)
-    groupings = {0: {"ms": t_batch * 1e3, "graph_kernels": graph_kernels}}
-    for grouping in (1, 2):
+    used = batch.grouping()
+    groupings = {used: {"ms": t_batch * 1e3, "graph_kernels": graph_kernels}}
+    for grouping in (0, 1, 2):
+        if grouping == used:
+            continue
         batch.set_grouping(grouping)
         batch.fmg_solve(prms, stream)
         groupings[grouping] = {"ms": timed(lambda: batch.fmg_solve(prms, stream), args.steps) * 1e3,
                                "graph_kernels": batch.launch_counts()[0]}
-    batch.set_grouping(0)
+    batch.set_grouping(-1)
+    aligned = aligned_batch(timed)
     clocks = sampler.stop()
     # accuracy of a few problems: delta against the discrete solution (Eq. relative-error)
     deltas = []
@@ -459,10 +491,12 @@ def run_batched(args):
                                    "random smooth forcing (8 sine modes per component), zero Dirichlet data",
                        "dofs": dofs, "problems": len(pbs), "graph_kernels": graph_kernels,
                        "problem_kernels": problem_kernels, "setup_s": t_setup,
+                       "grouping_used": used,
                        "groupings": {"0 (cohorts of identical sequences)": groupings[0],
                                      "1 (cohorts by structure)": groupings[1],
                                      "2 (one branch per problem, no merging)": groupings[2]},
                        "sequential_ms": t_seq * 1e3, "batch_speedup_vs_sequential": t_seq / t_batch,
+                       "aligned_batch": aligned,
                        "accuracy": deltas},
             "clocks": clocks}
     print(json.dumps(line))

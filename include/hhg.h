@@ -367,15 +367,33 @@ int hhg_batch_fmg_solve(hhg_batch* batch, const hhg_params* params, void* stream
  * the kernels of the problems' own sequences (their sum over the problems) */
 int hhg_batch_launch_counts(const hhg_batch* batch, int64_t* launches, int64_t* problem_kernels);
 /* How the batch's sequences are grouped (next solve; drops the cached graph).
- * 0 (default): cohorts of problems whose kernel sequences are the same op
- * for op (discretisation, precision, coarse and finest level, viscosity
- * model, smoothing tuple, resident-smoother CTA counts per level) -- many
- * short chains side by side.  1: cohorts by discretisation, precision,
- * coarse level, viscosity model and smoothing tuple only, whatever the
- * problems' sizes -- fewer, longer chains and fewer launches; the merge
- * aligns the sequences as far as they agree.  2: no merging, one graph
- * branch per problem.  HHG_EINVAL otherwise. */
+ * 0: cohorts of problems whose kernel sequences are the same op for op
+ * (discretisation, precision, coarse and finest level, viscosity model,
+ * smoothing tuple, resident-smoother CTA counts per level) -- many short
+ * chains side by side.  1: cohorts by discretisation, precision, coarse
+ * level, viscosity model and smoothing tuple only, whatever the problems'
+ * sizes -- fewer, longer chains and fewer launches; the merge aligns the
+ * sequences as far as they agree.  2: no merging, one graph branch per
+ * problem.  -1 (default): 0 if the cohorts of grouping 0 hold at least four
+ * problems each on average, else 2.  HHG_EINVAL otherwise.
+ * hhg_batch_get_grouping: the grouping of the current graph (-1 before the
+ * first solve). */
 int hhg_batch_set_grouping(hhg_batch* batch, int grouping);
+int hhg_batch_get_grouping(const hhg_batch* batch, int* grouping);
+
+/* One end-to-end solve from host data: the right-hand sides of every level
+ * lc..L from nodal data in host memory (f_nodal[l - lc], w_nodal[l - lc] as
+ * for hhg_set_rhs), FMG (Algorithm 1) with params, and the solution in
+ * canonical order to x_host (3 n_v + n_p doubles, host; may be null).  The
+ * same results as hhg_set_rhs_levels + hhg_fmg_solve + hhg_vector_to_host;
+ * the finest level's right-hand side is assembled on a second stream while
+ * the FMG stages below it run (when they replay as graphs; the stages then
+ * run on an internal stream of the highest priority), so that its host
+ * copies and assembly overlap them.  Host buffers in pinned memory let
+ * the copies run asynchronously.  Synchronises before returning (the host
+ * buffers may then be reused).  *stats optional as for hhg_fmg_solve. */
+int hhg_fmg_solve_host(hhg_problem* pb, const hhg_params* params, const double* const* f_nodal,
+                       const double* const* w_nodal, double* x_host, hhg_stats* stats);
 
 /* Whether hhg_fmg_solve records its kernel sequence once per parameter tuple
  * as a CUDA graph and replays it (default on).  Graphs are used only when the

@@ -262,6 +262,19 @@ __device__ __forceinline__ void pdl_trigger() { cudaTriggerProgrammaticLaunchCom
 
 // FP32 P2-P1 rows: at most 80 registers (three 256-thread blocks per SM);
 // the shorter P1-P1 rows, and FP64 (bound by its arithmetic), uncapped
+// the work item's table (a device copy) staged in the block's shared memory,
+// so that the unrolled terms read their weights and offsets from there
+template <class Tab>
+__device__ __forceinline__ const Tab& stage_table(const Tab* src) {
+  extern __shared__ __align__(16) unsigned char kb_tab_smem[];
+  static_assert(sizeof(Tab) % 4 == 0, "tables are copied as 4-byte words");
+  const unsigned* s = reinterpret_cast<const unsigned*>(src);
+  unsigned* d = reinterpret_cast<unsigned*>(kb_tab_smem);
+  for (int q = threadIdx.x; q < int(sizeof(Tab) / 4); q += blockDim.x) d[q] = __ldg(s + q);
+  __syncthreads();
+  return *reinterpret_cast<const Tab*>(kb_tab_smem);
+}
+
 // arguments of the row kernels as a work item of a merged launch (the table
 // as a device copy)
 template <class T, class Tab>
@@ -291,7 +304,8 @@ __global__ void __launch_bounds__(256, DISC == 2 && sizeof(T) == 4 ? 3 : 1) kb_r
   uint3 bid, gd;
   const auto& it = batch_item<RowsA<T, Tab>>(items, n, bid, gd);
   const RowsA<T, Tab>& a = it.a;
-  rows_vec_body<DISC, VARNU, OP, T, MODE, V>(bid, a.g, a.x, a.b, a.y, a.alpha, a.op, a.kp, *a.tab);
+  const Tab& tab = stage_table(a.tab);
+  rows_vec_body<DISC, VARNU, OP, T, MODE, V>(bid, a.g, a.x, a.b, a.y, a.alpha, a.op, a.kp, tab);
 }
 
 template <int DISC, int VARNU, int OP, class T, int MODE, class Tab>
@@ -318,7 +332,8 @@ __global__ void __launch_bounds__(256) kb_rows_fast(const void* items, int n) {
   uint3 bid, gd;
   const auto& it = batch_item<RowsA<T, Tab>>(items, n, bid, gd);
   const RowsA<T, Tab>& a = it.a;
-  rows_fast_body<DISC, VARNU, OP, T, MODE>(bid, a.g, a.x, a.b, a.y, a.alpha, a.op, a.kp, *a.tab);
+  const Tab& tab = stage_table(a.tab);
+  rows_fast_body<DISC, VARNU, OP, T, MODE>(bid, a.g, a.x, a.b, a.y, a.alpha, a.op, a.kp, tab);
 }
 
 // -------------------------------------------------- Gauss-Seidel phase kernel
@@ -423,7 +438,8 @@ __global__ void __launch_bounds__(256) kb_gs_fast(const void* items, int n) {
   uint3 bid, gd;
   const auto& it = batch_item<GsA<T, Tab>>(items, n, bid, gd);
   const GsA<T, Tab>& a = it.a;
-  gs_site<DISC, VARNU, GRP, T, LP, NC, rw.t0, rw.n1>(bid, a.g, a.u, a.rhs, a.inv_diag, a.colour, *a.tab);
+  const Tab& tab = stage_table(a.tab);
+  gs_site<DISC, VARNU, GRP, T, LP, NC, rw.t0, rw.n1>(bid, a.g, a.u, a.rhs, a.inv_diag, a.colour, tab);
 }
 
 }  // namespace
@@ -534,7 +550,7 @@ void record_rows(const Geo& g, const OpDev& op, const void* tab, int mode, const
     fn = mode == MODE_SET   ? reinterpret_cast<const void*>(kb_rows_fast<DISC, VARNU, OP, T, MODE_SET>)
          : mode == MODE_RES ? reinterpret_cast<const void*>(kb_rows_fast<DISC, VARNU, OP, T, MODE_RES>)
                             : reinterpret_cast<const void*>(kb_rows_fast<DISC, VARNU, OP, T, MODE_ADD>);
-  g_rec->add(fn, rg.grd, rg.blk, 0, 1, ra);
+  g_rec->add(fn, rg.grd, rg.blk, sizeof(Tab), 1, ra);
 }
 
 template <int DISC, int VARNU, class T>
@@ -549,7 +565,7 @@ void record_gs(const Geo& g, const void* tab, int grp, int colour, double inv_di
     if constexpr (DISC == 2 || GRP == 0) {
       const void* fn = comp < 0 ? reinterpret_cast<const void*>(kb_gs_fast<DISC, VARNU, GRP, T, LP, 3>)
                                 : reinterpret_cast<const void*>(kb_gs_fast<DISC, VARNU, GRP, T, LP, 1>);
-      g_rec->add(fn, gg.grd, gg.blk, 0, 1, GsA<T, Tab>{g, u + cs, rhs + cs, T(inv_diag), colour, dtab});
+      g_rec->add(fn, gg.grd, gg.blk, sizeof(Tab), 1, GsA<T, Tab>{g, u + cs, rhs + cs, T(inv_diag), colour, dtab});
     }
   });
 }

@@ -194,10 +194,18 @@ struct hhg_problem {
   double nn_tscale = 1.0;        // training targets are multiplied by this (unit RMS)
 
   struct Graph { cudaGraphExec_t exec; int64_t kernels; double wu; };
-  std::map<std::tuple<int, int, int, int, int, int, double>, Graph> graphs;
+  // (parameter tuple, part: 0 whole solve, 1 stages below L, 2 stage L)
+  std::map<std::tuple<int, int, int, int, int, int, double, int>, Graph> graphs;
+  // second stream and events of hhg_fmg_solve_host (created on first use)
+  cudaStream_t aux = nullptr, hp = nullptr;     // assembly; the FMG's stages at the highest priority
+  cudaEvent_t ev_start = nullptr, ev_coarse = nullptr, ev_fine = nullptr, ev_done = nullptr;
 
   ~hhg_problem() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+    for (cudaStream_t st : {aux, hp})
+      if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : {ev_start, ev_coarse, ev_fine, ev_done})
+      if (e) cudaEventDestroy(e);
   }
 
   Level& L(int l) { return lv[l - desc.coarse_level]; }
@@ -1258,8 +1266,14 @@ int enqueue_rhs(hhg_problem* pb, int level, const double* f_nodal, const double*
   HHG_CHECK_LAUNCH();
   if (pb->ov == 1 && pb->desc.pspg_rhs) HHG_TRY(apply_op<double>(pb, lv, OP_LOAD, MODE_ADD, lv.tmp64, nullptr, lv.rhs, 1.0));
   const int64_t po = p_offset(lv);
-  launch_reduce<double>(RED_SUM, lv.rhs + po, nullptr, nullptr, g.arr, pb->partials, pb->max_blocks, pb->scal, pb->stream);
-  launch_sub_scalar_p<double>(g, lv.rhs + po, pb->scal, 1.0 / double((g.nx + 1) * int64_t(g.ny + 1) * (g.nz + 1)), pb->stream);
+  // the mean's partial sums in the level's own scratch vector where it holds
+  // them (so that a finest-level assembly may overlap solver stages, which use
+  // the problem's reduction buffers)
+  const bool own = lv.nvec() >= int64_t(pb->max_blocks) + 8;
+  double* part = own ? lv.bw64 : pb->partials;
+  double* sum = own ? lv.bw64 + pb->max_blocks : pb->scal;
+  launch_reduce<double>(RED_SUM, lv.rhs + po, nullptr, nullptr, g.arr, part, pb->max_blocks, sum, pb->stream);
+  launch_sub_scalar_p<double>(g, lv.rhs + po, sum, 1.0 / double((g.nx + 1) * int64_t(g.ny + 1) * (g.nz + 1)), pb->stream);
   HHG_CHECK_LAUNCH();
   HHG_CUDA(cudaMemsetAsync(lv.tmp64, 0, size_t(lv.nvec()) * 8, pb->stream));
   HHG_CUDA(cudaMemsetAsync(lv.bw64, 0, size_t(lv.nvec()) * 8, pb->stream));
@@ -1419,14 +1433,20 @@ double model_wu(const hhg_problem* pb, const hhg_params& p) {
 }  // namespace
 
 namespace {
-// the kernel sequence of one FMG solve (Algorithm 1); no host synchronisation
-int fmg_core(hhg_problem* pb, const hhg_params* prm) {
-  pb->wu_counted = 0.0;
+// the kernel sequence of one FMG solve (Algorithm 1), or of its stages
+// first..last (stage lc: the coarse solve; stage l > lc: the FMG
+// interpolation to level l and its kappa cycles); no host synchronisation
+int fmg_core(hhg_problem* pb, const hhg_params* prm, int first = -1, int last = -1) {
   const int lc = pb->desc.coarse_level;
-  Level& c = pb->L(lc);
-  HHG_TRY(coarse_solve<double>(pb, c.rhs, c.x64));
-  HHG_TRY(project_pressure(pb, c, c.x64));
-  for (int l = lc + 1; l <= pb->desc.L; ++l) {
+  if (first < 0) first = lc;
+  if (last < 0) last = pb->desc.L;
+  if (first == lc) {
+    pb->wu_counted = 0.0;
+    Level& c = pb->L(lc);
+    HHG_TRY(coarse_solve<double>(pb, c.rhs, c.x64));
+    HHG_TRY(project_pressure(pb, c, c.x64));
+  }
+  for (int l = std::max(first, lc + 1); l <= last; ++l) {
     Level& lv = pb->L(l);
     HHG_TRY(fmg_interpolate(pb, l));
     for (int kk = 0; kk < prm->kappa; ++kk) {
@@ -1539,19 +1559,20 @@ extern "C" int hhg_set_small_level_mode(hhg_problem* pb, int on) {
   return HHG_OK;
 }
 
-extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats* stats) {
-  HHG_TRY(check_level(pb, pb ? pb->desc.L : 0));
-  HHG_TRY(check_params(prm));
-  for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l)
-    if (!pb->L(l).has_rhs) return fail(HHG_ESTATE, "hhg_set_rhs missing on a level");
-  int64_t kernels = 0;
+namespace {
+// stages first..last of the FMG on pb->stream: recorded once per parameter
+// tuple and part as a CUDA graph and replayed (or launched directly when
+// graphs are off or the stream cannot be captured); adds the kernel count
+int run_stages(hhg_problem* pb, const hhg_params* prm, int part, int first, int last, int64_t* kernels) {
   if (pb->use_graphs && capturable(pb->stream)) {
-    auto key = std::make_tuple(prm->nu_pre, prm->nu_post, prm->nu_inc, prm->kappa, prm->ahat, prm->xi, prm->omega_inv);
+    auto key = std::make_tuple(prm->nu_pre, prm->nu_post, prm->nu_inc, prm->kappa, prm->ahat, prm->xi, prm->omega_inv,
+                               part);
     auto it = pb->graphs.find(key);
     if (it == pb->graphs.end()) {
       const int64_t l0 = g_launches;
+      const double wu0 = first == pb->desc.coarse_level ? 0.0 : pb->wu_counted;   // fmg_core restarts the count
       HHG_CUDA(cudaStreamBeginCapture(pb->stream, cudaStreamCaptureModeThreadLocal));
-      int rc = fmg_core(pb, prm);
+      int rc = fmg_core(pb, prm, first, last);
       cudaGraph_t graph = nullptr;
       cudaError_t ec = cudaStreamEndCapture(pb->stream, &graph);
       if (rc != HHG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
@@ -1560,29 +1581,118 @@ extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out
       cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       if (ei != cudaSuccess) return fail(HHG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
-      it = pb->graphs.emplace(key, hhg_problem::Graph{exec, g_launches - l0, pb->wu_counted}).first;
+      it = pb->graphs.emplace(key, hhg_problem::Graph{exec, g_launches - l0, pb->wu_counted - wu0}).first;
+      pb->wu_counted = wu0;       // the capture counted the stages; the replay below counts them once
     }
     HHG_CUDA(cudaGraphLaunch(it->second.exec, pb->stream));
-    kernels = it->second.kernels;
-    pb->wu_counted = it->second.wu;
+    *kernels += it->second.kernels;
+    pb->wu_counted = (first == pb->desc.coarse_level ? 0.0 : pb->wu_counted) + it->second.wu;
   } else {
     const int64_t l0 = g_launches;
-    HHG_TRY(fmg_core(pb, prm));
-    kernels = g_launches - l0;
+    HHG_TRY(fmg_core(pb, prm, first, last));
+    *kernels += g_launches - l0;
   }
+  return HHG_OK;
+}
+
+int fill_stats(hhg_problem* pb, const hhg_params* prm, int64_t kernels, hhg_stats* stats) {
+  Level& top = pb->L(pb->desc.L);
+  stats->wu_model = model_wu(pb, *prm);
+  stats->wu_counted = pb->wu_counted;
+  HHG_TRY(residual<double>(pb, top, top.x64, top.rhs, top.tmp64));
+  double nr[2];
+  HHG_TRY(norms_of(pb, top, HHG_FP64, top.tmp64, nr));
+  stats->res_u = nr[0];
+  stats->res_p = nr[1];
+  stats->kernel_launches = kernels;
+  if (!std::isfinite(nr[0]) || !std::isfinite(nr[1])) return fail(HHG_EDIVERGED, "FMG produced a non-finite residual");
+  return HHG_OK;
+}
+}  // namespace
+
+extern "C" int hhg_fmg_solve(hhg_problem* pb, const hhg_params* prm, void* x_out, hhg_stats* stats) {
+  HHG_TRY(check_level(pb, pb ? pb->desc.L : 0));
+  HHG_TRY(check_params(prm));
+  for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l)
+    if (!pb->L(l).has_rhs) return fail(HHG_ESTATE, "hhg_set_rhs missing on a level");
+  int64_t kernels = 0;
+  HHG_TRY(run_stages(pb, prm, 0, pb->desc.coarse_level, pb->desc.L, &kernels));
   Level& top = pb->L(pb->desc.L);
   if (x_out) HHG_CUDA(cudaMemcpyAsync(x_out, top.x64, size_t(top.nvec()) * 8, cudaMemcpyDeviceToDevice, pb->stream));
-  if (stats) {
-    stats->wu_model = model_wu(pb, *prm);
-    stats->wu_counted = pb->wu_counted;
-    HHG_TRY(residual<double>(pb, top, top.x64, top.rhs, top.tmp64));
-    double nr[2];
-    HHG_TRY(norms_of(pb, top, HHG_FP64, top.tmp64, nr));
-    stats->res_u = nr[0];
-    stats->res_p = nr[1];
-    stats->kernel_launches = kernels;
-    if (!std::isfinite(nr[0]) || !std::isfinite(nr[1])) return fail(HHG_EDIVERGED, "FMG produced a non-finite residual");
+  if (stats) HHG_TRY(fill_stats(pb, prm, kernels, stats));
+  return HHG_OK;
+}
+
+extern "C" int hhg_fmg_solve_host(hhg_problem* pb, const hhg_params* prm, const double* const* f_nodal,
+                                  const double* const* w_nodal, double* x_host, hhg_stats* stats) {
+  if (!pb) return fail(HHG_EINVAL, "null problem");
+  HHG_TRY(check_params(prm));
+  if (!f_nodal || !w_nodal) return fail(HHG_EINVAL, "null pointer arrays");
+  const int lc = pb->desc.coarse_level, L = pb->desc.L;
+  for (int l = lc; l <= L; ++l) HHG_TRY(check_rhs_args(pb, l, f_nodal[l - lc], w_nodal[l - lc]));
+  if (!pb->aux) {
+    int least = 0, greatest = 0;
+    HHG_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    HHG_CUDA(cudaStreamCreateWithFlags(&pb->aux, cudaStreamNonBlocking));
+    HHG_CUDA(cudaStreamCreateWithPriority(&pb->hp, cudaStreamNonBlocking, greatest));
+    for (cudaEvent_t* e : {&pb->ev_start, &pb->ev_coarse, &pb->ev_fine, &pb->ev_done})
+      HHG_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
+  cudaStream_t main = pb->stream;
+  // the finest level's assembly may run beside the stages below it when its
+  // scratch holds the reduction and the stages replay as graphs
+  const bool overlap = L > lc && pb->use_graphs && capturable(main) &&
+                       pb->L(L).nvec() >= int64_t(pb->max_blocks) + 8;
+  // right-hand sides on the second stream, after the work already queued on
+  // the problem's stream (which may still read the previous ones)
+  HHG_CUDA(cudaEventRecord(pb->ev_start, main));
+  HHG_CUDA(cudaStreamWaitEvent(pb->aux, pb->ev_start, 0));
+  pb->stream = pb->aux;
+  int rc = HHG_OK;
+  for (int l = lc; l < L && rc == HHG_OK; ++l) rc = enqueue_rhs(pb, l, f_nodal[l - lc], w_nodal[l - lc]);
+  if (rc == HHG_OK) rc = cudaEventRecord(pb->ev_coarse, pb->aux) == cudaSuccess ? HHG_OK : fail(HHG_ECUDA, "event record");
+  if (rc == HHG_OK) rc = enqueue_rhs(pb, L, f_nodal[L - lc], w_nodal[L - lc]);
+  if (rc == HHG_OK) rc = cudaEventRecord(pb->ev_fine, pb->aux) == cudaSuccess ? HHG_OK : fail(HHG_ECUDA, "event record");
+  pb->stream = main;
+  if (rc != HHG_OK) {
+    cudaStreamSynchronize(pb->aux);
+    return rc;
+  }
+  // the FMG: the stages below L once the coarse right-hand sides are in,
+  // stage L once the finest one is
+  int64_t kernels = 0;
+  if (overlap) {
+    // the stages on a stream of the highest priority, so that their short
+    // launches go first while the finest level's assembly holds the SMs
+    HHG_CUDA(cudaStreamWaitEvent(pb->hp, pb->ev_start, 0));
+    HHG_CUDA(cudaStreamWaitEvent(pb->hp, pb->ev_coarse, 0));
+    pb->stream = pb->hp;
+    rc = run_stages(pb, prm, 1, lc, L - 1, &kernels);
+    if (rc == HHG_OK) rc = cudaStreamWaitEvent(pb->hp, pb->ev_fine, 0) == cudaSuccess ? HHG_OK : fail(HHG_ECUDA, "wait");
+    if (rc == HHG_OK) rc = run_stages(pb, prm, 2, L, L, &kernels);
+    pb->stream = main;
+    if (rc == HHG_OK) rc = cudaEventRecord(pb->ev_done, pb->hp) == cudaSuccess ? HHG_OK : fail(HHG_ECUDA, "event record");
+    if (rc == HHG_OK) rc = cudaStreamWaitEvent(main, pb->ev_done, 0) == cudaSuccess ? HHG_OK : fail(HHG_ECUDA, "wait");
+  } else {
+    HHG_CUDA(cudaStreamWaitEvent(main, pb->ev_fine, 0));
+    rc = run_stages(pb, prm, 0, lc, L, &kernels);
+  }
+  // the solution in canonical order to the host
+  Level& top = pb->L(L);
+  if (rc == HHG_OK && x_host) {
+    const int64_t nvn = velocity_nodes(top.g), npn = pressure_nodes(top.g);
+    launch_canon_gather<double>(top.g, top.x64, top.bw64, nvn, npn, main);
+    rc = cudaMemcpyAsync(x_host, top.bw64, size_t(3 * nvn + npn) * 8, cudaMemcpyDeviceToHost, main) == cudaSuccess
+             ? HHG_OK : fail(HHG_ECUDA, "solution copy");
+  }
+  if (rc == HHG_OK && stats) rc = fill_stats(pb, prm, kernels, stats);
+  cudaStreamSynchronize(pb->aux);
+  cudaStreamSynchronize(pb->hp);
+  if (rc != HHG_OK) {
+    cudaStreamSynchronize(main);
+    return rc;
+  }
+  HHG_CUDA(cudaStreamSynchronize(main));
   return HHG_OK;
 }
 
@@ -2029,7 +2139,8 @@ struct hhg_batch {
   std::vector<hhg_params> key;            // parameters the graph was recorded with
   int64_t kernels = 0;
   int64_t ops = 0;                        // kernels of the problems' own sequences
-  int grouping = 0;                       // hhg_batch_set_grouping
+  int grouping = -1;                      // hhg_batch_set_grouping (-1: automatic)
+  int used_grouping = -1;                 // the grouping of the current graph
   std::vector<std::unique_ptr<Recorder>> recs;   // per cohort: device tables and work items of the merged launches
   ~hhg_batch() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -2150,17 +2261,18 @@ struct RecordScope {
 // 1: the problems with the same discretisation, precision, coarse level,
 // viscosity model and smoothing tuple, whatever their size (fewer, longer
 // chains; the merge aligns their sequences as far as they agree)
-int capture_merged(hhg_batch* bt, const hhg_params* params, cudaGraph_t* graph) {
+// cohort of every problem under grouping 0 or 1; returns the cohort count
+int cohorts_of(const hhg_batch* bt, const hhg_params* params, int grouping, std::vector<int>& cohort) {
   const int n = int(bt->pbs.size());
   std::vector<std::vector<int>> keys;
-  std::vector<int> cohort(n);
+  cohort.assign(n, 0);
   for (int i = 0; i < n; ++i) {
     hhg_problem* pb = bt->pbs[i];
     const hhg_params& p = params[i];
     const int prec = pb->desc.solve == HHG_SOLVE_FP64 ? HHG_FP64 : HHG_FP32;
     std::vector<int> key = {pb->desc.disc, pb->desc.solve, pb->desc.coarse_level, pb->desc.nu_a != 0.0 ? 1 : 0,
                             p.nu_pre, p.nu_post, p.nu_inc, p.kappa, p.ahat, p.xi};
-    if (bt->grouping == 0) {
+    if (grouping == 0) {
       key.push_back(pb->desc.L);
       for (int l = pb->desc.coarse_level; l <= pb->desc.L; ++l) key.push_back(pb->L(l).rctas[prec]);
     }
@@ -2168,7 +2280,13 @@ int capture_merged(hhg_batch* bt, const hhg_params* params, cudaGraph_t* graph) 
     cohort[i] = int(it - keys.begin());
     if (it == keys.end()) keys.push_back(key);
   }
-  const int nc = int(keys.size());
+  return int(keys.size());
+}
+
+int capture_merged(hhg_batch* bt, const hhg_params* params, int grouping, cudaGraph_t* graph) {
+  const int n = int(bt->pbs.size());
+  std::vector<int> cohort;
+  const int nc = cohorts_of(bt, params, grouping, cohort);
   std::vector<std::unique_ptr<Recorder>> recs(nc);
   std::vector<std::vector<BatchLaunch>> launches(nc);
   int64_t batched = 0;
@@ -2235,10 +2353,18 @@ extern "C" int hhg_batch_fmg_solve(hhg_batch* bt, const hhg_params* params, void
   cudaStream_t s0 = static_cast<cudaStream_t>(stream);
   if (!bt->exec || !same_params(bt->key, params)) {
     if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
-    bool plain = bt->grouping != 2;
+    // automatic grouping: merge the cohorts of identical sequences when they
+    // hold four problems each on average, else one branch per problem
+    int grouping = bt->grouping;
+    if (grouping < 0) {
+      std::vector<int> cohort;
+      grouping = n >= 4 * cohorts_of(bt, params, 0, cohort) ? 0 : 2;
+    }
+    bool plain = grouping != 2;
     for (hhg_problem* pb : bt->pbs) plain = plain && pb->nn_mode == 0 && !pb->nn_recording;
     cudaGraph_t graph = nullptr;
-    const int rc = plain ? capture_merged(bt, params, &graph) : capture_branches(bt, params, &graph);
+    const int rc = plain ? capture_merged(bt, params, grouping, &graph) : capture_branches(bt, params, &graph);
+    bt->used_grouping = plain ? grouping : 2;
     if (rc != HHG_OK) {
       if (graph) cudaGraphDestroy(graph);
       return rc;
@@ -2254,7 +2380,7 @@ extern "C" int hhg_batch_fmg_solve(hhg_batch* bt, const hhg_params* params, void
 }
 
 extern "C" int hhg_batch_set_grouping(hhg_batch* bt, int grouping) {
-  if (!bt || grouping < 0 || grouping > 2) return fail(HHG_EINVAL, "hhg_batch_set_grouping: bad arguments");
+  if (!bt || grouping < -1 || grouping > 2) return fail(HHG_EINVAL, "hhg_batch_set_grouping: bad arguments");
   if (grouping != bt->grouping && bt->exec) {
     cudaGraphExecDestroy(bt->exec);
     bt->exec = nullptr;
@@ -2267,6 +2393,12 @@ extern "C" int hhg_batch_launch_counts(const hhg_batch* bt, int64_t* launches, i
   if (!bt || !launches || !problem_kernels) return fail(HHG_EINVAL, "hhg_batch_launch_counts: null argument");
   *launches = bt->kernels;
   *problem_kernels = bt->ops;
+  return HHG_OK;
+}
+
+extern "C" int hhg_batch_get_grouping(const hhg_batch* bt, int* grouping) {
+  if (!bt || !grouping) return fail(HHG_EINVAL, "hhg_batch_get_grouping: null argument");
+  *grouping = bt->used_grouping;
   return HHG_OK;
 }
 

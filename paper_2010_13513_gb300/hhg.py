@@ -99,6 +99,7 @@ def load():
         "hhg_coarse_solve": [P, I, VP, VP],
         "hhg_vcycle": [P, I, C.POINTER(Params), I, VP, VP],
         "hhg_fmg_solve": [P, C.POINTER(Params), VP, C.POINTER(Stats)],
+        "hhg_fmg_solve_host": [P, C.POINTER(Params), C.POINTER(DP), C.POINTER(DP), DP, C.POINTER(Stats)],
         "hhg_estimate_omega": [P, I, I, DP, DP],
         "hhg_set_graph_mode": [P, I],
         "hhg_set_small_level_mode": [P, I],
@@ -124,6 +125,7 @@ def load():
         "hhg_batch_fmg_solve": [P, C.POINTER(Params), VP, C.POINTER(C.c_int64)],
         "hhg_batch_launch_counts": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
         "hhg_batch_set_grouping": [P, I],
+        "hhg_batch_get_grouping": [P, C.POINTER(C.c_int)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -331,6 +333,31 @@ class Problem:
                "hhg_fmg_solve")
         return st if stats else None
 
+    def fmg_solve_host(self, prm, f_levels, w_levels, out=None, stats=True):
+        """End-to-end solve from host nodal data of every level (coarse level
+        first; CPU float64 tensors or arrays in canonical order, pinned memory
+        for asynchronous copies); the solution in canonical order goes to
+        `out` (a contiguous CPU float64 tensor or array of n_dofs, or None)."""
+        n = self.L - self.lc + 1
+        if len(f_levels) != n or len(w_levels) != n:
+            raise ValueError("one f and one w per level from the coarse level to L")
+        keep = []
+        fp = (C.POINTER(C.c_double) * n)()
+        wp = (C.POINTER(C.c_double) * n)()
+        for i in range(n):
+            nv = 3 * self.layout(self.lc + i).n_velocity_nodes
+            fp[i], kf = _host_ptr(f_levels[i], nv)
+            wp[i], kw = _host_ptr(w_levels[i], nv)
+            keep += [kf, kw]
+        xo = None
+        if out is not None:
+            xo, ko = _host_ptr(out, self.layout(self.L).n_dofs)
+            keep.append(ko)
+        st = Stats()
+        _check(load().hhg_fmg_solve_host(self.h, C.byref(prm), fp, wp, xo, C.byref(st) if stats else None),
+               "hhg_fmg_solve_host")
+        return st if stats else None
+
     def set_graph_mode(self, on):
         _check(load().hhg_set_graph_mode(self.h, int(on)), "hhg_set_graph_mode")
 
@@ -475,9 +502,17 @@ class Batch:
         return k.value
 
     def set_grouping(self, grouping):
-        """0: cohorts of identical kernel sequences (default); 1: cohorts by
-        structure only, whatever the sizes; 2: one graph branch per problem."""
+        """0: cohorts of identical kernel sequences; 1: cohorts by structure
+        only, whatever the sizes; 2: one graph branch per problem; -1
+        (default): 0 when its cohorts hold four problems each on average,
+        else 2."""
         _check(load().hhg_batch_set_grouping(self.h, int(grouping)), "hhg_batch_set_grouping")
+
+    def grouping(self):
+        """The grouping of the current graph (-1 before the first solve)."""
+        g = C.c_int()
+        _check(load().hhg_batch_get_grouping(self.h, C.byref(g)), "hhg_batch_get_grouping")
+        return g.value
 
     def launch_counts(self):
         """(kernels of the batch graph, kernels of the problems' own sequences)."""

@@ -581,3 +581,36 @@ def test_autotune_keeps_results():
     # launch shapes do not change the arithmetic; the resident smoother's CTA
     # count changes the order of the FP32 partial sums of a row
     assert rel(x1.cpu().numpy(), x2.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_fmg_solve_host_matches_separate_calls(graphs):
+    """hhg_fmg_solve_host (right-hand sides of every level from host nodal
+    data, the finest one assembled on a second stream beside the FMG stages
+    below it, the FMG, the solution to the host) gives exactly the result of
+    hhg_set_rhs_levels + hhg_fmg_solve + hhg_vector_to_host, on repeated
+    calls (the second replays the split graphs) and without graphs."""
+    from hhg_inputs import Workload
+    from paper_2010_13513_gb300 import hhg
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pb = lib_problem((1, 1, 1), 4, "P2P1", lc=1, solve="mixed")
+        pb.set_graph_mode(graphs)
+        wl = Workload("paper")
+        f, w = [], []
+        for l in range(1, 5):
+            X = hhg.velocity_coords(pb.layout(l))
+            f.append(torch.from_numpy(np.ascontiguousarray(wl.forcing(X).T.ravel())).pin_memory())
+            w.append(torch.from_numpy(np.ascontiguousarray(wl.dirichlet(X).T.ravel())).pin_memory())
+        prm = hhg.Params.make(1, 3, 1, 1, "f", 3, OMEGA_INV["P2P1"])
+        pb.set_rhs_levels(1, f, w)
+        x = pb.new_vector(4)
+        st_ref = pb.fmg_solve(prm, x)
+        ref = torch.from_numpy(np.array(pb.to_host(4, x)))
+        out = torch.empty(pb.layout(4).n_dofs, dtype=torch.float64).pin_memory()
+        for _ in range(3):
+            out.zero_()
+            st = pb.fmg_solve_host(prm, f, w, out=out)
+            assert torch.equal(out, ref)
+            assert st.res_u == st_ref.res_u and st.res_p == st_ref.res_p
+            assert st.wu_counted == pytest.approx(st_ref.wu_counted, rel=1e-12)
