@@ -206,13 +206,16 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
+TRAFFIC_PROFILE = "profiles/apply_{disc}_l{L}_fp32.md"
+
+
 def measured_traffic(shape):
     """DRAM bytes per launch of the roofline apply from the committed ncu
     summary of that kernel and workload, if it was taken on the current
     kernel sources with the same apply launch shape -- streaming-row threads
     per CTA and sites per thread, slots 3 and 4 of the level's launch shape --
     (else None)."""
-    path = os.path.join(ROOT, "profiles", f"apply_{WORKLOAD['disc'].lower()}_l{WORKLOAD['L']}_fp32.md")
+    path = os.path.join(ROOT, TRAFFIC_PROFILE.format(disc=WORKLOAD["disc"].lower(), L=WORKLOAD["L"]))
     try:
         fields = dict(l.strip("- \n").split(": ", 1) for l in open(path) if l.startswith("- ") and ": " in l)
         if fields.get("kernel_source_sha256") == kernel_source_hash() and \
@@ -929,6 +932,7 @@ def main():
     e2e_v = dofs / statistics.mean(e2e_t)
     nn = learned_coarse(pb, wl, prm, max(3, args.steps // 2), 2, stream) if learned else None
     sh = pb.launch_shape(L)
+    traffic = measured_traffic(sh)
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -947,7 +951,12 @@ def main():
                    "fp64_gpu_ms_per_step": t64 * 1e3, "mixed_speedup_vs_fp64_gpu": t64 / t_step,
                    "mixed_vs_fp64_rel_diff": mixed_vs_fp64, "learned_coarse": nn},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": measured_traffic(sh),
+                     "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                     "traffic_source": (f"carried over from the committed ncu summary "
+                                        f"{TRAFFIC_PROFILE.format(disc=WORKLOAD['disc'].lower(), L=L)} "
+                                        f"(DRAM bytes of one apply; taken on the same kernel sources, "
+                                        f"sha256 {kernel_source_hash()[:12]}..., and the same apply shape "
+                                        f"{[sh[3], sh[4]]})") if traffic is not None else None,
                      "kernel": f"FP32 operator apply y = calA x, level {L} (FULL; launch shape {list(sh)})",
                      "alg_bytes": alg_bytes, "avg_launch_us": t_apply * 1e6, "peak_source": src},
         "e2e": {"value": e2e_v, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
