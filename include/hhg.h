@@ -389,8 +389,8 @@ int hhg_batch_get_grouping(const hhg_batch* batch, int* grouping);
  * the finest level's right-hand side is assembled on a second stream while
  * the FMG stages below it run (when they replay as graphs; the stages then
  * run on an internal stream of the highest priority), so that its host
- * copies and assembly overlap them.  Host buffers in pinned memory let
- * the copies run asynchronously.  Synchronises before returning (the host
+ * copies and assembly overlap them.  Host buffers in pinned memory let the
+ * copies run asynchronously.  Synchronises before returning (the host
  * buffers may then be reused).  *stats optional as for hhg_fmg_solve. */
 int hhg_fmg_solve_host(hhg_problem* pb, const hhg_params* params, const double* const* f_nodal,
                        const double* const* w_nodal, double* x_host, hhg_stats* stats);

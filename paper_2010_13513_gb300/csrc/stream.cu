@@ -6,19 +6,20 @@
 // by the rows of every DoF group at about 27 neighbouring sites, so a kernel
 // that loads every term on its own moves each input value from L2 into the SM
 // many times.  Here a block owns M consecutive positions of the flattened
-// (i, j) plane (M = 4 x threads; a thread owns four consecutive positions,
-// one 16-byte aligned quad, since the j pitch sx is a multiple of four) and a
-// run of consecutive k planes, and marches through the run plane by plane:
+// (i, j) plane (M = V x threads; a thread owns V = 2 or 4 consecutive
+// positions, one aligned vector, since the j pitch sx is a multiple of four)
+// and a run of consecutive k planes, and marches through the run plane by
+// plane:
 //   * planes k-1, k, k+1 of the staged input arrays sit in a ring of four
 //     shared-memory buffers (positions [m0 - sx - 4, m0 + M + sx + 4) of each
 //     plane: the tile plus one lattice row and one quad of halo), and the
 //     fourth buffer is filled with plane k+2 by cp.async while plane k is
 //     evaluated, so every input value crosses from HBM/L2 once per pass;
 //   * a thread loads each line (array, dj, dk) of its stencil footprint once
-//     per plane -- a 16-byte shared load of its quad, and the i-1 / i+4
-//     neighbours from the neighbouring lanes by shuffles -- and applies every
-//     term of every row that reads that line to its four sites from
-//     registers.
+//     per plane -- one vector shared load of its V values and the i-1 / i+V
+//     neighbours the line's terms need (V = 2: a scalar shared load each;
+//     V = 4: from the neighbouring lanes by shuffles) -- and applies every
+//     term of every row that reads that line to its V sites from registers.
 // The plan (which arrays a pass stages, which rows it evaluates, the terms of
 // each line with their row, segment and weight index) is emitted at build
 // time by gen_structure.cpp from the stencil builder: every term is a
@@ -173,8 +174,7 @@ __device__ __forceinline__ void line_terms(const T (&w)[V + 2], Acc<T, NA, V>& a
 __device__ __forceinline__ int64_t buf_of(int kp, int64_t bufsz) { return ((kp + 1) & 3) * bufsz; }
 
 // shared-memory loads with 32-bit shared addresses: the thread's V values
-// (into w[1 .. V]), and one value loaded by one lane only (predicated, no
-// branch)
+// (into w[1 .. V]), and one value
 template <int V>
 __device__ __forceinline__ void lds_vec(uint32_t a, float (&w)[V + 2]) {
   if constexpr (V == 4)
@@ -189,6 +189,8 @@ __device__ __forceinline__ void lds_vec(uint32_t a, double (&w)[V + 2]) {
   for (int h = 0; h < V / 2; ++h)
     asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(w[2 * h + 1]), "=d"(w[2 * h + 2]) : "r"(a + 16 * h));
 }
+__device__ __forceinline__ void lds1(uint32_t a, float& v) { asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a)); }
+// one value loaded by one lane only (predicated, no branch)
 __device__ __forceinline__ void lds_if(bool on, uint32_t a, float& v) {
   asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f32 %0, [%2];\n}"
                : "+f"(v) : "r"(unsigned(on)), "r"(a));
@@ -197,11 +199,13 @@ __device__ __forceinline__ void lds_if(bool on, uint32_t a, double& v) {
   asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f64 %0, [%2];\n}"
                : "+d"(v) : "r"(unsigned(on)), "r"(a));
 }
+__device__ __forceinline__ void lds1(uint32_t a, double& v) { asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a)); }
 
-// one line (slot, dj, dk): the thread's quad and the neighbours the line's
-// terms need, then every term of the line.  pb[dk + 1] is the shared address
-// of the thread's quad in slot 0 of plane k + dk; lwb, sxb: the slot and row
-// strides in bytes.
+// one line (slot, dj, dk): the thread's V values and the neighbours i - 1
+// and i + V that the line's terms need (the staged line holds them for every
+// lane), then every term of the line.  pb[dk + 1] is
+// the shared address of the thread's values in slot 0 of plane k + dk; lwb,
+// sxb: the slot and row strides in bytes.
 template <class SPT, int L, int VARNU, int PSLOT, class T, class Tab, int NA, int V>
 __device__ __forceinline__ void eval_line(const uint32_t (&pb)[3], int lwb, int sxb, int lane, T hs,
                                           Acc<T, NA, V>& acc, const Tab& tab) {
@@ -210,15 +214,25 @@ __device__ __forceinline__ void eval_line(const uint32_t (&pb)[3], int lwb, int 
   const uint32_t a = pb[ln.dk + 1] + uint32_t(ln.slot * lwb + ln.dj * sxb);
   T w[V + 2];
   lds_vec<V>(a, w);
-  if constexpr (ln.lmin < 0) {
-    T v = __shfl_up_sync(0xffffffffu, w[V], 1);
-    lds_if(lane == 0, a - es, v);
-    w[0] = v;
-  }
-  if constexpr (ln.lmax > 0) {
-    T v = __shfl_down_sync(0xffffffffu, w[1], 1);
-    lds_if(lane == 31, a + V * es, v);
-    w[V + 1] = v;
+  if constexpr (V == 2) {
+    // lanes two values apart: a scalar load per neighbour (two-way bank
+    // conflict) issues fewer instructions than a shuffle
+    if constexpr (ln.lmin < 0) lds1(a - es, w[0]);
+    if constexpr (ln.lmax > 0) lds1(a + V * es, w[V + 1]);
+  } else {
+    // lanes four values apart: the neighbours from the neighbouring lanes by
+    // shuffles, and the block's end values by one lane's load (a scalar load
+    // per lane would be a four-way bank conflict)
+    if constexpr (ln.lmin < 0) {
+      T v = __shfl_up_sync(0xffffffffu, w[V], 1);
+      lds_if(lane == 0, a - es, v);
+      w[0] = v;
+    }
+    if constexpr (ln.lmax > 0) {
+      T v = __shfl_down_sync(0xffffffffu, w[1], 1);
+      lds_if(lane == 31, a + V * es, v);
+      w[V + 1] = v;
+    }
   }
   if constexpr (!VARNU && ln.slot == PSLOT) {
 #pragma unroll
