@@ -106,3 +106,21 @@ def test_bind_rejects_small_or_misaligned_workspace(hhg):
     assert lib.hhg_problem_bind(pb, C.c_void_p(257), 1 << 40, None) == -1
     lib.hhg_problem_destroy(pb)
     lib.hhg_mesh_destroy(mesh)
+
+
+def test_batch_and_host_solve_entry_points_reject_bad_arguments(hhg):
+    """The batch and end-to-end entry points validate their arguments on the
+    host before any device work: null handles and out-of-range groupings give
+    HHG_EINVAL and an error text."""
+    lib = hhg.load()
+    EINVAL = -1
+    assert lib.hhg_batch_create(None, 0, None) == EINVAL
+    assert lib.hhg_batch_set_grouping(None, 0) == EINVAL
+    assert lib.hhg_batch_get_grouping(None, None) == EINVAL
+    a, b = C.c_int64(), C.c_int64()
+    assert lib.hhg_batch_launch_counts(None, C.byref(a), C.byref(b)) == EINVAL
+    prm = hhg.Params.make()
+    assert lib.hhg_fmg_solve_host(None, C.byref(prm), None, None, None, None) == EINVAL
+    buf = C.create_string_buffer(256)
+    lib.hhg_last_error(buf, 256)
+    assert buf.value
