@@ -263,6 +263,16 @@ __device__ __forceinline__ T boundary_c(const Geo& g, const T* sm, int64_t bufsz
 }
 
 // --------------------------------------------------------------- outputs
+// where the thread's sites lie, for the output groups of both parities of
+// each index (group offset o = 0: lattice sites 0 .. n; o = 1: 0 .. n - 1,
+// never on a face): the i flags once per tile, the k flags once per plane
+template <int V>
+struct SiteFlags {
+  bool in0[V], in1[V];   // 0 <= i <= nx, 0 <= i <= nx - 1
+  bool ib[V];            // i == 0 or i == nx
+  bool jin0, jin1, jb;   // the same for j
+  bool kin1, kb;         // k <= nz - 1; k == 0 or k == nz (k <= nz always)
+};
 // the rows of part P at the thread's V sites (positions fk .. fk + V - 1 of
 // the k plane: coarse indices (i0 .. i0 + V - 1, j, k)), written to y as one
 // vector.  Positions outside the group's sites (the halo column, the row
@@ -272,13 +282,14 @@ __device__ __forceinline__ T boundary_c(const Geo& g, const T* sm, int64_t bufsz
 template <class SPT, int Q, int P, int VARNU, int PSLOT, class T, int MODE, class Tab, int NA, int V>
 __device__ __forceinline__ void store_part(const Geo& g, const T* __restrict__ b, T* __restrict__ y, const T* sm,
                                            int64_t bufsz, int lw, int lf, int k, int i0, int j, int64_t fk, T es, T eis,
-                                           const Acc<T, NA, V>& acc, const Tab& tab) {
+                                           const Acc<T, NA, V>& acc, const Tab& tab, const SiteFlags<V>& sf) {
   constexpr gen::PartT pt = SPT::parts[SPT::passes[Q].p0 + P];
   constexpr bool HAS_C = part_has_c<SPT, Q, P>();
   using PP = Par<pt.og>;
-  if (j < 0 || j > g.ny - PP::oy || k > g.nz - PP::oz) return;
-  const bool bjk = 2 * j + PP::oy == 0 || 2 * j + PP::oy == 2 * g.ny || 2 * k + PP::oz == 0 ||
-                   2 * k + PP::oz == 2 * g.nz;
+  // the row's DoF at doubled position 2 (i, j, k) + (ox, oy, oz): an odd
+  // component never lies on a face
+  if (!(PP::oy ? sf.jin1 : sf.jin0) || (PP::oz && !sf.kin1)) return;
+  const bool bjk = (PP::oy ? false : sf.jb) || (PP::oz ? false : sf.kb);
   T a0[V], a1[V], a2[V], v[V];
   acc.get(3 * P, a0);
   if (VARNU) acc.get(3 * P + 1, a1);
@@ -294,8 +305,8 @@ __device__ __forceinline__ void store_part(const Geo& g, const T* __restrict__ b
     if (HAS_C) v[s] += VARNU ? eis * a2[s] : a2[s];
     if (!VARNU) v[s] *= hs;
     const int i = i0 + s;
-    const bool bnd = bjk || 2 * i + PP::ox == 0 || 2 * i + PP::ox == 2 * g.nx;
-    keep[s] = i >= 0 && i <= g.nx - PP::ox && (pt.all || !bnd);
+    const bool bnd = bjk || (PP::ox ? false : sf.ib[s]);
+    keep[s] = (PP::ox ? sf.in1[s] : sf.in0[s]) && (pt.all || !bnd);
     if constexpr (HAS_C) {
       if (keep[s] && bnd) {                            // boundary pressure row: clipped C stencil
         static_assert(PSLOT >= 0, "the pressure array is staged with the C terms");
@@ -329,9 +340,9 @@ __device__ __forceinline__ void store_part(const Geo& g, const T* __restrict__ b
 template <class SPT, int Q, int VARNU, int PSLOT, class T, int MODE, class Tab, int NA, int V, int... I>
 __device__ __forceinline__ void store_parts(const Geo& g, const T* __restrict__ b, T* __restrict__ y, const T* sm,
                                             int64_t bufsz, int lw, int lf, int k, int i0, int j, int64_t fk, T es,
-                                            T eis, const Acc<T, NA, V>& acc, const Tab& tab,
+                                            T eis, const Acc<T, NA, V>& acc, const Tab& tab, const SiteFlags<V>& sf,
                                             std::integer_sequence<int, I...>) {
-  (store_part<SPT, Q, I, VARNU, PSLOT, T, MODE>(g, b, y, sm, bufsz, lw, lf, k, i0, j, fk, es, eis, acc, tab), ...);
+  (store_part<SPT, Q, I, VARNU, PSLOT, T, MODE>(g, b, y, sm, bufsz, lw, lf, k, i0, j, fk, es, eis, acc, tab, sf), ...);
 }
 
 // cp.async of plane kp of the pass's arrays (array slot A at buf + A lw);
@@ -404,6 +415,17 @@ __device__ __forceinline__ void stream_body(const unsigned bx, const unsigned gx
     const int64_t f = m0 + V * tid;                    // the thread's first site
     const int j = int(f / sx) - 1;
     const int i0 = int(f - int64_t(j + 1) * sx) - 1;
+    SiteFlags<V> sf;
+#pragma unroll
+    for (int s = 0; s < V; ++s) {
+      const int i = i0 + s;
+      sf.in0[s] = i >= 0 && i <= g.nx;
+      sf.in1[s] = i >= 0 && i <= g.nx - 1;
+      sf.ib[s] = i == 0 || i == g.nx;
+    }
+    sf.jin0 = j >= 0 && j <= g.ny;
+    sf.jin1 = j >= 0 && j <= g.ny - 1;
+    sf.jb = j == 0 || j == g.ny;
     auto load = [&](int kp) {
       stage_plane<SPT, Q>(x, sm + buf_of(kp, bufsz), int64_t(kp + 1) * g.sy + gbase, g.arr, vlen, lw, nch, tid, nt,
                           std::make_integer_sequence<int, ps.na>{});
@@ -433,8 +455,10 @@ __device__ __forceinline__ void stream_body(const unsigned bx, const unsigned gx
         es = T(g.esc[k]);
         eis = T(g.eisc[k]);
       }
+      sf.kin1 = k <= g.nz - 1;
+      sf.kb = k == 0 || k == g.nz;
       store_parts<SPT, Q, VARNU, PSLOT, T, MODE>(g, b, y, sm, bufsz, lw, lf, k, i0, j, int64_t(k + 1) * g.sy + f, es,
-                                                 eis, acc, tab, std::make_integer_sequence<int, ps.np>{});
+                                                 eis, acc, tab, sf, std::make_integer_sequence<int, ps.np>{});
       __syncthreads();                                 // plane k-1's buffer is refilled next
     }
     cp_wait0();
