@@ -917,6 +917,18 @@ def main():
         dist.destroy_process_group()
         return
 
+    # the same mixed solve with the FP64 refinement residual instead of the
+    # double-float one (the default): its time and the solutions' difference
+    refine = {"kind": pb.refinement_residual_kind()}
+    if refine["kind"] == "df32":
+        xf = pb.new_vector(L)
+        pb.set_refinement_residual("fp64")
+        tf = statistics.mean(time_steps(pb, prm, xf, max(3, args.steps // 2), 2, stream)) * 1e-3
+        pb.set_refinement_residual("df32")
+        refine.update({"fp64_refinement_ms_per_step": tf * 1e3, "df32_speedup": tf / t_step,
+                       "rel_diff_vs_fp64_refinement": float(torch.linalg.norm(x - xf) / torch.linalg.norm(xf))})
+        del xf
+
     # FP64-only GPU solve of the same workload (same tuple, same omega)
     pb64, _ = make_problem("fp64")
     pb64.autotune(reps=3)
@@ -949,7 +961,8 @@ def main():
                    "wu_model_under_target": bool(st.wu_model < 10.0),
                    "launch_shapes": {str(k): v for k, v in shapes.items()},
                    "fp64_gpu_ms_per_step": t64 * 1e3, "mixed_speedup_vs_fp64_gpu": t64 / t_step,
-                   "mixed_vs_fp64_rel_diff": mixed_vs_fp64, "learned_coarse": nn},
+                   "mixed_vs_fp64_rel_diff": mixed_vs_fp64, "refinement_residual": refine,
+                   "learned_coarse": nn},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
                      "traffic_source": (f"carried over from the committed ncu summary "

@@ -79,6 +79,10 @@ extern "C" {
 #define HHG_SOLVE_FP64  0   /* every level in double */
 #define HHG_SOLVE_MIXED 1   /* FP32 V-cycles inside FP64 iterative refinement */
 
+/* arithmetic of the mixed solve's refinement residual */
+#define HHG_REFINE_FP64 0   /* FP64 rows, rounded to FP32 for the V-cycle          */
+#define HHG_REFINE_DF32 1   /* double-float rows (two FP32 numbers per value)      */
+
 /* operators for hhg_apply */
 #define HHG_OP_FULL     0   /* y = calA x                                     */
 #define HHG_OP_A        1   /* velocity rows: A u_c; pressure rows 0          */
@@ -205,6 +209,28 @@ int hhg_apply(hhg_problem* pb, int level, int op, int prec, const void* x, void*
 /* r = b - calA x; if norms != NULL, norms[0] = ||r_u||_2, norms[1] = ||r_p||_2
  * (synchronises). */
 int hhg_residual(hhg_problem* pb, int level, int prec, const void* x, const void* b, void* r, double* norms);
+/* The defect of one refinement step of the mixed solve (HHG_SOLVE_MIXED, a
+ * GPU execution choice outside the paper: FP32 V-cycles of Algorithm 1 on the
+ * defect of the FP64 iterate), as
+ * hhg_fmg_solve computes it: r = fl32(b - calA x) for the full operator of
+ * `level`, x and b FP64 device vectors (x in lifting form, 16-byte aligned),
+ * r an FP32 device vector.  With HHG_REFINE_DF32 (the default where it
+ * applies) every row is a compensated dot product in double-float arithmetic
+ * (Ogita, Rump and Oishi's Dot2 on x and the weights split into two FP32
+ * numbers each): |r - fl32(b - calA x)| <= 2^-24 |b - calA x| + about
+ * (n^2 2^-48 + 2^-46) sum_j |a_ij x_j| for a row of n terms.  With
+ * HHG_REFINE_FP64 the rows are FP64 and rounded to FP32.  Overwrites the
+ * level's internal FP32 iterate and FP64 scratch vector (x, b and r must not
+ * be those).  HHG_EINVAL unless the problem was created with
+ * HHG_SOLVE_MIXED. */
+int hhg_refinement_residual(hhg_problem* pb, int level, const double* x, const double* b, float* r);
+/* Arithmetic of the refinement residual (HHG_REFINE_FP64 or HHG_REFINE_DF32;
+ * default HHG_REFINE_DF32).  HHG_REFINE_DF32 covers the operators with
+ * constant viscosity (HHG_EINVAL otherwise; variable-viscosity problems use
+ * FP64).  Drops cached graphs when the choice changes.  The get call reports
+ * the arithmetic in effect. */
+int hhg_set_refinement_residual(hhg_problem* pb, int kind);
+int hhg_get_refinement_residual(hhg_problem* pb, int* kind);
 /* `sweeps` inexact Uzawa iterations (Eq. uzawa-iteration) on x in place. */
 int hhg_smooth(hhg_problem* pb, int level, const hhg_params* prm, int sweeps, int prec, void* x, const void* b);
 /* r_coarse = I_l^{l-1} r_fine = (I_{l-1}^l)^T r_fine (Sec. 3.3), Dirichlet rows 0. */

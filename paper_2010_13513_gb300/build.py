@@ -32,7 +32,7 @@ SOURCES = [("kernels.cu", "kernels", []), ("fast.cu", "fast64", ["-DHHG_FAST_ONL
            ("stream.cu", "stream32v2b", ["-DHHG_STREAM_ONLY=32", "-DHHG_STREAM_V=2", "-DHHG_STREAM_BATCHED"]),
            ("small.cu", "small", []),
            ("nn.cu", "nn", []), ("noalloc.cu", "noalloc", []), ("stencils.cpp", "stencils", []),
-           ("batch.cpp", "batch", []), ("problem.cpp", "problem", [])]
+           ("dfres.cu", "dfres", []), ("batch.cpp", "batch", []), ("problem.cpp", "problem", [])]
 
 
 def _nvcc():

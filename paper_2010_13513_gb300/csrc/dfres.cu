@@ -1,0 +1,316 @@
+// Refinement residual of the mixed-precision solve in double-float arithmetic.
+//
+// The mixed solve (FP32 V-cycles inside an FP64 iterative refinement) needs
+// the outer residual r = b - calA x of every FMG stage to well below FP32
+// rounding.  FP64 arithmetic gives that, but on this GPU the FP64 pipe runs
+// at about 1/64 of the FP32 rate, so the FP64 residual of the finest level is
+// bound by it (it was the largest single kernel of the level-7 solve).  Here
+// every FP64 value v is carried as two FP32 numbers v = v_hi + v_lo (47
+// significant bits, split by integer bit operations, no FP64 instruction on
+// the common path), and each row is evaluated as the compensated dot product
+// "Dot2" of Ogita, Rump and Oishi (Accurate sum and dot product, SIAM J. Sci.
+// Comput. 26(6), 2005): the product w_hi x_hi is split exactly into p + e by
+// one FMA, p enters the running sum through Knuth's error-free TwoSum (The Art
+// of Computer Programming, vol. 2, Sec. 4.2.2), and the sum's rounding errors,
+// e and the small products w_lo x_hi + w_hi x_lo are collected in a second
+// FP32 accumulator.  With u = 2^-24 and n terms the computed row differs from
+// the exact one by at most about u |r| + (n^2 u^2 + 2^-46) sum_j |a_ij x_j|: as
+// if evaluated in 47-bit arithmetic and then rounded to FP32, the precision
+// the V-cycle takes its right-hand side in.
+//
+// Work layout (as the vector row kernels of the FP32/FP64 path): grid x over
+// the padded (i, j) plane in warps of 4 x 32 positions, y over groups of kp
+// planes, z over the rows of the operator; a thread evaluates 4 sites 32
+// positions apart.  The terms of a row are a loop over weights and offsets in
+// the constant bank, so a row's code stays small in the instruction cache.
+// Boundary pressure rows (P1-P1: the C terms of the cubes inside the box) add
+// their per-cube C terms in FP64; they are a few per cent of the pressure
+// rows.
+#include "dfres.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <type_traits>
+
+#include "batch.h"
+#include "kernels.h"
+#include "structure.inc"
+
+namespace hhg {
+namespace {
+
+template <int N>
+struct DfTab {
+  float wh[N];       // weights: w = wh + wl (|w - wh - wl| <= 2^-48 |w|)
+  float wl[N];
+  int off[N];        // linear offsets arr * array_stride + di + dj sx + dk sy
+};
+
+template <int DISC>
+using DfTabOf = DfTab<gen::S<DISC, 0, OP_FULL>::N>;
+
+// v = hi + lo with |v - hi - lo| < 2^-46 |v|: hi takes the leading 24 bits of
+// v's significand, lo the next 23 (both truncated).  For v = 0, |v| < 2^-100
+// or |v| >= 2^126, hi = fl32(v) and lo = 0 (an FP64 conversion off the common
+// path).
+__device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned top = unsigned(u >> 32);
+  const unsigned sgn = top & 0x80000000u;
+  const int e = int((top >> 20) & 0x7ffu);           // biased FP64 exponent
+  if (e >= 923 && e <= 1148) {
+    // FP32 exponent field e - 1023 + 127; significand bits 51..29
+    hi = __uint_as_float(sgn | (unsigned(e - 896) << 23) | unsigned((u >> 29) & 0x7fffffu));
+    // bits 28..6 of the significand scaled by 2^(e - 1069): (1 + f) 2^E - 2^E
+    // with E = e - 1046, an exact FP32 subtraction
+    const unsigned eb = unsigned(e - 919) << 23;
+    lo = __fsub_rn(__uint_as_float(sgn | eb | (unsigned(u & 0x1fffffffu) >> 6)), __uint_as_float(sgn | eb));
+  } else if (e == 0) {
+    hi = __uint_as_float(sgn);                       // +-0 (and FP64 subnormals, < 2^-1022)
+    lo = 0.0f;
+  } else {
+    hi = __double2float_rn(v);
+    lo = 0.0f;
+  }
+}
+
+// one Dot2 step: (s, c) += (wh + wl) (xh + xl); the rounded operations are
+// the _rn intrinsics, which the compiler never contracts into FMAs
+__device__ __forceinline__ void dot2_term(float wh, float wl, float xh, float xl, float& s, float& c) {
+  const float p = __fmul_rn(wh, xh);
+  float e = __fmaf_rn(wh, xh, -p);                   // wh xh = p + e exactly
+  e = __fmaf_rn(wl, xh, e);
+  e = __fmaf_rn(wh, xl, e);
+  const float t = __fadd_rn(s, p);                   // TwoSum: s + p = t + d exactly
+  const float z = __fsub_rn(t, s);
+  const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(d, e));
+}
+
+// terms [T0, T0 + N) of a row at NS sites 32 positions apart (idx + 32 v)
+template <int T0, int N, int NS, class Tab>
+__device__ __forceinline__ void dot2_seg(const Tab& tab, const float* __restrict__ xh, const float* __restrict__ xl,
+                                         int64_t idx, float (&s)[NS], float (&c)[NS]) {
+#pragma unroll 2
+  for (int t = T0; t < T0 + N; ++t) {
+    const float wh = tab.wh[t], wl = tab.wl[t];
+    const int64_t q = idx + tab.off[t];
+#pragma unroll
+    for (int v = 0; v < NS; ++v) dot2_term(wh, wl, __ldg(xh + q + 32 * v), __ldg(xl + q + 32 * v), s[v], c[v]);
+  }
+}
+
+// per-cube C terms of boundary pressure row r at site (i, j, k) (index idx),
+// the cubes inside the box only, in FP64 with x = xh + xl
+__device__ double boundary_c64(const Geo& g, const OpDev& op, int r, int i, int j, int k, const float* xh,
+                               const float* xl, int64_t idx) {
+  const DRow row = op.rows[r];
+  double a = 0.0;
+  for (int t = row.b0 + row.m0 + row.m1; t < row.b0 + row.m0 + row.m1 + row.m2; ++t) {
+    const DTermB tm = op.bterms[t];
+    const int qx = i + tm.cx, qy = j + tm.cy, qz = k + tm.cz;
+    if (qx < 0 || qy < 0 || qz < 0 || qx >= g.nx || qy >= g.ny || qz >= g.nz) continue;
+    const int64_t q = int64_t(tm.arr) * g.arr + idx + tm.off;
+    a += __ldg(op.bw64 + t) * (double(__ldg(xh + q)) + double(__ldg(xl + q)));
+  }
+  return a;
+}
+
+// the residual of row R at one site from its sums: (s, c) over segments 0
+// and 1, (s2, c2) over segment 2 (C); bnd: the site lies on the box boundary
+template <int OUT, int ALL, int N2>
+__device__ __forceinline__ void df_store(const Geo& g, const OpDev& op, int R, int i, int j, int k, bool bnd,
+                                         const float* xh, const float* xl, int64_t idx, float s, float c, float s2,
+                                         float c2, const double* __restrict__ b, float* __restrict__ r) {
+  const int64_t iy = int64_t(OUT) * g.arr + idx;
+  if (bnd && !ALL) {                                 // Dirichlet velocity row
+    r[iy] = 0.0f;
+    return;
+  }
+  const double bv = __ldg(b + iy);
+  if (N2 > 0 && bnd) {
+    // boundary pressure row: the clipped C terms in FP64
+    const double cb = boundary_c64(g, op, R, i, j, k, xh, xl, idx);
+    r[iy] = __double2float_rn(bv - (double(s) + double(c)) - cb);
+    return;
+  }
+  if (N2 > 0) {                                      // (s, c) += (s2, c2)
+    const float t = __fadd_rn(s, s2);
+    const float z = __fsub_rn(t, s);
+    const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(c2, d));
+  }
+  float bh, bl;
+  split_df(bv, bh, bl);
+  // (bh + bl) - (s + c): TwoSum of bh and -s, then the small parts
+  const float t = __fsub_rn(bh, s);
+  const float z = __fsub_rn(t, bh);
+  const float d = __fadd_rn(__fsub_rn(bh, __fsub_rn(t, z)), __fsub_rn(-s, z));
+  r[iy] = __fadd_rn(t, __fsub_rn(__fadd_rn(d, bl), c));
+}
+
+// row R = (OUT, OG, ALL, T0, N0, N1, N2) on the sites of the block: the
+// indexing of the vector row kernels (four runs of 32 positions per warp; a
+// warp whose last run passes the group's last site takes its sites one by one)
+template <int OUT, int OG, int ALL, int T0, int N0, int N1, int N2, class Tab>
+__device__ __forceinline__ void df_rows(const Geo& g, int R, const float* __restrict__ xh,
+                                        const float* __restrict__ xl, const double* __restrict__ b,
+                                        float* __restrict__ r, const OpDev& op, const Tab& tab, int kp) {
+  constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
+  constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
+  constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
+  constexpr int V = 4;
+  const int m0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * V);
+  const int lane = int(threadIdx.x & 31);
+  const int mlast = (g.ny - oy) * g.sx + (g.nx - ox);
+  if (m0 > mlast) return;
+  const int k0 = blockIdx.y * kp, k1 = min(k0 + kp, g.nz - oz + 1);
+  if (m0 + 32 * V - 1 > mlast) {                     // warp-uniform: the plane's last warp
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k)
+#pragma unroll 1
+      for (int v = 0; v < V; ++v) {
+        const int m = m0 + lane + 32 * v;
+        const int j = m / g.sx, i = m - j * g.sx;
+        if (m > mlast || i > g.nx - ox) continue;
+        const bool bnd = 2 * i + ox == 0 || 2 * i + ox == 2 * g.nx || 2 * j + oy == 0 || 2 * j + oy == 2 * g.ny ||
+                         2 * k + oz == 0 || 2 * k + oz == 2 * g.nz;
+        const int64_t idx = int64_t(m) + 1 + g.sx + int64_t(k + 1) * g.sy;
+        float s[1] = {0.0f}, c[1] = {0.0f}, s2[1] = {0.0f}, c2[1] = {0.0f};
+        if (!bnd || ALL) {
+          dot2_seg<T0, N0 + N1, 1>(tab, xh, xl, idx, s, c);
+          if (N2 > 0 && !bnd) dot2_seg<T0 + N0 + N1, N2, 1>(tab, xh, xl, idx, s2, c2);
+        }
+        df_store<OUT, ALL, N2>(g, op, R, i, j, k, bnd, xh, xl, idx, s[0], c[0], s2[0], c2[0], b, r);
+      }
+    return;
+  }
+  int iv[V], jv[V];
+  bool okv[V], bijv[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int m = m0 + lane + 32 * v;
+    jv[v] = m / g.sx;
+    iv[v] = m - jv[v] * g.sx;
+    okv[v] = iv[v] <= g.nx - ox;
+    bijv[v] = 2 * iv[v] + ox == 0 || 2 * iv[v] + ox == 2 * g.nx || 2 * jv[v] + oy == 0 || 2 * jv[v] + oy == 2 * g.ny;
+  }
+#pragma unroll 1
+  for (int k = k0; k < k1; ++k) {
+    const int64_t idx = int64_t(m0 + lane) + 1 + g.sx + int64_t(k + 1) * g.sy;
+    float s[V], c[V], s2[V], c2[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) s[v] = c[v] = s2[v] = c2[v] = 0.0f;
+    dot2_seg<T0, N0 + N1, V>(tab, xh, xl, idx, s, c);
+    if (N2 > 0) dot2_seg<T0 + N0 + N1, N2, V>(tab, xh, xl, idx, s2, c2);
+    const bool bk = 2 * k + oz == 0 || 2 * k + oz == 2 * g.nz;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+      if (okv[v])
+        df_store<OUT, ALL, N2>(g, op, R, iv[v], jv[v], k, bijv[v] || bk, xh, xl, idx + 32 * v, s[v], c[v], s2[v],
+                               c2[v], b, r);
+  }
+}
+
+template <class S, int R, class F>
+__device__ __forceinline__ void by_row(int r, F&& f) {
+  if constexpr (R < S::R) {
+    if (r == R) f(std::integral_constant<int, R>{});
+    else by_row<S, R + 1>(r, f);
+  }
+}
+
+template <int DISC>
+__global__ void __launch_bounds__(128) k_res_df(Geo g, const float* __restrict__ xh, const float* __restrict__ xl,
+                                                const double* __restrict__ b, float* __restrict__ r, OpDev op, int kp,
+                                                const __grid_constant__ DfTabOf<DISC> tab) {
+  using S = gen::S<DISC, 0, OP_FULL>;
+  by_row<S, 0>(int(blockIdx.z), [&](auto rc) {
+    constexpr int R = decltype(rc)::value;
+    constexpr gen::RowS rw = S::rows[R];
+    df_rows<rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, xh, xl, b, r, op, tab, kp);
+  });
+}
+
+// hi[q] + lo[q] = x[q] (split_df), two elements per thread and step (n even)
+__global__ void k_split_df(const double2* __restrict__ x, float2* __restrict__ hi, float2* __restrict__ lo,
+                           int64_t n2) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n2; q += int64_t(gridDim.x) * blockDim.x) {
+    const double2 v = x[q];
+    float2 h, l;
+    split_df(v.x, h.x, l.x);
+    split_df(v.y, h.y, l.y);
+    hi[q] = h;
+    lo[q] = l;
+  }
+}
+
+constexpr int kDfThreads = 128;
+constexpr int kDfPlanes = 2;
+
+template <int DISC>
+void launch_df(const Geo& g, const OpDev& od, const char* tab, const double* x, const double* b, float* xh, float* xl,
+               float* r, cudaStream_t s) {
+  using S = gen::S<DISC, 0, OP_FULL>;
+  DfTabOf<DISC> tb;
+  std::memcpy(&tb, tab, sizeof(tb));
+  const int64_t n = (3 * int64_t(g.G) + 1) * g.arr;  // a multiple of 64
+  const int64_t n2 = n / 2;
+  ++g_launches;
+  k_split_df<<<unsigned(std::min<int64_t>((n2 + 255) / 256, 152 * 8)), 256, 0, s>>>(
+      reinterpret_cast<const double2*>(x), reinterpret_cast<float2*>(xh), reinterpret_cast<float2*>(xl), n2);
+  // warps of 4 x 32 positions over the padded plane up to the last site
+  const int64_t warps = ((int64_t(g.ny) * g.sx + g.nx + 1) + 127) / 128;
+  const dim3 grd(unsigned((warps * 32 + kDfThreads - 1) / kDfThreads), unsigned((g.nz + 1 + kDfPlanes - 1) / kDfPlanes),
+                 unsigned(S::R));
+  ++g_launches;
+  k_res_df<DISC><<<grd, kDfThreads, 0, s>>>(g, xh, xl, b, r, od, kDfPlanes, tb);
+}
+
+void df_launch(int disc, const Geo& g, const OpDev& od, const char* tab, const double* x, const double* b, float* xh,
+               float* xl, float* r, cudaStream_t s) {
+  if (disc == 1) launch_df<1>(g, od, tab, x, b, xh, xl, r, s);
+  else launch_df<2>(g, od, tab, x, b, xh, xl, r, s);
+}
+
+}  // namespace
+
+bool df_supported(int disc, int varnu) { return varnu == 0 && (disc == 1 || disc == 2); }
+
+bool df_table(int disc, int varnu, const std::vector<char>& ftab64, std::vector<char>& out) {
+  out.clear();
+  if (!df_supported(disc, varnu)) return false;
+  const int N = disc == 1 ? gen::S<1, 0, OP_FULL>::N : gen::S<2, 0, OP_FULL>::N;
+  const size_t bytes = disc == 1 ? sizeof(DfTabOf<1>) : sizeof(DfTabOf<2>);
+  if (ftab64.size() < size_t(N) * 12) return false;
+  // the FP64 table image: N weights, then N offsets
+  const double* w = reinterpret_cast<const double*>(ftab64.data());
+  const int* off = reinterpret_cast<const int*>(ftab64.data() + size_t(N) * 8);
+  out.assign(bytes, 0);
+  float* wh = reinterpret_cast<float*>(out.data());
+  float* wl = wh + N;
+  int* o = reinterpret_cast<int*>(out.data() + size_t(2 * N) * 4);
+  for (int t = 0; t < N; ++t) {
+    wh[t] = float(w[t]);
+    wl[t] = float(w[t] - double(wh[t]));
+    o[t] = off[t];
+  }
+  return true;
+}
+
+void df_residual(int disc, const Geo& g, const OpDev& od, const std::vector<char>& dftab, const double* x,
+                 const double* b, float* xh, float* xl, float* r, cudaStream_t s) {
+  const char* tab = dftab.data();
+  if (g_rec) {
+    g_rec->native([=](cudaStream_t s_) { df_launch(disc, g, od, tab, x, b, xh, xl, r, s_); });
+    return;
+  }
+  df_launch(disc, g, od, tab, x, b, xh, xl, r, s);
+}
+
+}  // namespace hhg

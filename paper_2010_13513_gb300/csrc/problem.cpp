@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "batch.h"
+#include "dfres.h"
 #include "fast.h"
 #include "internal.h"
 #include "kernels.h"
@@ -132,6 +133,9 @@ struct Level {
   // parameter blocks of the specialised kernels (FastTab<T, N> images)
   std::vector<char> ftab64[OP_COUNT], ftab32[OP_COUNT];
   bool has_fast[OP_COUNT] = {};
+  // parameter block of the double-float refinement residual (dfres.cu);
+  // empty if the operator is not covered
+  std::vector<char> dftab;
   // parameter blocks of the streaming kernels (FULL, B^T, (B, -C))
   std::vector<char> stab64[OP_COUNT], stab32[OP_COUNT];
   bool has_stream[OP_COUNT] = {};
@@ -178,6 +182,7 @@ struct hhg_problem {
   // CUDA graphs of whole FMG solves, keyed by the parameter tuple
   bool use_graphs = true;
   bool use_cluster = true;       // cluster-resident smoother on small levels
+  int refine = HHG_REFINE_DF32;  // arithmetic of the mixed solve's refinement residual
   // learned coarse correction
   int nn_n = 0, nn_h = 0, nn_S = 0, nn_B = 0, nn_mode = 0;
   int64_t nn_P = 0;
@@ -345,6 +350,7 @@ extern "C" int hhg_problem_create(const hhg_mesh* mesh, const hhg_problem_desc* 
         };
         if (!image(0.0, lv.ftab64[o]) || !image(0.0f, lv.ftab32[o])) return fail(HHG_EINVAL, "level too large for 32-bit offsets");
         lv.has_fast[o] = true;
+        if (o == OP_FULL) df_table(desc->disc, varnu, lv.ftab64[o], lv.dftab);
       }
       if (N >= 0 && (o == OP_FULL || o == OP_BT || o == OP_BC)) {
         // streaming kernels: the weights, and the boundary C stencil of the
@@ -844,6 +850,24 @@ template <class T>
 int residual(hhg_problem* pb, Level& lv, const T* x, const T* b, T* r) {
   HHG_TRY(apply_op<T>(pb, lv, OP_FULL, MODE_RES, x, b, r));
   pb->wu_counted += level_weight(pb, lv);
+  return HHG_OK;
+}
+
+// the defect of the mixed solve's refinement step, r32 = fl32(b - calA x):
+// the double-float kernels where they cover the operator (x32 and tmp64
+// serve as scratch for the two FP32 parts of x), else the FP64 residual in
+// tmp64 rounded to FP32
+int refinement_residual(hhg_problem* pb, Level& lv, const double* x, const double* b, float* r32) {
+  if (pb->refine == HHG_REFINE_DF32 && !lv.dftab.empty()) {
+    df_residual(pb->desc.disc, lv.g, lv.op[OP_FULL], lv.dftab, x, b, lv.x32, reinterpret_cast<float*>(lv.tmp64), r32,
+                pb->stream);
+    HHG_CHECK_LAUNCH();
+    pb->wu_counted += level_weight(pb, lv);
+    return HHG_OK;
+  }
+  HHG_TRY(residual<double>(pb, lv, x, b, lv.tmp64));
+  launch_cast_d2f(lv.tmp64, r32, lv.nvec(), pb->stream);
+  HHG_CHECK_LAUNCH();
   return HHG_OK;
 }
 
@@ -1376,6 +1400,15 @@ extern "C" int hhg_residual(hhg_problem* pb, int level, int prec, const void* x,
   return HHG_OK;
 }
 
+extern "C" int hhg_refinement_residual(hhg_problem* pb, int level, const double* x, const double* b, float* r) {
+  HHG_TRY(check_level(pb, level));
+  if (pb->desc.solve != HHG_SOLVE_MIXED) return fail(HHG_EINVAL, "the refinement residual needs a mixed-precision problem");
+  if (!x || !b || !r) return fail(HHG_EINVAL, "null vector");
+  if (reinterpret_cast<uintptr_t>(x) & 15) return fail(HHG_EINVAL, "x must be 16-byte aligned");
+  Level& lv = pb->L(level);
+  return refinement_residual(pb, lv, x, b, r);
+}
+
 extern "C" int hhg_smooth(hhg_problem* pb, int level, const hhg_params* prm, int sweeps, int prec, void* x, const void* b) {
   HHG_TRY(check_level(pb, level));
   HHG_TRY(check_params(prm));
@@ -1453,9 +1486,9 @@ int fmg_core(hhg_problem* pb, const hhg_params* prm, int first = -1, int last = 
       if (pb->desc.solve == HHG_SOLVE_FP64) {
         HHG_TRY(vcycle<double>(pb, l, l, *prm, lv.x64, lv.rhs));
       } else {
-        // iterative refinement: FP64 residual, FP32 V-cycle on the defect, FP64 update
-        HHG_TRY(residual<double>(pb, lv, lv.x64, lv.rhs, lv.tmp64));
-        launch_cast_d2f(lv.tmp64, lv.b32, lv.nvec(), pb->stream);
+        // iterative refinement: residual of the FP64 iterate (FP64, or
+        // double-float into FP32), FP32 V-cycle on the defect, FP64 update
+        HHG_TRY(refinement_residual(pb, lv, lv.x64, lv.rhs, lv.b32));
         HHG_CUDA(launch_zero(lv.x32, size_t(lv.nvec()) * 4, pb->stream));
         HHG_TRY(vcycle<float>(pb, l, l, *prm, lv.x32, lv.b32));
         launch_add_f2d(lv.x32, lv.x64, lv.nvec(), pb->stream);
@@ -1471,6 +1504,28 @@ bool capturable(cudaStream_t s) {
   return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
 }
 }  // namespace
+
+extern "C" int hhg_set_refinement_residual(hhg_problem* pb, int kind) {
+  if (!pb) return fail(HHG_EINVAL, "null problem");
+  if (kind != HHG_REFINE_FP64 && kind != HHG_REFINE_DF32)
+    return fail(HHG_EINVAL, "kind must be HHG_REFINE_FP64 or HHG_REFINE_DF32");
+  if (kind == HHG_REFINE_DF32 && !df_supported(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0))
+    return fail(HHG_EINVAL, "the double-float residual needs a constant viscosity");
+  if (pb->refine != kind) {
+    for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
+    pb->graphs.clear();
+  }
+  pb->refine = kind;
+  return HHG_OK;
+}
+
+extern "C" int hhg_get_refinement_residual(hhg_problem* pb, int* kind) {
+  if (!pb || !kind) return fail(HHG_EINVAL, "null argument");
+  *kind = pb->refine == HHG_REFINE_DF32 && df_supported(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0)
+              ? HHG_REFINE_DF32
+              : HHG_REFINE_FP64;
+  return HHG_OK;
+}
 
 extern "C" int hhg_set_graph_mode(hhg_problem* pb, int on) {
   if (!pb) return fail(HHG_EINVAL, "null problem");

@@ -23,6 +23,7 @@ FP32 = 1
 SOLVE_FP64 = 0
 SOLVE_MIXED = 1
 OP = {"FULL": 0, "A": 1, "BT": 2, "B": 3, "C": 4, "MASS": 5}
+REFINE = {"fp64": 0, "df32": 1}   # arithmetic of the refinement residual
 AHAT = {"f": 0, "s": 1}
 
 
@@ -93,6 +94,9 @@ def load():
         "hhg_level_vector": [P, I, I, C.POINTER(VP)],
         "hhg_apply": [P, I, I, I, VP, VP],
         "hhg_residual": [P, I, I, VP, VP, VP, DP],
+        "hhg_refinement_residual": [P, I, VP, VP, VP],
+        "hhg_set_refinement_residual": [P, I],
+        "hhg_get_refinement_residual": [P, C.POINTER(C.c_int)],
         "hhg_smooth": [P, I, C.POINTER(Params), I, I, VP, VP],
         "hhg_restrict": [P, I, I, VP, VP],
         "hhg_prolongate_add": [P, I, I, VP, VP],
@@ -310,6 +314,20 @@ class Problem:
         _check(load().hhg_residual(self.h, level, self._prec(x), _ptr(x), _ptr(b), _ptr(r),
                                    _dp(nr) if norms else None), "hhg_residual")
         return (float(nr[0]), float(nr[1])) if norms else None
+
+    def refinement_residual(self, level, x, b, r):
+        """r (FP32) = fl32(b - calA x) of the mixed solve's refinement step,
+        x and b FP64 device tensors (hhg_refinement_residual)."""
+        _check(load().hhg_refinement_residual(self.h, level, _ptr(x), _ptr(b), _ptr(r)), "hhg_refinement_residual")
+
+    def set_refinement_residual(self, kind):
+        """kind: "fp64" or "df32" (hhg_set_refinement_residual)."""
+        _check(load().hhg_set_refinement_residual(self.h, REFINE[kind]), "hhg_set_refinement_residual")
+
+    def refinement_residual_kind(self):
+        k = C.c_int()
+        _check(load().hhg_get_refinement_residual(self.h, C.byref(k)), "hhg_get_refinement_residual")
+        return {v: n for n, v in REFINE.items()}[k.value]
 
     def smooth(self, level, prm, sweeps, x, b):
         _check(load().hhg_smooth(self.h, level, C.byref(prm), sweeps, self._prec(x), _ptr(x), _ptr(b)),

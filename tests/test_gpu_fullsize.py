@@ -109,6 +109,23 @@ def _dirichlet_mask(info, disc):
     return (I == 0) | (I == a - 1) | (J == 0) | (J == b - 1) | (K == 0) | (K == c - 1)
 
 
+def _smooth_field(info, disc):
+    """x = sin(pi X) sin(pi Y) sin(pi Z) (1 + c/2) on velocity component c
+    (0 on the boundary) and cos(pi X) cos(pi Y) cos(pi Z) on the pressure
+    nodes, canonical order, for a box mapped to the unit cube."""
+    def coords(a, b, c):
+        idx = np.arange(a * b * c, dtype=np.int64)
+        return (idx % a) / (a - 1), ((idx // a) % b) / (b - 1), (idx // (a * b)) / (c - 1)
+    if disc == "P2P1":
+        X, Y, Z = coords(2 * info.nx + 1, 2 * info.ny + 1, 2 * info.nz + 1)
+    else:
+        X, Y, Z = coords(info.nx + 1, info.ny + 1, info.nz + 1)
+    xp, yp, zp = coords(info.nx + 1, info.ny + 1, info.nz + 1)
+    su = np.sin(np.pi * X) * np.sin(np.pi * Y) * np.sin(np.pi * Z)
+    return np.concatenate([su * (1.0 + 0.5 * c) for c in range(3)] +
+                          [np.cos(np.pi * xp) * np.cos(np.pi * yp) * np.cos(np.pi * zp)])
+
+
 def _gather(vec, rows, nv):
     return np.array([vec[f * nv + n] if f < 3 else vec[3 * nv + n] for f, n in rows])
 
@@ -155,6 +172,22 @@ def test_fullsize_rows_match_oracle(disc, box, H, L, lc, nu_a):
     assert nr[0] == pytest.approx(np.linalg.norm(rh[:3 * nv]), rel=1e-12)
     assert nr[1] == pytest.approx(np.linalg.norm(rh[3 * nv:]), rel=1e-12)
     del xd, y, r, rh
+
+    # the mixed solve's refinement defect (double-float rows where they apply,
+    # else FP64 rows rounded to FP32) on a smooth x with b = 0: each row
+    # cancels to O(h^2) of s_i, so plain FP32 rows would miss the bound
+    xs = _smooth_field(info, disc)
+    xs[:3 * nv] *= vmask
+    refs, ss = sample_rows(box, H, L, disc, xs, rows, nu_a, with_abs=True)
+    assert pb.refinement_residual_kind() == ("df32" if nu_a == 0.0 else "fp64")
+    rd = pb.new_vector(L, prec=hhg.FP32)
+    pb.refinement_residual(L, pb.to_device(L, xs), pb.new_vector(L), rd)
+    gd = _gather(pb.to_host(L, rd), rows, nv)
+    errd = np.abs(gd + refs)
+    boundd = 2.0 ** -24 * np.abs(refs) + 2.0 ** -32 * ss
+    assert np.all(errd <= boundd), float((errd / np.maximum(boundd, 1e-300)).max())
+    assert np.median(np.abs(refs[~dirichlet]) / ss[~dirichlet]) < 1e-3
+    del rd
 
     # FP32 apply and residual (the V-cycle precision; the benchmark's roofline kernel)
     x32 = x.astype(np.float32).astype(np.float64)

@@ -422,6 +422,73 @@ def test_mixed_precision_close_to_fp64_oracle():
     assert err < 1e-5
 
 
+def _abs_row_sums(lev, x):
+    """s_i = sum_j |a_ij x_j| of the oracle's operator rows."""
+    u, p = lev.split(np.abs(x))
+    su = [abs(lev.A) @ u[c] + abs(lev.B[c]).T @ p for c in range(3)]
+    sp = sum(abs(lev.B[c]) @ u[c] for c in range(3)) + abs(lev.C) @ p
+    return lev.join(su, sp)
+
+
+@pytest.mark.parametrize("disc,box,L,H", [("P2P1", (1, 1, 1), 3, 1.0), ("P1P1", (2, 2, 2), 3, 0.5),
+                                          ("P1P1", (1, 2, 1), 4, 1.0)])
+def test_refinement_residual_double_float(disc, box, L, H):
+    """The mixed solve's refinement defect r = fl32(b - calA x)
+    (hhg_refinement_residual) in double-float arithmetic and in FP64, against
+    the oracle's FP64 residual, entrywise:
+        |r_i - r_i^oracle| <= 2^-24 |r_i^oracle| + 2^-32 (s_i + |b_i|),
+    s_i = sum_j |a_ij x_j|.  b = calA x + 1e-6 noise, so each row cancels to
+    about 1e-6 s_i: a row summed in plain FP32 (error ~ n 2^-24 s_i) misses
+    the bound by orders of magnitude, a dropped low part (2^-24 s_i) too.
+    P1-P1 boxes exercise the clipped C terms of the boundary pressure rows;
+    the 1 x 2 x 1 box at level 4 leaves a partly filled last warp."""
+    from paper_2010_13513_gb300 import hhg
+    pb = lib_problem(box, L, disc, lc=1, solve="mixed", H=H)
+    hy = oracle_hierarchy(box, L, disc, lc=1, H=H)
+    lev = hy.lv[L]
+    x = random_vector(lev, 21)
+    b = lev.apply(x) + 1e-6 * random_vector(lev, 22)
+    ref = lev.residual(x, b)
+    bound = 2.0 ** -24 * np.abs(ref) + 2.0 ** -32 * (_abs_row_sums(lev, x) + np.abs(b))
+    assert pb.refinement_residual_kind() == "df32"
+    xd, bd = pb.to_device(L, x), pb.to_device(L, b)
+    for kind in ("df32", "fp64"):
+        pb.set_refinement_residual(kind)
+        assert pb.refinement_residual_kind() == kind
+        r = pb.new_vector(L, prec=hhg.FP32)
+        pb.refinement_residual(L, xd, bd, r)
+        err = np.abs(pb.to_host(L, r) - ref)
+        assert np.all(err <= bound), (kind, float((err / bound).max()))
+    # plain FP32 rows on the same input miss the bound (the bound is sharp enough to tell)
+    r32 = pb.new_vector(L, prec=hhg.FP32)
+    pb.residual(L, pb.to_device(L, x, prec=hhg.FP32), pb.to_device(L, b, prec=hhg.FP32), r32)
+    assert np.any(np.abs(pb.to_host(L, r32) - ref) > bound)
+
+
+@pytest.mark.parametrize("disc,box,L,lc", [("P2P1", (1, 1, 1), 4, 2), ("P1P1", (1, 1, 1), 4, 0)])
+def test_mixed_fmg_refinement_kinds_agree(disc, box, L, lc):
+    """The mixed-precision FMG with the double-float refinement residual (the
+    default) and with the FP64 one: both within 1e-5 of the FP64 oracle's FMG
+    and within 1e-6 of each other.  The two defects differ by ~2^-40 of the
+    row sums before their rounding to FP32, which then differs in the last
+    bit for some entries; the FP32 V-cycles carry that into corrections that
+    differ at FP32 rounding (~1e-7 relative), not at the defects' 2^-40."""
+    from oracle.stokes import Params
+    from paper_2010_13513_gb300.hhg import Params as LParams
+    wl = curl_workload()
+    s = dict(nu_pre=3, nu_post=3, nu_inc=0, kappa=1, ahat="s", xi=1, omega_inv=OMEGA_INV[disc])
+    pb = lib_problem(box, L, disc, lc=lc, solve="mixed", workload=wl)
+    ref = oracle_hierarchy(box, L, disc, lc=lc, workload=wl).fmg(Params(**s))
+    sols = {}
+    for kind in ("df32", "fp64"):
+        pb.set_refinement_residual(kind)
+        x = pb.new_vector(L)
+        pb.fmg_solve(LParams.make(**s), x)
+        sols[kind] = pb.to_host(L, x)
+        assert rel(sols[kind], ref) < 1e-5, kind
+    assert rel(sols["df32"], sols["fp64"]) < 1e-6
+
+
 def test_fp32_kernels_track_fp64():
     """FP32 apply of the same operator: relative difference at FP32 rounding."""
     box, L = (1, 1, 1), 3

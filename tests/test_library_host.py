@@ -61,11 +61,11 @@ def test_mesh_rejects_other_meshes(hhg):
     assert b"origin" in buf.value
 
 
-def _problem(hhg, disc, L, lc, solve=0, err=0, box=(1, 1, 1)):
+def _problem(hhg, disc, L, lc, solve=0, err=0, box=(1, 1, 1), nu_a=0.0):
     lib = hhg.load()
     mesh = C.c_void_p()
     assert lib.hhg_mesh_create_box(*box, 1.0, C.byref(mesh)) == 0
-    d = hhg.ProblemDesc(disc, L, lc, solve, 0.0, 1, err)
+    d = hhg.ProblemDesc(disc, L, lc, solve, nu_a, 1, err)
     pb = C.c_void_p()
     rc = lib.hhg_problem_create(mesh, C.byref(d), C.byref(pb))
     return rc, pb, mesh
@@ -124,3 +124,35 @@ def test_batch_and_host_solve_entry_points_reject_bad_arguments(hhg):
     buf = C.create_string_buffer(256)
     lib.hhg_last_error(buf, 256)
     assert buf.value
+
+
+@pytest.mark.parametrize("disc", ["P1P1", "P2P1"])
+def test_refinement_residual_kind_and_argument_checks(hhg, disc):
+    """The refinement residual's arithmetic: double-float by default with a
+    constant viscosity, FP64 with a variable one (double-float refused);
+    out-of-range kinds, null handles and unbound problems give errors before
+    any device work."""
+    lib = hhg.load()
+    EINVAL, ESTATE = -1, -7
+    d = hhg.P1P1 if disc == "P1P1" else hhg.P2P1
+    kind = C.c_int(-1)
+    rc, pb, mesh = _problem(hhg, d, 3, 1, solve=1)
+    assert rc == 0
+    assert lib.hhg_get_refinement_residual(pb, C.byref(kind)) == 0 and kind.value == hhg.REFINE["df32"]
+    assert lib.hhg_set_refinement_residual(pb, hhg.REFINE["fp64"]) == 0
+    assert lib.hhg_get_refinement_residual(pb, C.byref(kind)) == 0 and kind.value == hhg.REFINE["fp64"]
+    assert lib.hhg_set_refinement_residual(pb, 7) == EINVAL
+    assert lib.hhg_set_refinement_residual(pb, hhg.REFINE["df32"]) == 0
+    assert lib.hhg_refinement_residual(pb, 3, C.c_void_p(256), C.c_void_p(256), C.c_void_p(256)) == ESTATE
+    lib.hhg_problem_destroy(pb)
+    lib.hhg_mesh_destroy(mesh)
+    rc, pb, mesh = _problem(hhg, d, 3, 1, solve=1, nu_a=1.5)
+    assert rc == 0
+    assert lib.hhg_get_refinement_residual(pb, C.byref(kind)) == 0 and kind.value == hhg.REFINE["fp64"]
+    assert lib.hhg_set_refinement_residual(pb, hhg.REFINE["df32"]) == EINVAL
+    assert lib.hhg_set_refinement_residual(pb, hhg.REFINE["fp64"]) == 0
+    lib.hhg_problem_destroy(pb)
+    lib.hhg_mesh_destroy(mesh)
+    assert lib.hhg_set_refinement_residual(None, 0) == EINVAL
+    assert lib.hhg_get_refinement_residual(None, C.byref(kind)) == EINVAL
+    assert lib.hhg_refinement_residual(None, 3, None, None, None) == EINVAL
