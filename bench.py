@@ -940,8 +940,12 @@ def main():
     alg_bytes, t_apply = apply_roofline(pb)
     pk, src = peaks()
     achieved = alg_bytes / t_apply / 1e9
-    e2e_t, h2d, d2h = e2e_steps(pb, wl, prm, max(2, min(args.steps, 3)))
-    e2e_v = dofs / statistics.mean(e2e_t)
+    # wall-clock steps on a shared host: an occasional step stalls for tens of
+    # ms outside the library (seen as isolated 56-94 ms steps among 28.5 ms
+    # ones), so the value is the median step; the mean and every step are
+    # reported beside it
+    e2e_t, h2d, d2h = e2e_steps(pb, wl, prm, max(3, min(args.steps, 7)))
+    e2e_v = dofs / statistics.median(e2e_t)
     nn = learned_coarse(pb, wl, prm, max(3, args.steps // 2), 2, stream) if learned else None
     sh = pb.launch_shape(L)
     traffic = measured_traffic(sh)
@@ -972,7 +976,9 @@ def main():
                                         f"{[sh[3], sh[4]]})") if traffic is not None else None,
                      "kernel": f"FP32 operator apply y = calA x, level {L} (FULL; launch shape {list(sh)})",
                      "alg_bytes": alg_bytes, "avg_launch_us": t_apply * 1e6, "peak_source": src},
-        "e2e": {"value": e2e_v, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_v, "unit": "DoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "statistic": "median step", "mean_value": dofs / statistics.mean(e2e_t),
+                "step_ms": [t * 1e3 for t in e2e_t]},
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
     }

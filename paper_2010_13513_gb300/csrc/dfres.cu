@@ -21,7 +21,7 @@
 // Work layout (as the vector row kernels of the FP32/FP64 path): grid x over
 // the padded (i, j) plane in warps of 4 x 32 positions, y over groups of kp
 // planes, z over the rows of the operator; a thread evaluates 4 sites 32
-// positions apart.  The terms of a row are a loop over weights and offsets in
+// positions apart, two at a time with the paired FP32 (f32x2) instructions.  The terms of a row are a loop over weights and offsets in
 // the constant bank, so a row's code stays small in the instruction cache.
 // Boundary pressure rows (P1-P1: the C terms of the cubes inside the box) add
 // their per-cube C terms in FP64; they are a few per cent of the pressure
@@ -91,16 +91,66 @@ __device__ __forceinline__ void dot2_term(float wh, float wl, float xh, float xl
   c = __fadd_rn(c, __fadd_rn(d, e));
 }
 
-// terms [T0, T0 + N) of a row at NS sites 32 positions apart (idx + 32 v)
+// a - b on both halves (sub.rn.f32x2: each half rounds as the scalar
+// subtraction)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rr;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rr, ra, rb;\n mov.b64 {%0, %1}, rr;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
+// dot2_term on two sites at once with the paired FP32 instructions (each
+// half of an f32x2 operation rounds as the scalar one, so the sums are those
+// of dot2_term bit for bit)
+__device__ __forceinline__ void dot2_term2(float2 wh, float2 wl, float2 xh, float2 xl, float2& s, float2& c) {
+  const float2 p = __fmul2_rn(wh, xh);
+  float2 e = __ffma2_rn(wh, xh, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(wl, xh, e);
+  e = __ffma2_rn(wh, xl, e);
+  const float2 t = __fadd2_rn(s, p);
+  const float2 z = sub2(t, s);
+  const float2 d = __fadd2_rn(sub2(s, sub2(t, z)), sub2(p, z));
+  s = t;
+  c = __fadd2_rn(c, __fadd2_rn(d, e));
+}
+
+// terms [T0, T0 + N) of a row at NS sites 32 positions apart (idx + 32 v);
+// an even NS runs the sites in pairs
 template <int T0, int N, int NS, class Tab>
 __device__ __forceinline__ void dot2_seg(const Tab& tab, const float* __restrict__ xh, const float* __restrict__ xl,
                                          int64_t idx, float (&s)[NS], float (&c)[NS]) {
-#pragma unroll 2
-  for (int t = T0; t < T0 + N; ++t) {
-    const float wh = tab.wh[t], wl = tab.wl[t];
-    const int64_t q = idx + tab.off[t];
+  if constexpr (NS % 2 == 0) {
+    float2 s2[NS / 2], c2[NS / 2];
 #pragma unroll
-    for (int v = 0; v < NS; ++v) dot2_term(wh, wl, __ldg(xh + q + 32 * v), __ldg(xl + q + 32 * v), s[v], c[v]);
+    for (int h = 0; h < NS / 2; ++h) {
+      s2[h] = make_float2(s[2 * h], s[2 * h + 1]);
+      c2[h] = make_float2(c[2 * h], c[2 * h + 1]);
+    }
+#pragma unroll 4
+    for (int t = T0; t < T0 + N; ++t) {
+      const float wh = tab.wh[t], wl = tab.wl[t];
+      const int64_t q = idx + tab.off[t];
+#pragma unroll
+      for (int h = 0; h < NS / 2; ++h)
+        dot2_term2(make_float2(wh, wh), make_float2(wl, wl),
+                   make_float2(__ldg(xh + q + 64 * h), __ldg(xh + q + 64 * h + 32)),
+                   make_float2(__ldg(xl + q + 64 * h), __ldg(xl + q + 64 * h + 32)), s2[h], c2[h]);
+    }
+#pragma unroll
+    for (int h = 0; h < NS / 2; ++h) {
+      s[2 * h] = s2[h].x; s[2 * h + 1] = s2[h].y;
+      c[2 * h] = c2[h].x; c[2 * h + 1] = c2[h].y;
+    }
+  } else {
+#pragma unroll 4
+    for (int t = T0; t < T0 + N; ++t) {
+      const float wh = tab.wh[t], wl = tab.wl[t];
+      const int64_t q = idx + tab.off[t];
+#pragma unroll
+      for (int v = 0; v < NS; ++v) dot2_term(wh, wl, __ldg(xh + q + 32 * v), __ldg(xl + q + 32 * v), s[v], c[v]);
+    }
   }
 }
 
