@@ -569,6 +569,16 @@ def run_p1_visc(args):
     t = _timed(lambda: pb.fmg_solve(prm, x, stats=False), args.steps, args.warmup, stream)
     clocks = sampler.stop()
     gu, gp = _gamma(pb, wl, prm, x, L)
+    # the same solve with the FP64 refinement defect instead of the double-float one
+    refine = {"kind": pb.refinement_residual_kind()}
+    if refine["kind"] == "df32":
+        xf = pb.new_vector(L)
+        pb.set_refinement_residual("fp64")
+        tf = _timed(lambda: pb.fmg_solve(prm, xf, stats=False), max(3, args.steps // 2), 2, stream)
+        pb.set_refinement_residual("df32")
+        refine.update({"fp64_refinement_ms_per_step": tf * 1e3, "df32_speedup": tf / t,
+                       "rel_diff_vs_fp64_refinement": float(torch.linalg.norm(x - xf) / torch.linalg.norm(xf))})
+        del xf
     # operator apply roofline at this size (FP32)
     xa = pb.new_vector(L, 1)
     xa.uniform_(-1, 1)
@@ -583,6 +593,7 @@ def run_p1_visc(args):
         "config": {"workload": f"P1-P1 PSPG, 48-tet cube, level 7, nu = exp({a:.4f} z), curl solution, FP32 V-cycles "
                                "in FP64 refinement", "dofs": info.n_dofs, "omega_inv": om,
                    "params": [2, 3, 2, 1, "s", 1], "gamma_u": gu, "gamma_p": gp, "wu_model": st.wu_model,
+                   "refinement_residual": refine,
                    "launch_shapes": {str(k): v for k, v in shapes.items()}},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": ach / pk["hbm_gbs"], "kernel": "FP32 FULL apply, level 7", "avg_launch_us": ta * 1e6,

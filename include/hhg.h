@@ -217,18 +217,19 @@ int hhg_residual(hhg_problem* pb, int level, int prec, const void* x, const void
  * r an FP32 device vector.  With HHG_REFINE_DF32 (the default where it
  * applies) every row is a compensated dot product in double-float arithmetic
  * (Ogita, Rump and Oishi's Dot2 on x and the weights split into two FP32
- * numbers each): |r - fl32(b - calA x)| <= 2^-24 |b - calA x| + about
- * (n^2 2^-48 + 2^-46) sum_j |a_ij x_j| for a row of n terms.  With
+ * numbers each; with a variable viscosity the row's segments scaled by their
+ * FP64 factors exp(+-a h k) in the same arithmetic): |r - fl32(b - calA x)|
+ * <= 2^-24 |b - calA x| + about (n^2 2^-48 + 2^-46) sum_j |a_ij x_j| for a
+ * row of n terms.  With
  * HHG_REFINE_FP64 the rows are FP64 and rounded to FP32.  Overwrites the
  * level's internal FP32 iterate and FP64 scratch vector (x, b and r must not
  * be those).  HHG_EINVAL unless the problem was created with
  * HHG_SOLVE_MIXED. */
 int hhg_refinement_residual(hhg_problem* pb, int level, const double* x, const double* b, float* r);
 /* Arithmetic of the refinement residual (HHG_REFINE_FP64 or HHG_REFINE_DF32;
- * default HHG_REFINE_DF32).  HHG_REFINE_DF32 covers the operators with
- * constant viscosity (HHG_EINVAL otherwise; variable-viscosity problems use
- * FP64).  Drops cached graphs when the choice changes.  The get call reports
- * the arithmetic in effect. */
+ * default HHG_REFINE_DF32, which covers both discretisations with constant
+ * or variable viscosity).  Drops cached graphs when the choice changes.  The
+ * get call reports the arithmetic in effect. */
 int hhg_set_refinement_residual(hhg_problem* pb, int kind);
 int hhg_get_refinement_residual(hhg_problem* pb, int* kind);
 /* `sweeps` inexact Uzawa iterations (Eq. uzawa-iteration) on x in place. */

@@ -25,7 +25,9 @@
 // the constant bank, so a row's code stays small in the instruction cache.
 // Boundary pressure rows (P1-P1: the C terms of the cubes inside the box) add
 // their per-cube C terms in FP64; they are a few per cent of the pressure
-// rows.
+// rows.  With a variable viscosity nu = exp(a z) the segments of a row are
+// summed apart and scaled by the row's FP64 factors exp(+-a h k) in
+// double-float arithmetic.
 #include "dfres.h"
 
 #include <cuda_runtime.h>
@@ -49,8 +51,8 @@ struct DfTab {
   int off[N];        // linear offsets arr * array_stride + di + dj sx + dk sy
 };
 
-template <int DISC>
-using DfTabOf = DfTab<gen::S<DISC, 0, OP_FULL>::N>;
+template <int DISC, int VARNU>
+using DfTabOf = DfTab<gen::S<DISC, VARNU, OP_FULL>::N>;
 
 // v = hi + lo with |v - hi - lo| < 2^-46 |v|: hi takes the leading 24 bits of
 // v's significand, lo the next 23 (both truncated).  For v = 0, |v| < 2^-100
@@ -170,25 +172,50 @@ __device__ double boundary_c64(const Geo& g, const OpDev& op, int r, int i, int 
   return a;
 }
 
-// the residual of row R at one site from its sums: (s, c) over segments 0
-// and 1, (s2, c2) over segment 2 (C); bnd: the site lies on the box boundary
-template <int OUT, int ALL, int N2>
+// (s, c) += a (u + v) for an FP64 factor a = ah + al: ah u = p + e exactly
+// (FMA), the small products into e, p into the sum by TwoSum
+__device__ __forceinline__ void df_add_scaled(double a, float u, float v, float& s, float& c) {
+  float ah, al;
+  split_df(a, ah, al);
+  const float p = __fmul_rn(ah, u);
+  float e = __fmaf_rn(ah, u, -p);
+  e = __fmaf_rn(ah, v, e);
+  e = __fmaf_rn(al, u, e);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(d, e));
+}
+
+// the residual of row R at one site from its sums: (s, c) over segment 0
+// (and segment 1 with a constant viscosity), (s1, c1) over segment 1 with a
+// variable one (scaled by exp(+nu_a h k)), (s2, c2) over segment 2 (C; scaled
+// by exp(-nu_a h k) with a variable viscosity); bnd: the site lies on the box
+// boundary
+template <int OUT, int ALL, int N2, int VARNU>
 __device__ __forceinline__ void df_store(const Geo& g, const OpDev& op, int R, int i, int j, int k, bool bnd,
-                                         const float* xh, const float* xl, int64_t idx, float s, float c, float s2,
-                                         float c2, const double* __restrict__ b, float* __restrict__ r) {
+                                         const float* xh, const float* xl, int64_t idx, float s, float c, float s1,
+                                         float c1, float s2, float c2, const double* __restrict__ b,
+                                         float* __restrict__ r) {
   const int64_t iy = int64_t(OUT) * g.arr + idx;
   if (bnd && !ALL) {                                 // Dirichlet velocity row
     r[iy] = 0.0f;
     return;
   }
   const double bv = __ldg(b + iy);
+  const double es = VARNU ? __ldg(g.esc + k) : 1.0, eis = VARNU ? __ldg(g.eisc + k) : 1.0;
   if (N2 > 0 && bnd) {
     // boundary pressure row: the clipped C terms in FP64
     const double cb = boundary_c64(g, op, R, i, j, k, xh, xl, idx);
-    r[iy] = __double2float_rn(bv - (double(s) + double(c)) - cb);
+    const double a1 = VARNU ? es * (double(s1) + double(c1)) : 0.0;
+    r[iy] = __double2float_rn(bv - (double(s) + double(c)) - a1 - eis * cb);
     return;
   }
-  if (N2 > 0) {                                      // (s, c) += (s2, c2)
+  if (VARNU) {
+    df_add_scaled(es, s1, c1, s, c);
+    if (N2 > 0) df_add_scaled(eis, s2, c2, s, c);
+  } else if (N2 > 0) {                               // (s, c) += (s2, c2)
     const float t = __fadd_rn(s, s2);
     const float z = __fsub_rn(t, s);
     const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
@@ -207,7 +234,7 @@ __device__ __forceinline__ void df_store(const Geo& g, const OpDev& op, int R, i
 // row R = (OUT, OG, ALL, T0, N0, N1, N2) on the sites of the block: the
 // indexing of the vector row kernels (four runs of 32 positions per warp; a
 // warp whose last run passes the group's last site takes its sites one by one)
-template <int OUT, int OG, int ALL, int T0, int N0, int N1, int N2, class Tab>
+template <int VARNU, int OUT, int OG, int ALL, int T0, int N0, int N1, int N2, class Tab>
 __device__ __forceinline__ void df_rows(const Geo& g, int R, const float* __restrict__ xh,
                                         const float* __restrict__ xl, const double* __restrict__ b,
                                         float* __restrict__ r, const OpDev& op, const Tab& tab, int kp) {
@@ -231,12 +258,18 @@ __device__ __forceinline__ void df_rows(const Geo& g, int R, const float* __rest
         const bool bnd = 2 * i + ox == 0 || 2 * i + ox == 2 * g.nx || 2 * j + oy == 0 || 2 * j + oy == 2 * g.ny ||
                          2 * k + oz == 0 || 2 * k + oz == 2 * g.nz;
         const int64_t idx = int64_t(m) + 1 + g.sx + int64_t(k + 1) * g.sy;
-        float s[1] = {0.0f}, c[1] = {0.0f}, s2[1] = {0.0f}, c2[1] = {0.0f};
+        float s[1] = {0.0f}, c[1] = {0.0f}, s1[1] = {0.0f}, c1[1] = {0.0f}, s2[1] = {0.0f}, c2[1] = {0.0f};
         if (!bnd || ALL) {
-          dot2_seg<T0, N0 + N1, 1>(tab, xh, xl, idx, s, c);
+          if (VARNU) {
+            dot2_seg<T0, N0, 1>(tab, xh, xl, idx, s, c);
+            dot2_seg<T0 + N0, N1, 1>(tab, xh, xl, idx, s1, c1);
+          } else {
+            dot2_seg<T0, N0 + N1, 1>(tab, xh, xl, idx, s, c);
+          }
           if (N2 > 0 && !bnd) dot2_seg<T0 + N0 + N1, N2, 1>(tab, xh, xl, idx, s2, c2);
         }
-        df_store<OUT, ALL, N2>(g, op, R, i, j, k, bnd, xh, xl, idx, s[0], c[0], s2[0], c2[0], b, r);
+        df_store<OUT, ALL, N2, VARNU>(g, op, R, i, j, k, bnd, xh, xl, idx, s[0], c[0], s1[0], c1[0], s2[0], c2[0], b,
+                                      r);
       }
     return;
   }
@@ -253,17 +286,22 @@ __device__ __forceinline__ void df_rows(const Geo& g, int R, const float* __rest
 #pragma unroll 1
   for (int k = k0; k < k1; ++k) {
     const int64_t idx = int64_t(m0 + lane) + 1 + g.sx + int64_t(k + 1) * g.sy;
-    float s[V], c[V], s2[V], c2[V];
+    float s[V], c[V], s1[V], c1[V], s2[V], c2[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) s[v] = c[v] = s2[v] = c2[v] = 0.0f;
-    dot2_seg<T0, N0 + N1, V>(tab, xh, xl, idx, s, c);
+    for (int v = 0; v < V; ++v) s[v] = c[v] = s1[v] = c1[v] = s2[v] = c2[v] = 0.0f;
+    if (VARNU) {
+      dot2_seg<T0, N0, V>(tab, xh, xl, idx, s, c);
+      dot2_seg<T0 + N0, N1, V>(tab, xh, xl, idx, s1, c1);
+    } else {
+      dot2_seg<T0, N0 + N1, V>(tab, xh, xl, idx, s, c);
+    }
     if (N2 > 0) dot2_seg<T0 + N0 + N1, N2, V>(tab, xh, xl, idx, s2, c2);
     const bool bk = 2 * k + oz == 0 || 2 * k + oz == 2 * g.nz;
 #pragma unroll
     for (int v = 0; v < V; ++v)
       if (okv[v])
-        df_store<OUT, ALL, N2>(g, op, R, iv[v], jv[v], k, bijv[v] || bk, xh, xl, idx + 32 * v, s[v], c[v], s2[v],
-                               c2[v], b, r);
+        df_store<OUT, ALL, N2, VARNU>(g, op, R, iv[v], jv[v], k, bijv[v] || bk, xh, xl, idx + 32 * v, s[v], c[v],
+                                      s1[v], c1[v], s2[v], c2[v], b, r);
   }
 }
 
@@ -275,15 +313,15 @@ __device__ __forceinline__ void by_row(int r, F&& f) {
   }
 }
 
-template <int DISC>
+template <int DISC, int VARNU>
 __global__ void __launch_bounds__(128) k_res_df(Geo g, const float* __restrict__ xh, const float* __restrict__ xl,
                                                 const double* __restrict__ b, float* __restrict__ r, OpDev op, int kp,
-                                                const __grid_constant__ DfTabOf<DISC> tab) {
-  using S = gen::S<DISC, 0, OP_FULL>;
+                                                const __grid_constant__ DfTabOf<DISC, VARNU> tab) {
+  using S = gen::S<DISC, VARNU, OP_FULL>;
   by_row<S, 0>(int(blockIdx.z), [&](auto rc) {
     constexpr int R = decltype(rc)::value;
     constexpr gen::RowS rw = S::rows[R];
-    df_rows<rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, xh, xl, b, r, op, tab, kp);
+    df_rows<VARNU, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, xh, xl, b, r, op, tab, kp);
   });
 }
 
@@ -303,11 +341,11 @@ __global__ void k_split_df(const double2* __restrict__ x, float2* __restrict__ h
 constexpr int kDfThreads = 128;
 constexpr int kDfPlanes = 2;
 
-template <int DISC>
+template <int DISC, int VARNU>
 void launch_df(const Geo& g, const OpDev& od, const char* tab, const double* x, const double* b, float* xh, float* xl,
                float* r, cudaStream_t s) {
-  using S = gen::S<DISC, 0, OP_FULL>;
-  DfTabOf<DISC> tb;
+  using S = gen::S<DISC, VARNU, OP_FULL>;
+  DfTabOf<DISC, VARNU> tb;
   std::memcpy(&tb, tab, sizeof(tb));
   const int64_t n = (3 * int64_t(g.G) + 1) * g.arr;  // a multiple of 64
   const int64_t n2 = n / 2;
@@ -319,24 +357,28 @@ void launch_df(const Geo& g, const OpDev& od, const char* tab, const double* x, 
   const dim3 grd(unsigned((warps * 32 + kDfThreads - 1) / kDfThreads), unsigned((g.nz + 1 + kDfPlanes - 1) / kDfPlanes),
                  unsigned(S::R));
   ++g_launches;
-  k_res_df<DISC><<<grd, kDfThreads, 0, s>>>(g, xh, xl, b, r, od, kDfPlanes, tb);
+  k_res_df<DISC, VARNU><<<grd, kDfThreads, 0, s>>>(g, xh, xl, b, r, od, kDfPlanes, tb);
 }
 
-void df_launch(int disc, const Geo& g, const OpDev& od, const char* tab, const double* x, const double* b, float* xh,
-               float* xl, float* r, cudaStream_t s) {
-  if (disc == 1) launch_df<1>(g, od, tab, x, b, xh, xl, r, s);
-  else launch_df<2>(g, od, tab, x, b, xh, xl, r, s);
+void df_launch(int disc, int varnu, const Geo& g, const OpDev& od, const char* tab, const double* x, const double* b,
+               float* xh, float* xl, float* r, cudaStream_t s) {
+  if (disc == 1 && !varnu) launch_df<1, 0>(g, od, tab, x, b, xh, xl, r, s);
+  else if (disc == 1) launch_df<1, 1>(g, od, tab, x, b, xh, xl, r, s);
+  else if (!varnu) launch_df<2, 0>(g, od, tab, x, b, xh, xl, r, s);
+  else launch_df<2, 1>(g, od, tab, x, b, xh, xl, r, s);
 }
 
 }  // namespace
 
-bool df_supported(int disc, int varnu) { return varnu == 0 && (disc == 1 || disc == 2); }
+bool df_supported(int disc, int varnu) { return (varnu == 0 || varnu == 1) && (disc == 1 || disc == 2); }
 
 bool df_table(int disc, int varnu, const std::vector<char>& ftab64, std::vector<char>& out) {
   out.clear();
   if (!df_supported(disc, varnu)) return false;
-  const int N = disc == 1 ? gen::S<1, 0, OP_FULL>::N : gen::S<2, 0, OP_FULL>::N;
-  const size_t bytes = disc == 1 ? sizeof(DfTabOf<1>) : sizeof(DfTabOf<2>);
+  const int N = disc == 1 ? (varnu ? gen::S<1, 1, OP_FULL>::N : gen::S<1, 0, OP_FULL>::N)
+                          : (varnu ? gen::S<2, 1, OP_FULL>::N : gen::S<2, 0, OP_FULL>::N);
+  const size_t bytes = disc == 1 ? (varnu ? sizeof(DfTabOf<1, 1>) : sizeof(DfTabOf<1, 0>))
+                                 : (varnu ? sizeof(DfTabOf<2, 1>) : sizeof(DfTabOf<2, 0>));
   if (ftab64.size() < size_t(N) * 12) return false;
   // the FP64 table image: N weights, then N offsets
   const double* w = reinterpret_cast<const double*>(ftab64.data());
@@ -353,14 +395,14 @@ bool df_table(int disc, int varnu, const std::vector<char>& ftab64, std::vector<
   return true;
 }
 
-void df_residual(int disc, const Geo& g, const OpDev& od, const std::vector<char>& dftab, const double* x,
+void df_residual(int disc, int varnu, const Geo& g, const OpDev& od, const std::vector<char>& dftab, const double* x,
                  const double* b, float* xh, float* xl, float* r, cudaStream_t s) {
   const char* tab = dftab.data();
   if (g_rec) {
-    g_rec->native([=](cudaStream_t s_) { df_launch(disc, g, od, tab, x, b, xh, xl, r, s_); });
+    g_rec->native([=](cudaStream_t s_) { df_launch(disc, varnu, g, od, tab, x, b, xh, xl, r, s_); });
     return;
   }
-  df_launch(disc, g, od, tab, x, b, xh, xl, r, s);
+  df_launch(disc, varnu, g, od, tab, x, b, xh, xl, r, s);
 }
 
 }  // namespace hhg

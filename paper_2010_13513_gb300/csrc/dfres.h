@@ -11,7 +11,7 @@
 namespace hhg {
 
 // whether the double-float residual covers this operator (the full operator
-// with constant viscosity)
+// of P1-P1 or P2-P1, constant or variable viscosity)
 bool df_supported(int disc, int varnu);
 
 // the kernel's parameter block (weights split into two FP32 numbers, linear
@@ -24,7 +24,7 @@ bool df_table(int disc, int varnu, const std::vector<char>& ftab64, std::vector<
 // floats each (they receive the two FP32 parts of x).  od: the level's
 // generic tables (per-cube terms of the boundary pressure rows).  While a
 // batch records, the launches are recorded as native ops.
-void df_residual(int disc, const Geo& g, const OpDev& od, const std::vector<char>& dftab, const double* x,
+void df_residual(int disc, int varnu, const Geo& g, const OpDev& od, const std::vector<char>& dftab, const double* x,
                  const double* b, float* xh, float* xl, float* r, cudaStream_t s);
 
 }  // namespace hhg

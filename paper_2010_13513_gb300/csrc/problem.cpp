@@ -859,8 +859,8 @@ int residual(hhg_problem* pb, Level& lv, const T* x, const T* b, T* r) {
 // tmp64 rounded to FP32
 int refinement_residual(hhg_problem* pb, Level& lv, const double* x, const double* b, float* r32) {
   if (pb->refine == HHG_REFINE_DF32 && !lv.dftab.empty()) {
-    df_residual(pb->desc.disc, lv.g, lv.op[OP_FULL], lv.dftab, x, b, lv.x32, reinterpret_cast<float*>(lv.tmp64), r32,
-                pb->stream);
+    df_residual(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0, lv.g, lv.op[OP_FULL], lv.dftab, x, b, lv.x32,
+                reinterpret_cast<float*>(lv.tmp64), r32, pb->stream);
     HHG_CHECK_LAUNCH();
     pb->wu_counted += level_weight(pb, lv);
     return HHG_OK;
@@ -1510,7 +1510,7 @@ extern "C" int hhg_set_refinement_residual(hhg_problem* pb, int kind) {
   if (kind != HHG_REFINE_FP64 && kind != HHG_REFINE_DF32)
     return fail(HHG_EINVAL, "kind must be HHG_REFINE_FP64 or HHG_REFINE_DF32");
   if (kind == HHG_REFINE_DF32 && !df_supported(pb->desc.disc, pb->desc.nu_a != 0.0 ? 1 : 0))
-    return fail(HHG_EINVAL, "the double-float residual needs a constant viscosity");
+    return fail(HHG_EINVAL, "the double-float residual does not cover this operator");
   if (pb->refine != kind) {
     for (auto& kv : pb->graphs) cudaGraphExecDestroy(kv.second.exec);
     pb->graphs.clear();

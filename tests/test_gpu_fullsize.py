@@ -173,13 +173,13 @@ def test_fullsize_rows_match_oracle(disc, box, H, L, lc, nu_a):
     assert nr[1] == pytest.approx(np.linalg.norm(rh[3 * nv:]), rel=1e-12)
     del xd, y, r, rh
 
-    # the mixed solve's refinement defect (double-float rows where they apply,
-    # else FP64 rows rounded to FP32) on a smooth x with b = 0: each row
-    # cancels to O(h^2) of s_i, so plain FP32 rows would miss the bound
+    # the mixed solve's refinement defect (double-float rows) on a smooth x
+    # with b = 0: each row cancels to O(h^2) of s_i, so plain FP32 rows would
+    # miss the bound
     xs = _smooth_field(info, disc)
     xs[:3 * nv] *= vmask
     refs, ss = sample_rows(box, H, L, disc, xs, rows, nu_a, with_abs=True)
-    assert pb.refinement_residual_kind() == ("df32" if nu_a == 0.0 else "fp64")
+    assert pb.refinement_residual_kind() == "df32"
     rd = pb.new_vector(L, prec=hhg.FP32)
     pb.refinement_residual(L, pb.to_device(L, xs), pb.new_vector(L), rd)
     gd = _gather(pb.to_host(L, rd), rows, nv)

@@ -430,9 +430,10 @@ def _abs_row_sums(lev, x):
     return lev.join(su, sp)
 
 
-@pytest.mark.parametrize("disc,box,L,H", [("P2P1", (1, 1, 1), 3, 1.0), ("P1P1", (2, 2, 2), 3, 0.5),
-                                          ("P1P1", (1, 2, 1), 4, 1.0)])
-def test_refinement_residual_double_float(disc, box, L, H):
+@pytest.mark.parametrize("disc,box,L,H,nu_a", [("P2P1", (1, 1, 1), 3, 1.0, 0.0), ("P1P1", (2, 2, 2), 3, 0.5, 0.0),
+                                               ("P1P1", (1, 2, 1), 4, 1.0, 0.0), ("P1P1", (2, 2, 2), 3, 0.5, 1.7),
+                                               ("P2P1", (1, 1, 1), 3, 1.0, 1.3)])
+def test_refinement_residual_double_float(disc, box, L, H, nu_a):
     """The mixed solve's refinement defect r = fl32(b - calA x)
     (hhg_refinement_residual) in double-float arithmetic and in FP64, against
     the oracle's FP64 residual, entrywise:
@@ -441,10 +442,11 @@ def test_refinement_residual_double_float(disc, box, L, H):
     about 1e-6 s_i: a row summed in plain FP32 (error ~ n 2^-24 s_i) misses
     the bound by orders of magnitude, a dropped low part (2^-24 s_i) too.
     P1-P1 boxes exercise the clipped C terms of the boundary pressure rows;
-    the 1 x 2 x 1 box at level 4 leaves a partly filled last warp."""
+    the 1 x 2 x 1 box at level 4 leaves a partly filled last warp; nu_a != 0
+    (nu = exp(nu_a z)) the segments scaled by the rows' exp(+-nu_a h k)."""
     from paper_2010_13513_gb300 import hhg
-    pb = lib_problem(box, L, disc, lc=1, solve="mixed", H=H)
-    hy = oracle_hierarchy(box, L, disc, lc=1, H=H)
+    pb = lib_problem(box, L, disc, lc=1, solve="mixed", H=H, nu_a=nu_a)
+    hy = oracle_hierarchy(box, L, disc, lc=1, H=H, nu_a=nu_a)
     lev = hy.lv[L]
     x = random_vector(lev, 21)
     b = lev.apply(x) + 1e-6 * random_vector(lev, 22)

@@ -128,10 +128,9 @@ def test_batch_and_host_solve_entry_points_reject_bad_arguments(hhg):
 
 @pytest.mark.parametrize("disc", ["P1P1", "P2P1"])
 def test_refinement_residual_kind_and_argument_checks(hhg, disc):
-    """The refinement residual's arithmetic: double-float by default with a
-    constant viscosity, FP64 with a variable one (double-float refused);
-    out-of-range kinds, null handles and unbound problems give errors before
-    any device work."""
+    """The refinement residual's arithmetic: double-float by default (constant
+    and variable viscosity), FP64 on request; out-of-range kinds, null
+    handles and unbound problems give errors before any device work."""
     lib = hhg.load()
     EINVAL, ESTATE = -1, -7
     d = hhg.P1P1 if disc == "P1P1" else hhg.P2P1
@@ -148,9 +147,10 @@ def test_refinement_residual_kind_and_argument_checks(hhg, disc):
     lib.hhg_mesh_destroy(mesh)
     rc, pb, mesh = _problem(hhg, d, 3, 1, solve=1, nu_a=1.5)
     assert rc == 0
-    assert lib.hhg_get_refinement_residual(pb, C.byref(kind)) == 0 and kind.value == hhg.REFINE["fp64"]
-    assert lib.hhg_set_refinement_residual(pb, hhg.REFINE["df32"]) == EINVAL
+    assert lib.hhg_get_refinement_residual(pb, C.byref(kind)) == 0 and kind.value == hhg.REFINE["df32"]
     assert lib.hhg_set_refinement_residual(pb, hhg.REFINE["fp64"]) == 0
+    assert lib.hhg_get_refinement_residual(pb, C.byref(kind)) == 0 and kind.value == hhg.REFINE["fp64"]
+    assert lib.hhg_set_refinement_residual(pb, hhg.REFINE["df32"]) == 0
     lib.hhg_problem_destroy(pb)
     lib.hhg_mesh_destroy(mesh)
     assert lib.hhg_set_refinement_residual(None, 0) == EINVAL
