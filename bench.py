@@ -405,6 +405,48 @@ def aligned_batch(timed, n=48, L=4):
     return out
 
 
+def accuracy_batch(n=24, levels=(3, 5)):
+    """Accuracy of batched solves at discretisation-error level: n uneven
+    problems (Kuhn boxes {1,2}^3, levels 3..5, P1-P1 / P2-P1) with the
+    manufactured curl solution, solved together by one batch graph; gamma_u,
+    gamma_p (Eq. gamma) of every problem, the largest of each, and whether all
+    meet the (2, 2) bound and the Table 3 bound pairs."""
+    import torch
+    from hhg_inputs import Workload, batched_problem_list
+    from paper_2010_13513_gb300 import hhg
+    specs = batched_problem_list(1, n=n, levels=levels)
+    pbs, prms, wls = [], [], []
+    for sp in specs:
+        lc = 0 if sp["disc"] == "P1P1" else 1
+        H = 1.0 / max(sp["box"])
+        pb = hhg.Problem(hhg.Mesh.box(*sp["box"], H), disc=sp["disc"], L=sp["level"], coarse_level=lc, solve="mixed",
+                         error_level=True)
+        wl = Workload("curl", box=sp["box"], H=H)
+        hhg.set_workload_rhs(pb, wl)
+        info = pb.layout(sp["level"])
+        om = pb.estimate_omega(sp["level"], np.random.default_rng(sp["seed"]).uniform(-1, 1, info.n_pressure_nodes), 30)
+        s = dict(nu_pre=2, nu_post=3, nu_inc=2, kappa=1, ahat="s", xi=1) if sp["disc"] == "P1P1" else PARAMS
+        prms.append(hhg.Params.make(**s, omega_inv=om))
+        pbs.append(pb)
+        wls.append(wl)
+    batch = hhg.Batch(pbs)
+    batch.fmg_solve(prms)
+    torch.cuda.synchronize()
+    rows = []
+    for sp, pb, prm, wl in zip(specs, pbs, prms, wls):
+        L = sp["level"]
+        gu, gp = _gamma(pb, wl, prm, pb.level_vector(L, "x").clone(), L)
+        rows.append({"disc": sp["disc"], "box": list(sp["box"]), "level": L, "gamma_u": gu, "gamma_p": gp})
+    gu_max = max(r["gamma_u"] for r in rows)
+    gp_max = max(r["gamma_p"] for r in rows)
+    return {"workload": f"{n} problems, Kuhn boxes {{1,2}}^3, levels {levels[0]}..{levels[1]}, P1-P1 / P2-P1, "
+                        "manufactured curl solution, one batch graph",
+            "grouping_used": batch.grouping(), "gamma_u_max": gu_max, "gamma_p_max": gp_max,
+            "all_within": {f"({bu}, {bp})": all(r["gamma_u"] <= bu and r["gamma_p"] <= bp for r in rows)
+                           for bu, bp in ((2, 2), (1.1, 2), (1.1, 5), (2, 10))},
+            "problems": rows}
+
+
 def run_batched(args):
     """The batched workload: 64 independent problems (Kuhn boxes {1,2}^3,
     levels 3..6, P1-P1 / P2-P1, random smooth forcing, zero Dirichlet data)
@@ -468,6 +510,7 @@ def run_batched(args):
     batch.set_grouping(-1)
     aligned = aligned_batch(timed)
     clocks = sampler.stop()
+    gamma_batch = accuracy_batch()
     # accuracy of a few problems: delta against the discrete solution (Eq. relative-error)
     deltas = []
     for idx in (0, 1, 2):
@@ -500,7 +543,7 @@ def run_batched(args):
                                      "2 (one branch per problem, no merging)": groupings[2]},
                        "sequential_ms": t_seq * 1e3, "batch_speedup_vs_sequential": t_seq / t_batch,
                        "aligned_batch": aligned,
-                       "accuracy": deltas},
+                       "accuracy": deltas, "accuracy_gamma": gamma_batch},
             "clocks": clocks}
     print(json.dumps(line))
 

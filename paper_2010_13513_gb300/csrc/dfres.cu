@@ -235,18 +235,18 @@ __device__ __forceinline__ void df_store(const Geo& g, const OpDev& op, int R, i
 // indexing of the vector row kernels (four runs of 32 positions per warp; a
 // warp whose last run passes the group's last site takes its sites one by one)
 template <int VARNU, int OUT, int OG, int ALL, int T0, int N0, int N1, int N2, class Tab>
-__device__ __forceinline__ void df_rows(const Geo& g, int R, const float* __restrict__ xh,
+__device__ __forceinline__ void df_rows(const uint3 bid, const Geo& g, int R, const float* __restrict__ xh,
                                         const float* __restrict__ xl, const double* __restrict__ b,
                                         float* __restrict__ r, const OpDev& op, const Tab& tab, int kp) {
   constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
   constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
   constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
   constexpr int V = 4;
-  const int m0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * V);
+  const int m0 = ((bid.x * blockDim.x + threadIdx.x) >> 5) * (32 * V);
   const int lane = int(threadIdx.x & 31);
   const int mlast = (g.ny - oy) * g.sx + (g.nx - ox);
   if (m0 > mlast) return;
-  const int k0 = blockIdx.y * kp, k1 = min(k0 + kp, g.nz - oz + 1);
+  const int k0 = bid.y * kp, k1 = min(k0 + kp, g.nz - oz + 1);
   if (m0 + 32 * V - 1 > mlast) {                     // warp-uniform: the plane's last warp
 #pragma unroll 1
     for (int k = k0; k < k1; ++k)
@@ -313,22 +313,29 @@ __device__ __forceinline__ void by_row(int r, F&& f) {
   }
 }
 
+template <int DISC, int VARNU, class Tab>
+__device__ __forceinline__ void res_df_body(const uint3 bid, const Geo& g, const float* __restrict__ xh,
+                                            const float* __restrict__ xl, const double* __restrict__ b,
+                                            float* __restrict__ r, const OpDev& op, int kp, const Tab& tab) {
+  using S = gen::S<DISC, VARNU, OP_FULL>;
+  by_row<S, 0>(int(bid.z), [&](auto rc) {
+    constexpr int R = decltype(rc)::value;
+    constexpr gen::RowS rw = S::rows[R];
+    df_rows<VARNU, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(bid, g, R, xh, xl, b, r, op, tab, kp);
+  });
+}
+
 template <int DISC, int VARNU>
 __global__ void __launch_bounds__(128) k_res_df(Geo g, const float* __restrict__ xh, const float* __restrict__ xl,
                                                 const double* __restrict__ b, float* __restrict__ r, OpDev op, int kp,
                                                 const __grid_constant__ DfTabOf<DISC, VARNU> tab) {
-  using S = gen::S<DISC, VARNU, OP_FULL>;
-  by_row<S, 0>(int(blockIdx.z), [&](auto rc) {
-    constexpr int R = decltype(rc)::value;
-    constexpr gen::RowS rw = S::rows[R];
-    df_rows<VARNU, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(g, R, xh, xl, b, r, op, tab, kp);
-  });
+  res_df_body<DISC, VARNU>(blockIdx, g, xh, xl, b, r, op, kp, tab);
 }
 
 // hi[q] + lo[q] = x[q] (split_df), two elements per thread and step (n even)
-__global__ void k_split_df(const double2* __restrict__ x, float2* __restrict__ hi, float2* __restrict__ lo,
-                           int64_t n2) {
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n2; q += int64_t(gridDim.x) * blockDim.x) {
+__device__ __forceinline__ void split_df_body(const uint3 bid, const uint3 gd, const double2* __restrict__ x,
+                                              float2* __restrict__ hi, float2* __restrict__ lo, int64_t n2) {
+  for (int64_t q = bid.x * int64_t(blockDim.x) + threadIdx.x; q < n2; q += int64_t(gd.x) * blockDim.x) {
     const double2 v = x[q];
     float2 h, l;
     split_df(v.x, h.x, l.x);
@@ -338,6 +345,31 @@ __global__ void k_split_df(const double2* __restrict__ x, float2* __restrict__ h
   }
 }
 
+__global__ void k_split_df(const double2* __restrict__ x, float2* __restrict__ hi, float2* __restrict__ lo,
+                           int64_t n2) {
+  split_df_body(blockIdx, gridDim, x, hi, lo, n2);
+}
+
+// the same two kernels as work items of a merged batch launch (batch.h; the
+// weight table as a device copy)
+struct SplitA { const double2* x; float2* hi; float2* lo; int64_t n2; };
+template <class Tab>
+struct ResDfA { Geo g; const float* xh; const float* xl; const double* b; float* r; OpDev op; int kp; const Tab* tab; };
+
+__global__ void kb_split_df(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<SplitA>(items, n, bid, gd);
+  split_df_body(bid, gd, it.a.x, it.a.hi, it.a.lo, it.a.n2);
+}
+
+template <int DISC, int VARNU>
+__global__ void __launch_bounds__(128) kb_res_df(const void* items, int n) {
+  uint3 bid, gd;
+  const auto& it = batch_item<ResDfA<DfTabOf<DISC, VARNU>>>(items, n, bid, gd);
+  const auto& a = it.a;
+  res_df_body<DISC, VARNU>(bid, a.g, a.xh, a.xl, a.b, a.r, a.op, a.kp, *a.tab);
+}
+
 constexpr int kDfThreads = 128;
 constexpr int kDfPlanes = 2;
 
@@ -345,17 +377,27 @@ template <int DISC, int VARNU>
 void launch_df(const Geo& g, const OpDev& od, const char* tab, const double* x, const double* b, float* xh, float* xl,
                float* r, cudaStream_t s) {
   using S = gen::S<DISC, VARNU, OP_FULL>;
-  DfTabOf<DISC, VARNU> tb;
-  std::memcpy(&tb, tab, sizeof(tb));
+  using Tab = DfTabOf<DISC, VARNU>;
   const int64_t n = (3 * int64_t(g.G) + 1) * g.arr;  // a multiple of 64
   const int64_t n2 = n / 2;
-  ++g_launches;
-  k_split_df<<<unsigned(std::min<int64_t>((n2 + 255) / 256, 152 * 8)), 256, 0, s>>>(
-      reinterpret_cast<const double2*>(x), reinterpret_cast<float2*>(xh), reinterpret_cast<float2*>(xl), n2);
+  const dim3 sgrd(unsigned(std::min<int64_t>((n2 + 255) / 256, 152 * 8)));
+  const SplitA sa{reinterpret_cast<const double2*>(x), reinterpret_cast<float2*>(xh), reinterpret_cast<float2*>(xl),
+                  n2};
   // warps of 4 x 32 positions over the padded plane up to the last site
   const int64_t warps = ((int64_t(g.ny) * g.sx + g.nx + 1) + 127) / 128;
   const dim3 grd(unsigned((warps * 32 + kDfThreads - 1) / kDfThreads), unsigned((g.nz + 1 + kDfPlanes - 1) / kDfPlanes),
                  unsigned(S::R));
+  if (g_rec) {                                       // a batch records: two work items
+    const Tab* dt = static_cast<const Tab*>(g_rec->table(tab, sizeof(Tab)));
+    g_rec->add(reinterpret_cast<const void*>(kb_split_df), sgrd, dim3(256), 0, 1, sa);
+    g_rec->add(reinterpret_cast<const void*>(kb_res_df<DISC, VARNU>), grd, dim3(kDfThreads), 0, 1,
+               ResDfA<Tab>{g, xh, xl, b, r, od, kDfPlanes, dt});
+    return;
+  }
+  Tab tb;
+  std::memcpy(&tb, tab, sizeof(tb));
+  ++g_launches;
+  k_split_df<<<sgrd, 256, 0, s>>>(sa.x, sa.hi, sa.lo, n2);
   ++g_launches;
   k_res_df<DISC, VARNU><<<grd, kDfThreads, 0, s>>>(g, xh, xl, b, r, od, kDfPlanes, tb);
 }
@@ -397,12 +439,7 @@ bool df_table(int disc, int varnu, const std::vector<char>& ftab64, std::vector<
 
 void df_residual(int disc, int varnu, const Geo& g, const OpDev& od, const std::vector<char>& dftab, const double* x,
                  const double* b, float* xh, float* xl, float* r, cudaStream_t s) {
-  const char* tab = dftab.data();
-  if (g_rec) {
-    g_rec->native([=](cudaStream_t s_) { df_launch(disc, varnu, g, od, tab, x, b, xh, xl, r, s_); });
-    return;
-  }
-  df_launch(disc, varnu, g, od, tab, x, b, xh, xl, r, s);
+  df_launch(disc, varnu, g, od, dftab.data(), x, b, xh, xl, r, s);
 }
 
 }  // namespace hhg

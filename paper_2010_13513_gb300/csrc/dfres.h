@@ -23,7 +23,8 @@ bool df_table(int disc, int varnu, const std::vector<char>& ftab64, std::vector<
 // accumulated in double-float arithmetic; xh, xl: scratch of n = (3G + 1) arr
 // floats each (they receive the two FP32 parts of x).  od: the level's
 // generic tables (per-cube terms of the boundary pressure rows).  While a
-// batch records, the launches are recorded as native ops.
+// batch records, the two kernels are recorded as work items (batched
+// variants kb_split_df, kb_res_df) that merge with other problems' ones.
 void df_residual(int disc, int varnu, const Geo& g, const OpDev& od, const std::vector<char>& dftab, const double* x,
                  const double* b, float* xh, float* xl, float* r, cudaStream_t s);
 
