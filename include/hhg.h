@@ -228,8 +228,9 @@ int hhg_residual(hhg_problem* pb, int level, int prec, const void* x, const void
 int hhg_refinement_residual(hhg_problem* pb, int level, const double* x, const double* b, float* r);
 /* Arithmetic of the refinement residual (HHG_REFINE_FP64 or HHG_REFINE_DF32;
  * default HHG_REFINE_DF32, which covers both discretisations with constant
- * or variable viscosity).  Drops cached graphs when the choice changes.  The
- * get call reports the arithmetic in effect. */
+ * or variable viscosity).  Drops the problem's cached graphs when the choice
+ * changes; a batch keeps the choice in effect when its graph was recorded.
+ * The get call reports the arithmetic in effect. */
 int hhg_set_refinement_residual(hhg_problem* pb, int kind);
 int hhg_get_refinement_residual(hhg_problem* pb, int* kind);
 /* `sweeps` inexact Uzawa iterations (Eq. uzawa-iteration) on x in place. */
