@@ -2,9 +2,10 @@
 //
 // The mixed solve (FP32 V-cycles inside an FP64 iterative refinement) needs
 // the outer residual r = b - calA x of every FMG stage to well below FP32
-// rounding.  FP64 arithmetic gives that, but on this GPU the FP64 pipe runs
-// at about 1/64 of the FP32 rate, so the FP64 residual of the finest level is
-// bound by it (it was the largest single kernel of the level-7 solve).  Here
+// rounding.  FP64 arithmetic gives that, but on this GPU FP64 FMAs run at
+// about 1/54 of the FP32 rate (1.26 against 68.5 TFLOP/s measured), so the
+// FP64 residual of the finest level is bound by them (it was the largest
+// single kernel of the level-7 solve).  Here
 // every FP64 value v is carried as two FP32 numbers v = v_hi + v_lo (47
 // significant bits, split by integer bit operations, no FP64 instruction on
 // the common path), and each row is evaluated as the compensated dot product
@@ -21,8 +22,9 @@
 // Work layout (as the vector row kernels of the FP32/FP64 path): grid x over
 // the padded (i, j) plane in warps of 4 x 32 positions, y over groups of kp
 // planes, z over the rows of the operator; a thread evaluates 4 sites 32
-// positions apart, two at a time with the paired FP32 (f32x2) instructions.  The terms of a row are a loop over weights and offsets in
-// the constant bank, so a row's code stays small in the instruction cache.
+// positions apart, two at a time with the paired FP32 (f32x2) instructions.
+// The terms of a row are a loop over weights and offsets in the constant
+// bank, so a row's code stays small in the instruction cache.
 // Boundary pressure rows (P1-P1: the C terms of the cubes inside the box) add
 // their per-cube C terms in FP64; they are a few per cent of the pressure
 // rows.  With a variable viscosity nu = exp(a z) the segments of a row are
