@@ -21,8 +21,9 @@
 //
 // Work layout (as the vector row kernels of the FP32/FP64 path): grid x over
 // the padded (i, j) plane in warps of 4 x 32 positions, y over groups of kp
-// planes, z over the rows of the operator; a thread evaluates 4 sites 32
-// positions apart, two at a time with the paired FP32 (f32x2) instructions.
+// planes, z over the rows of the operator; on large levels a thread
+// evaluates 4 sites 32 positions apart (two at a time with the paired FP32
+// f32x2 instructions) on 2 planes, on small ones 1 site on 1 plane.
 // The terms of a row are a loop over weights and offsets in the constant
 // bank, so a row's code stays small in the instruction cache.
 // Boundary pressure rows (P1-P1: the C terms of the cubes inside the box) add
@@ -236,14 +237,13 @@ __device__ __forceinline__ void df_store(const Geo& g, const OpDev& op, int R, i
 // row R = (OUT, OG, ALL, T0, N0, N1, N2) on the sites of the block: the
 // indexing of the vector row kernels (four runs of 32 positions per warp; a
 // warp whose last run passes the group's last site takes its sites one by one)
-template <int VARNU, int OUT, int OG, int ALL, int T0, int N0, int N1, int N2, class Tab>
+template <int V, int VARNU, int OUT, int OG, int ALL, int T0, int N0, int N1, int N2, class Tab>
 __device__ __forceinline__ void df_rows(const uint3 bid, const Geo& g, int R, const float* __restrict__ xh,
                                         const float* __restrict__ xl, const double* __restrict__ b,
                                         float* __restrict__ r, const OpDev& op, const Tab& tab, int kp) {
   constexpr int ox = OG == 1 || OG == 4 || OG == 5 || OG == 7;
   constexpr int oy = OG == 2 || OG == 4 || OG == 6 || OG == 7;
   constexpr int oz = OG == 3 || OG == 5 || OG == 6 || OG == 7;
-  constexpr int V = 4;
   const int m0 = ((bid.x * blockDim.x + threadIdx.x) >> 5) * (32 * V);
   const int lane = int(threadIdx.x & 31);
   const int mlast = (g.ny - oy) * g.sx + (g.nx - ox);
@@ -315,7 +315,7 @@ __device__ __forceinline__ void by_row(int r, F&& f) {
   }
 }
 
-template <int DISC, int VARNU, class Tab>
+template <int DISC, int VARNU, int V, class Tab>
 __device__ __forceinline__ void res_df_body(const uint3 bid, const Geo& g, const float* __restrict__ xh,
                                             const float* __restrict__ xl, const double* __restrict__ b,
                                             float* __restrict__ r, const OpDev& op, int kp, const Tab& tab) {
@@ -323,15 +323,15 @@ __device__ __forceinline__ void res_df_body(const uint3 bid, const Geo& g, const
   by_row<S, 0>(int(bid.z), [&](auto rc) {
     constexpr int R = decltype(rc)::value;
     constexpr gen::RowS rw = S::rows[R];
-    df_rows<VARNU, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(bid, g, R, xh, xl, b, r, op, tab, kp);
+    df_rows<V, VARNU, rw.out, rw.og, rw.all, rw.t0, rw.n0, rw.n1, rw.n2>(bid, g, R, xh, xl, b, r, op, tab, kp);
   });
 }
 
-template <int DISC, int VARNU>
+template <int DISC, int VARNU, int V>
 __global__ void __launch_bounds__(128) k_res_df(Geo g, const float* __restrict__ xh, const float* __restrict__ xl,
                                                 const double* __restrict__ b, float* __restrict__ r, OpDev op, int kp,
                                                 const __grid_constant__ DfTabOf<DISC, VARNU> tab) {
-  res_df_body<DISC, VARNU>(blockIdx, g, xh, xl, b, r, op, kp, tab);
+  res_df_body<DISC, VARNU, V>(blockIdx, g, xh, xl, b, r, op, kp, tab);
 }
 
 // hi[q] + lo[q] = x[q] (split_df), two elements per thread and step (n even)
@@ -364,16 +364,19 @@ __global__ void kb_split_df(const void* items, int n) {
   split_df_body(bid, gd, it.a.x, it.a.hi, it.a.lo, it.a.n2);
 }
 
-template <int DISC, int VARNU>
+template <int DISC, int VARNU, int V>
 __global__ void __launch_bounds__(128) kb_res_df(const void* items, int n) {
   uint3 bid, gd;
   const auto& it = batch_item<ResDfA<DfTabOf<DISC, VARNU>>>(items, n, bid, gd);
   const auto& a = it.a;
-  res_df_body<DISC, VARNU>(bid, a.g, a.xh, a.xl, a.b, a.r, a.op, a.kp, *a.tab);
+  res_df_body<DISC, VARNU, V>(bid, a.g, a.xh, a.xl, a.b, a.r, a.op, a.kp, *a.tab);
 }
 
 constexpr int kDfThreads = 128;
-constexpr int kDfPlanes = 2;
+// levels with at most this many lattice sites take one site and one plane
+// per thread (the row loops are latency-bound; more threads hide it), larger
+// ones four sites and two planes
+constexpr int64_t kDfSmallSites = 300000;
 
 template <int DISC, int VARNU>
 void launch_df(const Geo& g, const OpDev& od, const char* tab, const double* x, const double* b, float* xh, float* xl,
@@ -385,15 +388,18 @@ void launch_df(const Geo& g, const OpDev& od, const char* tab, const double* x, 
   const dim3 sgrd(unsigned(std::min<int64_t>((n2 + 255) / 256, 152 * 8)));
   const SplitA sa{reinterpret_cast<const double2*>(x), reinterpret_cast<float2*>(xh), reinterpret_cast<float2*>(xl),
                   n2};
-  // warps of 4 x 32 positions over the padded plane up to the last site
-  const int64_t warps = ((int64_t(g.ny) * g.sx + g.nx + 1) + 127) / 128;
-  const dim3 grd(unsigned((warps * 32 + kDfThreads - 1) / kDfThreads), unsigned((g.nz + 1 + kDfPlanes - 1) / kDfPlanes),
+  const bool small = int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1) <= kDfSmallSites;
+  const int v = small ? 1 : 4, kp = small ? 1 : 2;
+  // warps of v x 32 positions over the padded plane up to the last site
+  const int64_t warps = ((int64_t(g.ny) * g.sx + g.nx + 1) + 32 * v - 1) / (32 * v);
+  const dim3 grd(unsigned((warps * 32 + kDfThreads - 1) / kDfThreads), unsigned((g.nz + 1 + kp - 1) / kp),
                  unsigned(S::R));
   if (g_rec) {                                       // a batch records: two work items
     const Tab* dt = static_cast<const Tab*>(g_rec->table(tab, sizeof(Tab)));
     g_rec->add(reinterpret_cast<const void*>(kb_split_df), sgrd, dim3(256), 0, 1, sa);
-    g_rec->add(reinterpret_cast<const void*>(kb_res_df<DISC, VARNU>), grd, dim3(kDfThreads), 0, 1,
-               ResDfA<Tab>{g, xh, xl, b, r, od, kDfPlanes, dt});
+    g_rec->add(small ? reinterpret_cast<const void*>(kb_res_df<DISC, VARNU, 1>)
+                     : reinterpret_cast<const void*>(kb_res_df<DISC, VARNU, 4>),
+               grd, dim3(kDfThreads), 0, 1, ResDfA<Tab>{g, xh, xl, b, r, od, kp, dt});
     return;
   }
   Tab tb;
@@ -401,7 +407,8 @@ void launch_df(const Geo& g, const OpDev& od, const char* tab, const double* x, 
   ++g_launches;
   k_split_df<<<sgrd, 256, 0, s>>>(sa.x, sa.hi, sa.lo, n2);
   ++g_launches;
-  k_res_df<DISC, VARNU><<<grd, kDfThreads, 0, s>>>(g, xh, xl, b, r, od, kDfPlanes, tb);
+  if (small) k_res_df<DISC, VARNU, 1><<<grd, kDfThreads, 0, s>>>(g, xh, xl, b, r, od, kp, tb);
+  else k_res_df<DISC, VARNU, 4><<<grd, kDfThreads, 0, s>>>(g, xh, xl, b, r, od, kp, tb);
 }
 
 void df_launch(int disc, int varnu, const Geo& g, const OpDev& od, const char* tab, const double* x, const double* b,
