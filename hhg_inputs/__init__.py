@@ -62,6 +62,37 @@ def kuhn_box_macro_mesh(mx: int, my: int, mz: int, H: float = 1.0):
     return verts, np.array(tets, dtype=np.int32)
 
 
+def cube24_macro_mesh():
+    """The unit cube as 24 macro tetrahedra: the cube's 8 corners, its 6 face
+    centres and its centre; every face is cut into 4 triangles (two adjacent
+    corners and the face centre), each the base of one tetrahedron with apex at
+    the cube centre.  Not a Kuhn box (its refinement is not one lattice).
+
+    Returns (verts (15,3) float64, tets (24,4) int32)."""
+    corners = [(i, j, k) for k in (0, 1) for j in (0, 1) for i in (0, 1)]
+    verts = [tuple(float(c) for c in v) for v in corners]
+    tets = []
+    for d in range(3):
+        for side in (0.0, 1.0):
+            fc = [0.5, 0.5, 0.5]
+            fc[d] = side
+            verts.append(tuple(fc))
+            f = len(verts) - 1
+            # the face's corners in cyclic order around it
+            a, b = [e for e in range(3) if e != d]
+            ring = []
+            for ua, ub in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                v = [0.0, 0.0, 0.0]
+                v[d], v[a], v[b] = side, float(ua), float(ub)
+                ring.append(verts.index(tuple(v)))
+            for q in range(4):
+                tets.append([ring[q], ring[(q + 1) % 4], f])
+    verts.append((0.5, 0.5, 0.5))
+    c = len(verts) - 1
+    tets = [t + [c] for t in tets]
+    return np.array(verts, dtype=np.float64), np.array(tets, dtype=np.int32)
+
+
 # ---------------------------------------------------------------------------
 # manufactured solution "curl" (divergence-free by construction)
 # ---------------------------------------------------------------------------

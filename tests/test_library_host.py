@@ -8,7 +8,7 @@ import subprocess
 import numpy as np
 import pytest
 
-from hhg_inputs import kuhn_box_macro_mesh
+from hhg_inputs import cube24_macro_mesh, kuhn_box_macro_mesh
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -59,6 +59,12 @@ def test_mesh_rejects_other_meshes(hhg):
     buf = C.create_string_buffer(256)
     hhg.load().hhg_last_error(buf, 256)
     assert b"origin" in buf.value
+    # the paper's cube of 24 macro tetrahedra (corners, face centres, centre)
+    # is not a Kuhn box: rejected with the reason
+    v24, t24 = cube24_macro_mesh()
+    assert _create(hhg, v24, t24) == -1
+    hhg.load().hhg_last_error(buf, 256)
+    assert b"Kuhn" in buf.value
 
 
 def _problem(hhg, disc, L, lc, solve=0, err=0, box=(1, 1, 1), nu_a=0.0):

@@ -110,6 +110,58 @@ def test_table1_unknown_counts(level):
     assert t1["vertices"] == (N(n - 3), N(n + 1))
 
 
+def _refined_mesh_counts(verts, tets, level):
+    """(vertices, edges, faces, tetrahedra, boundary faces, volume) of the
+    macro mesh refined `level` times by Bey's rule; points keyed on the
+    dyadic grid of spacing 2^-(level+2), faces with the number of
+    tetrahedra that share them."""
+    kids = bey_refine(verts, tets, level)
+    s = 2.0 ** (level + 2)
+    key = lambda x: tuple(int(round(c * s)) for c in x)
+    V, E, F = set(), set(), {}
+    vol = 0.0
+    for t in kids:
+        ks = [key(x) for x in t]
+        V.update(ks)
+        E.update(frozenset((ks[a], ks[b])) for a in range(4) for b in range(a + 1, 4))
+        for f in itertools.combinations(ks, 3):
+            F[frozenset(f)] = F.get(frozenset(f), 0) + 1
+        X = np.array(t)
+        vol += abs(np.linalg.det(X[1:] - X[0])) / 6.0
+    assert set(F.values()) <= {1, 2}                       # conforming: a face is shared by at most two
+    return len(V), len(E), len(F), len(kids), sum(1 for m in F.values() if m == 1), vol
+
+
+def test_cube24_refinement_counts_and_paper_unknowns():
+    """The cube of 24 macro tetrahedra of Sec. 5.1.1 (corners, face centres,
+    centre): Bey refinement (Sec. 2) gives conforming meshes of volume 1
+    whose vertex, edge, face and tetrahedron counts follow uniform refinement
+    (every edge gets a midpoint, every face three inner edges and four faces,
+    every tetrahedron one inner edge, eight inner faces and eight children),
+    and continuing those counts to the paper's levels gives the unknowns it
+    quotes: about 4.3e6 for P1-P1 at L = 6 (four fields on the vertices) and
+    about 3.4e6 for P2-P1 at L = 5 (velocity on the level-6 vertices, which are
+    the level-5 P2 nodes, pressure on the level-5 vertices)."""
+    from hhg_inputs import cube24_macro_mesh
+    verts, tets = cube24_macro_mesh()
+    V, E, F, T = 15, 50, 60, 24
+    counts = [(V, E, F, T)]
+    for _ in range(6):
+        V, E, F, T = V + E, 2 * E + 3 * F + T, 4 * F + 8 * T, 8 * T
+        counts.append((V, E, F, T))
+    for level in (0, 1, 2):
+        v, e, f, t, fb, vol = _refined_mesh_counts(verts, tets, level)
+        assert (v, e, f, t) == counts[level]
+        assert fb == 24 * 4 ** level                        # the cube's 6 faces, 4 triangles each
+        assert v - e + f - t == 1                           # Euler characteristic of a ball
+        assert vol == pytest.approx(1.0, rel=1e-12)
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cube24_unknowns.json")))
+    p1 = 4 * counts[6][0]
+    p2 = 3 * counts[6][0] + counts[5][0]
+    assert (p1, p2) == (4293636, 3357572)
+    assert round(p1, -5) == gold["P1P1_L6_about"] and round(p2, -5) == gold["P2P1_L5_about"]
+
+
 @pytest.mark.parametrize("level", [1, 2, 3])
 def test_p2_nodes_equal_p1_next_level(level):
     a = Lattice((1, 1, 1), 1.0, level)
