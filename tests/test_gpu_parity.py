@@ -630,6 +630,36 @@ def test_batch_merges_aligned_problems():
     assert counts[1][0] <= counts[0][0] <= counts[2][0] + 50, counts
 
 
+def test_batch_variable_viscosity_matches_individual_solves():
+    """Mixed-precision problems with nu = exp(a z) in one batch (the
+    double-float defect's variable-viscosity kernels as merged work items):
+    every problem gets exactly its individual FMG result, merged and not."""
+    from hhg_inputs import Workload
+    from paper_2010_13513_gb300 import hhg
+    stream = torch.cuda.Stream()
+    specs = [("P1P1", (1, 1, 1), 0.9), ("P1P1", (2, 1, 1), 0.9), ("P2P1", (1, 1, 1), 1.4)]
+    pbs, prms, refs = [], [], []
+    with torch.cuda.stream(stream):
+        for i, (disc, box, nu_a) in enumerate(specs):
+            wl = Workload("modes", seed=300 + i, box=box, H=1.0 / max(box))
+            pbs.append(lib_problem(box, 3, disc, lc=1, solve="mixed", nu_a=nu_a, workload=wl))
+            prms.append(hhg.Params.make(1, 2, 1, 1, "f", 2, OMEGA_INV[disc]))
+        batch = hhg.Batch(pbs)
+        for pb, prm in zip(pbs, prms):
+            assert pb.refinement_residual_kind() == "df32"
+            x = pb.new_vector(3)
+            pb.fmg_solve(prm, x, stats=False)
+            refs.append(x.clone())
+        for grouping in (1, 2):
+            batch.set_grouping(grouping)
+            for pb in pbs:
+                pb.level_vector(pb.L, "x").zero_()
+            batch.fmg_solve(prms, stream)
+            stream.synchronize()
+            for pb, ref in zip(pbs, refs):
+                assert torch.equal(pb.level_vector(pb.L, "x"), ref), grouping
+
+
 def test_autotune_keeps_results():
     from paper_2010_13513_gb300 import hhg
     pb = lib_problem((1, 1, 1), 4, "P2P1", lc=1, solve="mixed", workload=curl_workload())
