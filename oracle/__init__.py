@@ -12,6 +12,11 @@ Modules:
                   transfers, bordered coarse solve, V-cycle, FMG, errors,
                   power iteration for omega^{-1}
   * workmodel  -- the paper's work-unit model
+  * unstructured -- the operator blocks on Bey-refined unstructured macro
+                  meshes (the paper's 24-tetrahedron cube), assembled
+                  element by element without a lattice
+  * sampled    -- single rows of the operator at any level
+  * mlp        -- the learned coarse correction's network (reference)
 
 Every function here is pinned by a test in tests/test_oracle_pins.py against
 values the paper prints, closed forms, invariants, dense linear algebra or

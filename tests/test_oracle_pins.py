@@ -162,6 +162,70 @@ def test_cube24_refinement_counts_and_paper_unknowns():
     assert round(p1, -5) == gold["P1P1_L6_about"] and round(p2, -5) == gold["P2P1_L5_about"]
 
 
+@pytest.mark.parametrize("disc,box,H", [("P1P1", (1, 1, 1), 1.0), ("P2P1", (1, 1, 1), 1.0),
+                                        ("P1P1", (2, 1, 1), 0.5), ("P2P1", (1, 2, 1), 0.5)])
+def test_unstructured_assembly_equals_lattice_on_kuhn_boxes(disc, box, H):
+    """The element-by-element assembly on a Bey-refined macro mesh
+    (oracle/unstructured.py, no lattice) and the lattice assembly
+    (StokesLevel) give the same blocks, masses and Dirichlet nodes on Kuhn
+    boxes, entry by entry: two independent paths to Eq. stokes-discrete."""
+    from oracle.unstructured import UnstructuredLevel
+    verts, tets = kuhn_box_macro_mesh(*box, H)
+    u = UnstructuredLevel(verts, tets, 2, disc)
+    lev = StokesLevel(box, H, 2, disc)
+    assert (u.nv, u.np) == (lev.nv, lev.np)
+    for a, b in [(u.A, lev.A), (u.Mv, lev.Mv), (u.C, lev.C), (u.Mp, lev.Mp_full)] + list(zip(u.B, lev.B)):
+        scale = max(abs(b).max(), 1e-300)
+        assert abs(a - b).max() <= 1e-13 * scale
+    assert np.array_equal(u.vbnd, lev.vbnd)
+    x = np.random.default_rng(5).uniform(-1, 1, lev.size)
+    x[:3 * lev.nv] *= np.tile(lev.vint, 3)
+    assert np.allclose(u.apply(x), lev.apply(x), rtol=0, atol=1e-13 * np.abs(lev.apply(x)).max())
+
+
+@pytest.mark.parametrize("disc,level", [("P1P1", 2), ("P2P1", 1)])
+def test_unstructured_operators_on_cube24(disc, level):
+    """Eq. stokes-discrete on the paper's cube of 24 macro tetrahedra (not a
+    Kuhn box): node counts of the refinement (P2 nodes = next level's
+    vertices), Dirichlet nodes = the nodes on the cube's surface, masses
+    integrating to the volume, A and C symmetric with zero row sums, A
+    annihilating linear fields at interior nodes and reproducing -Laplace(q)
+    for a quadratic q with P2, and the divergence blocks exact on linear
+    (P1) or quadratic (P2) velocities: (B_d u)_k = -int psi_k d_d u."""
+    from hhg_inputs import cube24_macro_mesh
+    from oracle.unstructured import UnstructuredLevel
+    verts, tets = cube24_macro_mesh()
+    u = UnstructuredLevel(verts, tets, level, disc)
+    V = [15, 65, 369, 2465]
+    assert u.np == V[level] and u.nv == (V[level] if disc == "P1P1" else V[level + 1])
+    on_surface = lambda P: np.any((np.abs(P) < 1e-12) | (np.abs(P - 1.0) < 1e-12), axis=1)
+    assert np.array_equal(u.vbnd, on_surface(u.vcoords))
+    one_v, one_p = np.ones(u.nv), np.ones(u.np)
+    assert one_v @ (u.Mv @ one_v) == pytest.approx(1.0, rel=1e-13)
+    assert one_p @ (u.Mp @ one_p) == pytest.approx(1.0, rel=1e-13)
+    for M, one in ((u.A, one_v), (u.C, one_p)):
+        size = max(abs(M).max(), 1e-300)
+        assert abs(M - M.T).max() <= 1e-14 * size
+        assert np.abs(M @ one).max() <= 1e-12 * size
+    X, Y, Z = u.vcoords.T
+    Xp = u.pcoords
+    lin = 0.3 * X - 0.7 * Y + 1.1 * Z
+    assert np.abs((u.A @ lin)[u.vint]).max() <= 1e-12 * abs(u.A).max()
+    if disc == "P2P1":
+        q = X * X + 2 * Y * Y - Z * Z + X * Y                   # Laplace q = 2 + 4 - 2 = 4
+        ref = -4.0 * (u.Mv @ one_v)
+        assert np.abs((u.A @ q - ref)[u.vint]).max() <= 1e-12 * np.abs(ref).max()
+    xp, yp, zp = Xp.T
+    for d, coord in enumerate((X, Y, Z)):
+        if disc == "P1P1":
+            # u_d = coordinate d: div u = 1
+            assert np.allclose(u.B[d] @ coord, -(u.Mp @ one_p), rtol=0, atol=1e-13)
+        else:
+            # u_d = coordinate d squared: div u = 2 x_d, linear, so the P1 pressure mass is exact
+            pd = (xp, yp, zp)[d]
+            assert np.allclose(u.B[d] @ (coord * coord), -2.0 * (u.Mp @ pd), rtol=0, atol=1e-13)
+
+
 @pytest.mark.parametrize("level", [1, 2, 3])
 def test_p2_nodes_equal_p1_next_level(level):
     a = Lattice((1, 1, 1), 1.0, level)
